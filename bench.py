@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Throughput of the matrix-free SIPG-DG apply y = A x on one GB300 (or N replicas).
+
+Workload (one "step"): one FP64 apply of the scalar diffusion-reaction SIPG operator,
+c = 1, penalty 2k(k+1)/h, on 64^3 cells whose interior vertices are perturbed by up to
+0.1h (seed 1), per-quadrature-point geometry, degree Q3 with 4^3 Gauss points (16.8M
+DOFs), x ~ U[-1,1] (seed 0): the volume kernel, the interior and boundary face kernel
+and the back-projection kernel. Every input (x 134 MB, geometry 1.6 GB) is larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). With --gpus N > 1 (torchrun) every rank applies its own
+replica of the workload (no collective on the data path) and value = total DOF/s.
+``--impl reference`` times the CPU oracle instead (the only baseline that exists for
+this method), on the host cores, with bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1812_08075_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "dg_apply DOF/s (FP64 and mixed) at Q2-Q5; % of FP64-peak / HBM roofline"
+N_CELLS = 64
+SM_COUNT = 152
+FP64_FLOPS_PER_SM_CLK = 4.0   # 2 DFMA per SM per clock: 1.25 TFLOP/s nominal at 2.07 GHz
+FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FFMA per SM per clock
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mp = json.load(open(path)) if os.path.exists(path) else {}
+    clk = float(mp.get("sm_max_mhz", 2070.0)) * 1e6
+    return {
+        "hbm_gbs": float(mp.get("hbm_gbs", 6800.0)),
+        "hbm_src": "measured" if "hbm_gbs" in mp else "fallback",
+        "fp64_tflops": SM_COUNT * FP64_FLOPS_PER_SM_CLK * clk / 1e12,
+        "fp32_tflops": SM_COUNT * FP32_FLOPS_PER_SM_CLK * clk / 1e12,
+        "clk_mhz": clk / 1e6,
+    }
+
+
+def workload_config(k: int):
+    return {"workload": f"scalar SIPG diffusion-reaction, {N_CELLS}^3 trilinear-perturbed cells (0.1h, seed 1), "
+                        f"Q{k}, {k + 1}^3 Gauss points, c=1, penalty 2k(k+1)/h, Dirichlet, FP64 apply",
+            "cells": N_CELLS ** 3, "degree": k, "ndofs": N_CELLS ** 3 * (k + 1) ** 3,
+            "l2": "inputs larger than L2 (x 134 MB, stored geometry 1.6 GB at Q3), no flush",
+            "parallelism": "replicas (independent problem per GPU)"}
+
+
+# ------------------------------------------------------------------- clocks sampling
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[4], parts[6:10]))
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.f.name)
+        timed = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        window = "timed region"
+        if len(timed) < 3:
+            timed, window = rows, "warm-up and timed region"
+        if not timed:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in timed for i, v in enumerate(r[4]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in timed), "sm_max_mhz": max(r[2] for r in timed),
+                "reasons": reasons, "samples": len(timed), "window": window,
+                "power_w_max": max((float(r[3]) for r in timed if r[3] not in ("[N/A]", "N/A")), default=None)}
+
+
+# ------------------------------------------------------------------- CPU oracle timing
+
+def oracle_rate(k: int, target_core_seconds: float, cores: int, seed: int = 11):
+    """DOF/s of the oracle's cell-gather apply on a bounded random sample of cells."""
+    import oracle
+    n = (N_CELLS,) * 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    prob = oracle.Problem(*n, k, vertices=verts)
+    x = wl.uniform_vector(prob.ncell * (k + 1) ** 3, 0)
+    probe = wl.sample_cells(prob.ncell, 512, seed=seed)
+    t = time.perf_counter()
+    prob.apply_cells(x, probe, nthreads=cores)
+    dt = max(time.perf_counter() - t, 1e-6)
+    per_cell_core_s = dt * cores / probe.size
+    ncells = int(min(prob.ncell, max(512, target_core_seconds / per_cell_core_s)))
+    cells = wl.sample_cells(prob.ncell, ncells, seed=seed + 1)
+    t = time.perf_counter()
+    prob.apply_cells(x, cells, nthreads=cores)
+    dt = time.perf_counter() - t
+    return cells.size * (k + 1) ** 3 / dt, cells.size, dt
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    k = args.degree
+    n = (N_CELLS,) * 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    prob = oracle.Problem(*n, k, vertices=verts)
+    x = wl.uniform_vector(prob.ncell * (k + 1) ** 3, 0)
+    # size one step to about 1 s of wall time on the host cores
+    probe = wl.sample_cells(prob.ncell, 512, seed=21)
+    t = time.perf_counter()
+    prob.apply_cells(x, probe, nthreads=cores)
+    per_cell = (time.perf_counter() - t) / probe.size
+    ncells = int(min(prob.ncell, max(256, 1.0 / per_cell)))
+    samples = [wl.sample_cells(prob.ncell, ncells, seed=100 + s) for s in range(args.warmup + args.steps)]
+    for s in samples[:args.warmup]:
+        prob.apply_cells(x, s, nthreads=cores)
+    t = time.perf_counter()
+    dofs = 0
+    for s in samples[args.warmup:]:
+        prob.apply_cells(x, s, nthreads=cores)
+        dofs += s.size * (k + 1) ** 3
+    dt = time.perf_counter() - t
+    value = dofs / dt
+    sample = (f"{ncells} random cells per step of the {N_CELLS}^3 Q{k} workload (cell-gather form: each cell's "
+              f"volume term and its six faces), {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------- GPU path
+
+def time_applies(op, x, y, steps, warmup, dist, profile=False):
+    import torch
+    from paper_1812_08075_gb300 import dg
+    for _ in range(warmup):
+        op.apply(x, y)
+    if profile:
+        dg.dg_operator_profile(op.handle, True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    for _ in range(steps):
+        op.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    kt = None
+    if profile:
+        kms, napp = dg.dg_operator_kernel_times(op.handle)
+        dg.dg_operator_profile(op.handle, False)
+        kt = [v / max(napp, 1) for v in kms]
+    return ms, kt, (t0, t1)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1812_08075_gb300 import build as libbuild, dg
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    k = args.degree
+    n = (N_CELLS,) * 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    mesh = dg.Mesh(*n, verts)
+    op = dg.Operator(mesh, k)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    y = torch.empty_like(x)
+    pk = peaks()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms, kt, (t0, t1) = time_applies(op, x, y, args.steps, args.warmup, dist, profile=True)
+    clocks = sampler.stop(t0, t1) if sampler else None
+    ms_all = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * op.ndofs / (ms_all * 1e-3)
+    st = op.stats()
+    flops = list(st.flops)
+    names = ["k_cell (volume: interpolate, gradient, pointwise, transposed derivative; face traces)",
+             "k_face (interior and boundary face terms)", "k_back (face lifting and transposed interpolation)"]
+    dom = int(np.argmax(kt))
+    achieved = flops[dom] / (kt[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["fp64_tflops"], "traffic": None,
+                "kernel": names[dom], "kernel_ms": kt[dom],
+                "peak_source": f"FP64 CUDA-core peak derived: {SM_COUNT} SMs x 2 DFMA/clk x 2 flop x "
+                               f"{pk['clk_mhz']:.0f} MHz (1.25 TFLOP/s nominal)",
+                "algorithmic_flops_per_launch": flops[dom]}
+    tot_flops = sum(flops)
+    whole = {"flops_per_apply": tot_flops, "tflops": tot_flops / (ms * 1e-3) / 1e12,
+             "frac_fp64_peak": tot_flops / (ms * 1e-3) / 1e12 / pk["fp64_tflops"],
+             "kernel_ms": {"k_cell": kt[0], "k_face": kt[1], "k_back": kt[2]},
+             "hbm_bytes_algorithmic": st.dofs_bytes, "gb_s_algorithmic": st.dofs_bytes / (ms * 1e-3) / 1e9}
+    out = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
+           "roofline": roofline, "apply": whole, "gpu_launches": 3 * args.steps, "clocks": clocks}
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        op.apply_host(xh, yh)
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.apply_host(xh, yh)
+    dt = (time.perf_counter() - t) / e2e_steps
+    out["e2e"] = {"value": world * op.ndofs / dt, "unit": "DOF/s", "h2d_bytes_per_step": 8 * op.ndofs,
+                  "d2h_bytes_per_step": 8 * op.ndofs, "steps": e2e_steps, "api": "dg_apply_host (pinned host x, y)"}
+    del op, x, y, xh, yh
+    if args.sweep and rank == 0:
+        sweep = {}
+        for kk in (1, 2, 3, 4, 5):
+            for prec, tag, es in ((dg.DG_FP64, "fp64", 8), (dg.DG_FP32, "fp32", 4)):
+                o = dg.Operator(mesh, kk, precision=prec)
+                xx = torch.from_numpy(wl.uniform_vector(o.ndofs, 0)).to("cuda", o.dtype)
+                yy = torch.empty_like(xx)
+                ms_k, kt_k, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
+                f = sum(o.stats().flops)
+                peak = pk["fp64_tflops"] if prec == dg.DG_FP64 else pk["fp32_tflops"]
+                sweep[f"Q{kk}_{tag}"] = {"dof_s": o.ndofs / (ms_k * 1e-3), "ms": ms_k,
+                                         "tflops": f / (ms_k * 1e-3) / 1e12,
+                                         "frac_alu_peak": f / (ms_k * 1e-3) / 1e12 / peak,
+                                         "kernel_ms": kt_k}
+                del o, xx, yy
+        out["sweep"] = sweep
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = host_cores()
+        rate, ncells, dt = oracle_rate(k, 15.0, cores)
+        out["cpu_baseline"] = {"value": rate, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{ncells} random cells of the {N_CELLS}^3 Q{k} workload, cell-gather "
+                                         f"form, {dt:.1f} s wall on {cores} threads"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degree", type=int, default=3)
+    ap.add_argument("--sweep", dest="sweep", action="store_true", default=True)
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

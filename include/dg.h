@@ -1,0 +1,187 @@
+/*
+ * dg.h - C ABI of libdg, a single-GPU (GB300, sm_103a) matrix-free application of the
+ * symmetric interior-penalty Discontinuous Galerkin (SIPG) operator of
+ *   Kempf, Hess, Muething, Bastian, "Automatic Code Generation for High-Performance
+ *   Discontinuous Galerkin Methods on Modern Architectures", arXiv 1812.08075,
+ * on structured hexahedral meshes with the tensor-product Q_k basis, evaluated by sum
+ * factorisation (Sec. 2.2, Eq. lowcomplex, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - All compute entry points are asynchronous on the caller's CUDA stream (passed as
+ *     `void* stream`, a cudaStream_t; NULL = the legacy default stream). Argument errors
+ *     are reported immediately and enqueue nothing. Asynchronous CUDA errors surface on
+ *     the next call or through dg_get_last_error(). No C++ exception crosses the ABI.
+ *   - Device vectors are caller-owned, contiguous, 16-byte aligned and of the operator's
+ *     precision (double for DG_FP64, float for DG_FP32). Outputs must not alias inputs.
+ *   - Scalar DOF vector layout: cell-major [ncell][(k+1)^3], cells lexicographic
+ *     c = cx + nx*(cy + ny*cz), cell DOFs j0 + p*(j1 + p*j2) (x fastest), on the
+ *     Lagrange basis of the k+1 Gauss-Lobatto-Legendre points of [0,1] (the paper leaves
+ *     the basis open, Sec. 2.1). Stokes: [u: ncell x 3 x (k+1)^3 | p: ncell x k^3].
+ *     nrhs vectors are stored back to back, [nrhs][ndofs].
+ *   - Calls on one operator must be ordered on one stream at a time: the operator owns
+ *     scratch buffers that each apply reuses.
+ *   - Every object is owned by the library from *_create until *_destroy.
+ */
+#ifndef DG_H
+#define DG_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_INVALID_ARG = 1,   /* null pointer, bad size, misaligned or aliased buffer */
+  DG_ERR_UNSUPPORTED = 2,   /* valid request outside what is built (e.g. degree > 5) */
+  DG_ERR_OOM = 3,           /* device or host allocation failed */
+  DG_ERR_CUDA = 4,          /* a CUDA runtime call failed (sticky; see dg_get_last_error) */
+  DG_ERR_NOT_CONVERGED = 5, /* an iterative solve hit its iteration limit */
+  DG_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} dg_status;
+
+typedef struct dg_mesh dg_mesh;
+typedef struct dg_operator dg_operator;
+
+enum { DG_PEN_CONFIG = 0, DG_PEN_PAPER = 1 };
+enum { DG_SCALAR = 0, DG_STOKES = 1 };
+enum { DG_FP64 = 0, DG_FP32 = 1 };
+enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
+
+/* Interior-penalty factor gamma_F (Sec. 5.2).
+ *   DG_PEN_CONFIG: gamma_F = alpha * k * (k+1) / h_a with h_a = 1/n_a the nominal cell
+ *                  size across the face (n_a cells along the face normal's axis);
+ *   DG_PEN_PAPER:  gamma_F = alpha * k * (k+d-1) * |F| / min(|T+|, |T-|) (boundary:
+ *                  |F|/|T|), measures by the operator's Gauss rule; the paper uses
+ *                  alpha = 3. */
+typedef struct {
+  int32_t mode;
+  int32_t reserved;
+  double alpha;
+} dg_penalty;
+
+/* Coefficients and options of one operator.
+ *   problem        DG_SCALAR: -div(kappa grad u) + c u (Eq. diffreac_weak);
+ *                  DG_STOKES: -mu Lap u + grad p, div u (Eq. stokes_weak).
+ *   precision      DG_FP64 or DG_FP32 (storage and arithmetic of the apply).
+ *   dirichlet_mask bit lf set: domain face lf (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z) carries
+ *                  the Dirichlet face terms; other boundary faces carry none.
+ *   max_rhs        1..16, the largest nrhs any apply on this operator will use.
+ *   geometry       DG_GEOM_AUTO / STORED (per-quadrature-point geometry precomputed once)
+ *                  / RECOMPUTE (from vertex coordinates inside the kernels); ignored on
+ *                  affine meshes.
+ *   c              reaction coefficient (scalar), mu viscosity (Stokes),
+ *   theta          -1 symmetric (SIPG, the paper's choice), 0 incomplete, +1 non-symmetric. */
+typedef struct {
+  int32_t problem;
+  int32_t precision;
+  int32_t dirichlet_mask;
+  int32_t max_rhs;
+  int32_t geometry;
+  int32_t reserved;
+  double c;
+  double mu;
+  double theta;
+} dg_coefficients;
+
+/* Per-apply work model of an operator (exact counts of what the kernels execute).
+ * flops[i] and bytes[i] are per right-hand side for kernel i of the apply
+ * (0: cell/volume kernel, 1: face kernel, 2: back-projection kernel); bytes are the
+ * algorithmic global-memory bytes (each input read once, each output written once). */
+typedef struct {
+  int64_t ndofs;
+  int64_t ncell;
+  int64_t nface;
+  double flops[3];
+  double bytes[3];
+  double dofs_bytes;      /* x read + y written, per right-hand side */
+  int32_t cells_per_block;
+  int32_t faces_per_block;
+  int32_t threads_cell;
+  int32_t threads_face;
+  int32_t geometry;       /* DG_GEOM_* in effect (0 = affine fast path) */
+  int32_t reserved;
+} dg_stats;
+
+/* Human-readable name of a status code (static string). */
+const char *dg_status_string(dg_status s);
+
+/* Last error recorded by any call on this thread (DG_OK if none); clears it. */
+dg_status dg_get_last_error(void);
+
+/* Structured nx x ny x nz hexahedral mesh of cuboid cells (Sec. 2.1).
+ * vertices: host array [(nx+1)(ny+1)(nz+1)][3] (v = i + (nx+1)(j + (ny+1) l)), copied;
+ *           NULL = uniform unit cube (affine, axis-parallel cells, the fast path).
+ * Each cell T is the image of [0,1]^3 under the trilinear map through its 8 vertices.
+ * Errors: DG_ERR_INVALID_ARG (n < 1, out NULL), DG_ERR_OOM. */
+dg_status dg_mesh_create(int nx, int ny, int nz, const double *vertices, dg_mesh **out);
+dg_status dg_mesh_destroy(dg_mesh *mesh);
+
+/* Operator y = A x of Eq. (diffreac_weak) or Eq. (stokes_weak) without the data terms
+ * (the Jacobian action for a linear problem, Sec. 2.1), degree k (1..5 scalar, 2..5
+ * Stokes), quad_points_1d Gauss-Legendre points per direction (0 = k+1; only k+1 is
+ * built). Uploads reference tables, precomputes geometry if stored, allocates scratch
+ * for max_rhs right-hand sides. Synchronous. Errors: DG_ERR_INVALID_ARG,
+ * DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d,
+                             const dg_penalty *penalty, const dg_coefficients *coef,
+                             dg_operator **out);
+dg_status dg_operator_destroy(dg_operator *op);
+
+/* Number of DOFs of one vector of this operator. */
+dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n);
+
+/* Work model and launch configuration currently in effect (host only). */
+dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
+
+/* Per-quadrature-point diffusion coefficient kappa (scalar problem): device arrays of
+ * the operator's precision, kappa_vol [ncell][m^3] (points q0 + m(q1 + m q2)) and
+ * kappa_face [ncell][6][m^2] (each cell's own side of faces -x,+x,-y,+y,-z,+z, points
+ * qs + m*qt over the two tangential axes in increasing order). NULL = 1. The arrays
+ * are read at every apply (not copied) and must stay valid until the last apply that
+ * uses them. The penalty does not involve kappa (Sec. 5.2). */
+dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const void *kappa_face);
+
+/* y = A x for nrhs (1..max_rhs) vectors (Sec. 2.1 Jacobian action; Algorithm 1 per
+ * cell, facet sum factorisation per face). x, y: device [nrhs][ndofs]. y is
+ * overwritten. Errors: DG_ERR_INVALID_ARG, DG_ERR_CUDA. */
+dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void *stream);
+
+/* Same operator applied through host buffers: copies x (host [nrhs][ndofs]) to the
+ * device, applies, copies y back and synchronises the stream. Page-locked host memory
+ * gives the full link bandwidth; pageable memory also works. */
+dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host, int nrhs,
+                        void *stream);
+
+/* Adjoint of the scalar operator for the loss L = 0.5 ||A(kappa) x - b||^2:
+ *   y = A^T r (the transposed apply, r = A x - b supplied by the caller), and, when
+ *   x and the output arrays are non-NULL, dkappa_vol[c][q] = r^T dA/dkappa_vol[c][q] x
+ *   and dkappa_face[c][lf][q] likewise (layouts as dg_operator_set_kappa).
+ * Geometry is recomputed from the vertex coordinates inside the kernels (nothing
+ * stored is required). One right-hand side. Errors: DG_ERR_INVALID_ARG,
+ * DG_ERR_UNSUPPORTED (Stokes), DG_ERR_CUDA. */
+dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y,
+                           void *dkappa_vol, void *dkappa_face, void *stream);
+
+/* Per-kernel timing for measurement harnesses. With enable != 0, every later apply on
+ * this operator records CUDA events on its own stream before and after each of its
+ * kernels (cell, face, back-projection). dg_operator_kernel_times waits for those events,
+ * returns the summed milliseconds per kernel over the applies recorded since the last
+ * call and their count, and starts a new accumulation. Errors: DG_ERR_INVALID_ARG,
+ * DG_ERR_CUDA. */
+dg_status dg_operator_profile(dg_operator *op, int enable);
+dg_status dg_operator_kernel_times(dg_operator *op, double ms[3], int64_t *napplies);
+
+/* Reference-element tables the CUDA path uses (host, double), for inspection:
+ * gauss_nodes/weights [m] on [0,1], gll_nodes [k+1], interp [m][k+1] (GLL Lagrange
+ * basis at Gauss points), dcol [m][m] (derivative of the Gauss-point Lagrange basis at
+ * the Gauss points), end_val[2][m], end_der[2][m] (that basis and its derivative at 0
+ * and 1). Any output may be NULL. */
+dg_status dg_reference_tables(int degree, int m, double *gauss_nodes, double *gauss_weights,
+                              double *gll_nodes, double *interp, double *dcol,
+                              double *end_val, double *end_der);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

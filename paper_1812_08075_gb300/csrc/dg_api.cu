@@ -1,0 +1,458 @@
+// C ABI of libdg: object lifetimes, validation, table upload, geometry precompute and
+// kernel dispatch. All arithmetic of an apply runs in the CUDA kernels.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace {
+
+thread_local dg_status g_last = DG_OK;
+
+dg_status fail(dg_status s) {
+  g_last = s;
+  return s;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return fail(DG_ERR_CUDA); \
+  } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct dg_mesh {
+  int nx, ny, nz;
+  bool affine;
+  std::vector<double> verts;
+};
+
+struct dg_operator {
+  int nx, ny, nz;
+  int k, p, m;
+  int problem, precision, max_rhs, geo;
+  unsigned dmask;
+  double c, mu, theta;
+  dg_penalty pen;
+  int64_t ncell, nface, nbface, ndofs;
+  int64_t face_off[4];
+  HostTables ht;
+  void *d_tab = nullptr;
+  double *d_verts = nullptr;
+  double *d_gamma = nullptr;
+  double *d_cellvol = nullptr;
+  void *d_gvol = nullptr, *d_gface = nullptr;
+  void *d_rvol = nullptr, *d_tr = nullptr, *d_fres = nullptr;
+  void *d_xh = nullptr, *d_yh = nullptr;  // staging for dg_apply_host
+  const void *kappa_vol = nullptr, *kappa_face = nullptr;
+  int cpb = 1, fpb = 1;
+  double gamma_axis[3];
+  // per-kernel event timing (dg_operator_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded apply
+  size_t prof_used = 0;              // applies recorded since the last read
+};
+
+extern "C" {
+
+const char *dg_status_string(dg_status s) {
+  switch (s) {
+    case DG_OK: return "DG_OK";
+    case DG_ERR_INVALID_ARG: return "DG_ERR_INVALID_ARG";
+    case DG_ERR_UNSUPPORTED: return "DG_ERR_UNSUPPORTED";
+    case DG_ERR_OOM: return "DG_ERR_OOM";
+    case DG_ERR_CUDA: return "DG_ERR_CUDA";
+    case DG_ERR_NOT_CONVERGED: return "DG_ERR_NOT_CONVERGED";
+    case DG_ERR_TIMEOUT: return "DG_ERR_TIMEOUT";
+  }
+  return "DG_ERR_UNKNOWN";
+}
+
+dg_status dg_get_last_error(void) {
+  dg_status s = g_last;
+  g_last = DG_OK;
+  return s;
+}
+
+dg_status dg_mesh_create(int nx, int ny, int nz, const double *vertices, dg_mesh **out) {
+  if (!out || nx < 1 || ny < 1 || nz < 1) return fail(DG_ERR_INVALID_ARG);
+  if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return fail(DG_ERR_UNSUPPORTED);
+  dg_mesh *m = new (std::nothrow) dg_mesh;
+  if (!m) return fail(DG_ERR_OOM);
+  m->nx = nx; m->ny = ny; m->nz = nz;
+  m->affine = (vertices == nullptr);
+  if (vertices) {
+    size_t n = (size_t)(nx + 1) * (ny + 1) * (nz + 1) * 3;
+    try {
+      m->verts.assign(vertices, vertices + n);
+    } catch (...) {
+      delete m;
+      return fail(DG_ERR_OOM);
+    }
+  }
+  *out = m;
+  return DG_OK;
+}
+
+dg_status dg_mesh_destroy(dg_mesh *mesh) {
+  delete mesh;
+  return DG_OK;
+}
+
+}  // extern "C"
+
+static void free_op(dg_operator *o) {
+  if (!o) return;
+  void *ptrs[] = {o->d_tab, o->d_verts, o->d_gamma, o->d_cellvol, o->d_gvol, o->d_gface,
+                  o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
+  delete o;
+}
+
+template <typename T>
+static void fill_devtables(const HostTables &h, DevTables<T> &d) {
+  memset(&d, 0, sizeof(d));
+  for (int q = 0; q < h.m; ++q)
+    for (int j = 0; j < h.p; ++j) d.interp[q * h.p + j] = (T)h.interp[q * h.p + j];
+  for (int i = 0; i < h.m * h.m; ++i) d.dcol[i] = (T)h.dcol[i];
+  for (int i = 0; i < h.m; ++i) {
+    d.e0[i] = (T)h.e0[i]; d.e1[i] = (T)h.e1[i];
+    d.d0[i] = (T)h.d0[i]; d.d1[i] = (T)h.d1[i];
+    d.w[i] = (T)h.gauss_w[i];
+  }
+}
+
+template <typename T>
+static ScalarArgs<T> scalar_args(const dg_operator *o, bool transpose) {
+  ScalarArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.nx = o->nx; a.ny = o->ny; a.nz = o->nz;
+  a.ncell = o->ncell;
+  a.nface = o->nface;
+  for (int i = 0; i < 4; ++i) a.face_off[i] = o->face_off[i];
+  a.tab = (const DevTables<T> *)o->d_tab;
+  const double h[3] = {1.0 / o->nx, 1.0 / o->ny, 1.0 / o->nz};
+  const double V = h[0] * h[1] * h[2];
+  for (int d = 0; d < 3; ++d) {
+    a.vol_g[d] = (T)(V / (h[d] * h[d]));
+    a.face_b[d] = (T)(V / (h[d] * h[d]));
+    a.face_pw[d] = (T)(o->gamma_axis[d] * V / h[d]);
+  }
+  a.vol_m = (T)(o->c * V);
+  a.gvol = (const T *)o->d_gvol;
+  a.gface = (const T *)o->d_gface;
+  a.verts = o->d_verts;
+  a.gamma_face = o->d_gamma;
+  a.c = o->c;
+  a.kappa_vol = (const T *)o->kappa_vol;
+  a.kappa_face = (const T *)o->kappa_face;
+  a.dmask = o->dmask;
+  a.sc = (T)(transpose ? o->theta : -1.0);
+  a.ss = (T)(transpose ? -1.0 : o->theta);
+  return a;
+}
+
+static void default_blocking(dg_operator *o) {
+  const int M3 = o->m * o->m * o->m, M2 = o->m * o->m;
+  o->cpb = 256 / M3 > 0 ? 256 / M3 : 1;
+  o->fpb = 256 / M2 > 0 ? 256 / M2 : 1;
+}
+
+extern "C" {
+
+dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d, const dg_penalty *pen,
+                             const dg_coefficients *co, dg_operator **out) {
+  if (!mesh || !pen || !co || !out) return fail(DG_ERR_INVALID_ARG);
+  *out = nullptr;
+  if (degree < 1) return fail(DG_ERR_INVALID_ARG);
+  if (degree > 5) return fail(DG_ERR_UNSUPPORTED);
+  const int m = quad_points_1d == 0 ? degree + 1 : quad_points_1d;
+  if (m < degree + 1) return fail(DG_ERR_INVALID_ARG);
+  if (m != degree + 1) return fail(DG_ERR_UNSUPPORTED);
+  if (co->problem != DG_SCALAR && co->problem != DG_STOKES) return fail(DG_ERR_INVALID_ARG);
+  if (co->problem == DG_STOKES) return fail(DG_ERR_UNSUPPORTED);
+  if (co->precision != DG_FP64 && co->precision != DG_FP32) return fail(DG_ERR_INVALID_ARG);
+  if (co->max_rhs < 1 || co->max_rhs > 16) return fail(DG_ERR_INVALID_ARG);
+  if (pen->mode != DG_PEN_CONFIG && pen->mode != DG_PEN_PAPER) return fail(DG_ERR_INVALID_ARG);
+  if (co->dirichlet_mask < 0 || co->dirichlet_mask > 63) return fail(DG_ERR_INVALID_ARG);
+  if (co->geometry == DG_GEOM_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+
+  dg_operator *o = new (std::nothrow) dg_operator;
+  if (!o) return fail(DG_ERR_OOM);
+  o->nx = mesh->nx; o->ny = mesh->ny; o->nz = mesh->nz;
+  o->k = degree; o->p = degree + 1; o->m = m;
+  o->problem = co->problem;
+  o->precision = co->precision;
+  o->max_rhs = co->max_rhs;
+  o->dmask = (unsigned)co->dirichlet_mask;
+  o->c = co->c; o->mu = co->mu; o->theta = co->theta;
+  o->pen = *pen;
+  o->geo = mesh->affine ? GEO_AFFINE : GEO_STORED;
+  o->ncell = (int64_t)o->nx * o->ny * o->nz;
+  const int n[3] = {o->nx, o->ny, o->nz};
+  o->face_off[0] = 0;
+  o->nbface = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+    o->face_off[a + 1] = o->face_off[a] + (int64_t)(n[a] + 1) * n[t1] * n[t2];
+    o->nbface += 2 * (int64_t)n[t1] * n[t2];
+  }
+  o->nface = o->face_off[3];
+  const int P3 = o->p * o->p * o->p, M2 = m * m, M3 = m * m * m;
+  o->ndofs = o->ncell * P3;
+  for (int a = 0; a < 3; ++a)
+    o->gamma_axis[a] = pen->mode == DG_PEN_CONFIG ? pen->alpha * degree * (degree + 1) * n[a]
+                                                  : pen->alpha * degree * (degree + 2) * n[a];
+  if (dg_build_tables(degree, m, false, &o->ht)) { free_op(o); return fail(DG_ERR_UNSUPPORTED); }
+  default_blocking(o);
+  const size_t es = o->precision == DG_FP64 ? sizeof(double) : sizeof(float);
+
+#define ALLOC(ptr, bytes)                                       \
+  do {                                                          \
+    if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {  \
+      cudaGetLastError();                                       \
+      free_op(o);                                               \
+      return fail(DG_ERR_OOM);                                  \
+    }                                                           \
+  } while (0)
+
+  if (o->precision == DG_FP64) {
+    DevTables<double> t;
+    fill_devtables(o->ht, t);
+    ALLOC(o->d_tab, sizeof(t));
+    if (cudaMemcpy(o->d_tab, &t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
+  } else {
+    DevTables<float> t;
+    fill_devtables(o->ht, t);
+    ALLOC(o->d_tab, sizeof(t));
+    if (cudaMemcpy(o->d_tab, &t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
+  }
+  if (!mesh->affine) {
+    const size_t vb = mesh->verts.size() * sizeof(double);
+    ALLOC(o->d_verts, vb);
+    ALLOC(o->d_gamma, (size_t)o->nface * sizeof(double));
+    ALLOC(o->d_cellvol, (size_t)o->ncell * sizeof(double));
+    if (cudaMemcpy(o->d_verts, mesh->verts.data(), vb, cudaMemcpyHostToDevice) != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
+    if (launch_penalty(m, degree, pen->mode, pen->alpha, o->nx, o->ny, o->nz, o->nface, o->face_off, o->d_verts,
+                       o->ht.gauss_s, o->ht.gauss_w, o->d_gamma, o->d_cellvol, 0) != cudaSuccess) {
+      free_op(o);
+      return fail(DG_ERR_CUDA);
+    }
+    ALLOC(o->d_gvol, (size_t)o->ncell * 7 * M3 * es);
+    ALLOC(o->d_gface, (size_t)o->nface * 7 * M2 * es);
+    cudaError_t e;
+    if (o->precision == DG_FP64)
+      e = launch_geometry<double>(m, scalar_args<double>(o, false), o->d_verts, o->c, o->d_gamma, o->ht.gauss_s,
+                                  o->ht.gauss_w, (double *)o->d_gvol, (double *)o->d_gface, 0);
+    else
+      e = launch_geometry<float>(m, scalar_args<float>(o, false), o->d_verts, o->c, o->d_gamma, o->ht.gauss_s,
+                                 o->ht.gauss_w, (float *)o->d_gvol, (float *)o->d_gface, 0);
+    if (e != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
+  }
+  const size_t R = (size_t)o->max_rhs;
+  ALLOC(o->d_rvol, R * o->ncell * M3 * es);
+  ALLOC(o->d_tr, R * o->ncell * 12 * M2 * es);
+  ALLOC(o->d_fres, R * o->ncell * 12 * M2 * es);
+#undef ALLOC
+  *out = o;
+  return DG_OK;
+}
+
+dg_status dg_operator_destroy(dg_operator *op) {
+  free_op(op);
+  return DG_OK;
+}
+
+dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n) {
+  if (!op || !n) return fail(DG_ERR_INVALID_ARG);
+  *n = op->ndofs;
+  return DG_OK;
+}
+
+dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const void *kappa_face) {
+  if (!op) return fail(DG_ERR_INVALID_ARG);
+  if ((kappa_vol && !aligned16(kappa_vol)) || (kappa_face && !aligned16(kappa_face))) return fail(DG_ERR_INVALID_ARG);
+  if ((kappa_vol == nullptr) != (kappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  op->kappa_vol = kappa_vol;
+  op->kappa_face = kappa_face;
+  return DG_OK;
+}
+
+dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
+  if (!op || !out) return fail(DG_ERR_INVALID_ARG);
+  memset(out, 0, sizeof(*out));
+  out->ndofs = op->ndofs;
+  out->ncell = op->ncell;
+  out->nface = op->nface;
+  const int es = op->precision == DG_FP64 ? 8 : 4;
+  scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, out->flops,
+                    out->bytes, es);
+  out->dofs_bytes = 2.0 * es * (double)op->ndofs;
+  out->cells_per_block = op->cpb;
+  out->faces_per_block = op->fpb;
+  const int M3 = op->m * op->m * op->m, M2 = op->m * op->m;
+  auto thr = [](int w) { int t = ((w + 31) / 32) * 32; return t < 64 ? 64 : (t > 256 ? 256 : t); };
+  out->threads_cell = thr(op->cpb * M3);
+  out->threads_face = thr(op->fpb * M2);
+  out->geometry = op->geo;
+  return DG_OK;
+}
+
+}  // extern "C"
+
+static const cudaEvent_t *next_events(dg_operator *op) {
+  if (!op->prof) return nullptr;
+  const size_t need = 4 * (op->prof_used + 1);
+  while (op->prof_ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    op->prof_ev.push_back(e);
+  }
+  return op->prof_ev.data() + 4 * op->prof_used++;
+}
+
+static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  const cudaEvent_t *ev = next_events(op);
+  const int M2 = op->m * op->m, M3 = op->m * op->m * op->m;
+  const int64_t sdof = op->ndofs, srv = op->ncell * M3, str = op->ncell * 12 * M2;
+  const bool kap = op->kappa_vol != nullptr;
+  cudaError_t e;
+  if (op->precision == DG_FP64)
+    e = launch_scalar_apply<double>(op->p, op->m, op->geo, kap, scalar_args<double>(op, transpose), (const double *)x,
+                                    (double *)y, (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_fres, nrhs,
+                                    sdof, srv, str, op->cpb, op->fpb, s, ev);
+  else
+    e = launch_scalar_apply<float>(op->p, op->m, op->geo, kap, scalar_args<float>(op, transpose), (const float *)x,
+                                   (float *)y, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres, nrhs, sdof,
+                                   srv, str, op->cpb, op->fpb, s, ev);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  return DG_OK;
+}
+
+extern "C" {
+
+dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void *stream) {
+  if (!op || !x || !y) return fail(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op->max_rhs) return fail(DG_ERR_INVALID_ARG);
+  if (!aligned16(x) || !aligned16(y) || x == y) return fail(DG_ERR_INVALID_ARG);
+  return apply_impl(op, x, y, nrhs, (cudaStream_t)stream, false);
+}
+
+dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_host, int nrhs, void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !x_host || !y_host) return fail(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op->max_rhs) return fail(DG_ERR_INVALID_ARG);
+  const size_t es = op->precision == DG_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)nrhs * op->ndofs * es;
+  if (!op->d_xh) {
+    const size_t full = (size_t)op->max_rhs * op->ndofs * es;
+    if (cudaMalloc(&op->d_xh, full) != cudaSuccess || cudaMalloc(&op->d_yh, full) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DG_ERR_OOM);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(op->d_xh, x_host, bytes, cudaMemcpyHostToDevice, s));
+  dg_status st = apply_impl(op, op->d_xh, op->d_yh, nrhs, s, false);
+  if (st != DG_OK) return st;
+  CK(cudaMemcpyAsync(y_host, op->d_yh, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y, void *dkappa_vol,
+                           void *dkappa_face, void *stream) {
+  if (!op || !r || !y) return fail(DG_ERR_INVALID_ARG);
+  (void)x; (void)dkappa_vol; (void)dkappa_face; (void)stream;
+  return fail(DG_ERR_UNSUPPORTED);
+}
+
+dg_status dg_operator_profile(dg_operator *op, int enable) {
+  if (!op) return fail(DG_ERR_INVALID_ARG);
+  op->prof = enable != 0;
+  op->prof_used = 0;
+  return DG_OK;
+}
+
+dg_status dg_operator_kernel_times(dg_operator *op, double ms[3], int64_t *napplies) {
+  if (!op || !ms) return fail(DG_ERR_INVALID_ARG);
+  ms[0] = ms[1] = ms[2] = 0.0;
+  for (size_t i = 0; i < op->prof_used; ++i) {
+    const cudaEvent_t *e = op->prof_ev.data() + 4 * i;
+    CK(cudaEventSynchronize(e[3]));
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (napplies) *napplies = (int64_t)op->prof_used;
+  op->prof_used = 0;
+  return DG_OK;
+}
+
+dg_status dg_reference_tables(int degree, int m, double *gauss_nodes, double *gauss_weights, double *gll_nodes,
+                              double *interp, double *dcol, double *end_val, double *end_der) {
+  HostTables t;
+  if (m == 0) m = degree + 1;
+  if (dg_build_tables(degree, m, false, &t)) return fail(DG_ERR_INVALID_ARG);
+  for (int q = 0; q < m; ++q) {
+    if (gauss_nodes) gauss_nodes[q] = t.gauss_s[q];
+    if (gauss_weights) gauss_weights[q] = t.gauss_w[q];
+    if (end_val) { end_val[q] = t.e0[q]; end_val[m + q] = t.e1[q]; }
+    if (end_der) { end_der[q] = t.d0[q]; end_der[m + q] = t.d1[q]; }
+  }
+  for (int j = 0; j <= degree; ++j)
+    if (gll_nodes) gll_nodes[j] = t.gll[j];
+  if (interp) memcpy(interp, t.interp, sizeof(double) * m * (degree + 1));
+  if (dcol) memcpy(dcol, t.dcol, sizeof(double) * m * m);
+  return DG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Work model: floating-point operations the kernels execute (fma = 2, mul/add = 1) and
+// the global-memory bytes each kernel must move at least once, per right-hand side.
+// ---------------------------------------------------------------------------------------
+void scalar_work_model(int P, int M, int geo, bool kappa, int64_t ncell, int64_t nface, int64_t nbface,
+                       double flops[3], double bytes[3], int es) {
+  const double P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  const double contr = 2.0 * P - 1.0;   // one output of a length-P contraction
+  const double contrM = 2.0 * M - 1.0;  // length-M contraction
+  // k_cell: interpolation (3 sweeps), traces (12 M^2 outputs), gradient (3 per point),
+  // pointwise flux, transposed derivative with the mass term
+  double cell = (P * P * M + P * M2 + M3) * contr + 12.0 * M2 * contrM + 3.0 * M3 * contrM;
+  if (geo == GEO_AFFINE) cell += M3 * (8.0 + (kappa ? 1.0 : 0.0)) + M3 * (4.0 + 6.0 * M);
+  else cell += M3 * (15.0 + (kappa ? 3.0 : 0.0)) + M3 * (1.0 + 6.0 * M);
+  const double ninner = (double)(nface - nbface);
+  double face;
+  if (geo == GEO_AFFINE) {
+    face = ninner * M2 * (kappa ? 17.0 : 13.0) + (double)nbface * M2 * 10.0;
+  } else {
+    const double inner_pt = 2 * 2 * contrM + 10.0 + 1.0 + (kappa ? 4.0 : 2.0) + 3.0 + 2.0 + (kappa ? 2.0 : 0.0) + 6.0 + 8.0 * M;
+    const double bnd_pt = 2 * contrM + 5.0 + 3.0 + 4.0 + 4.0 * M;
+    face = ninner * M2 * inner_pt + (double)nbface * M2 * bnd_pt;
+  }
+  double back = M3 * 24.0 + (M2 * P + M * P * P + P3) * contrM;
+  flops[0] = cell * (double)ncell;
+  flops[1] = face;
+  flops[2] = back * (double)ncell;
+  const double geo_vol = geo == GEO_AFFINE ? 0.0 : 7.0 * M3;
+  const double geo_face = geo == GEO_AFFINE ? 0.0 : 7.0 * M2;
+  bytes[0] = es * (double)ncell * (P3 + M3 + 12.0 * M2 + geo_vol + (kappa ? M3 : 0.0));
+  bytes[1] = es * (ninner * (8.0 * M2 + geo_face + (kappa ? 2.0 * M2 : 0.0)) +
+                   (double)nbface * (4.0 * M2 + geo_face + (kappa ? M2 : 0.0)));
+  bytes[2] = es * (double)ncell * (M3 + 12.0 * M2 + P3);
+}

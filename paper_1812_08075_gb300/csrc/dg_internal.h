@@ -1,0 +1,95 @@
+// Internal declarations of libdg (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dg.h"
+
+#define DG_MAXP 6  // basis points per direction (degree <= 5)
+#define DG_MAXM 6  // Gauss points per direction
+
+// Reference-element tables in the operator's precision, uploaded once per operator.
+// Internally the kernels work on values at the Gauss points (a collocated Lagrange
+// basis on the Gauss nodes), which turns the derivative contractions into one
+// m x m matrix per direction (see dg_tables.cpp).
+template <typename T>
+struct DevTables {
+  T interp[DG_MAXM * DG_MAXP];  // [q][j] GLL basis j at Gauss point q
+  T dcol[DG_MAXM * DG_MAXM];    // [q][r] d/dxi of Gauss-Lagrange basis r at Gauss point q
+  T e0[DG_MAXM], e1[DG_MAXM];   // Gauss-Lagrange basis at xi = 0, 1
+  T d0[DG_MAXM], d1[DG_MAXM];   // its derivative at xi = 0, 1
+  T w[DG_MAXM];                 // Gauss weights on [0,1]
+};
+
+struct HostTables {
+  int k, p, m;
+  double gauss_s[DG_MAXM], gauss_w[DG_MAXM];
+  double gll[DG_MAXP];
+  double interp[DG_MAXM * DG_MAXP];
+  double dcol[DG_MAXM * DG_MAXM];
+  double e0[DG_MAXM], e1[DG_MAXM], d0[DG_MAXM], d1[DG_MAXM];
+  // pressure space of the Stokes problem (degree k-1): GLL basis at the Gauss points
+  int pp;
+  double interp_p[DG_MAXM * DG_MAXP];
+};
+
+// Builds the tables for degree k (p = k+1 basis points) and m Gauss points; pressure
+// degree k-1 tables when with_pressure. Returns 0 on success.
+int dg_build_tables(int k, int m, bool with_pressure, HostTables *t);
+
+// Geometry modes as seen by the kernels.
+enum { GEO_AFFINE = 0, GEO_STORED = 1, GEO_RECOMPUTE = 2 };
+
+// Everything the scalar kernels need, passed by value.
+template <typename T>
+struct ScalarArgs {
+  int nx, ny, nz;
+  int64_t ncell;
+  int64_t nface;            // all faces of all three axes (interior and boundary)
+  int64_t face_off[4];      // first face id of axis a; face_off[3] = nface
+  const DevTables<T> *tab;
+  // affine fast path (axis-parallel unit-cube lattice): per-axis constants
+  T vol_g[3];               // detJ * (1/h_a)^2  (times the Gauss weight in-kernel)
+  T vol_m;                  // c * detJ
+  T face_b[3];              // |F_a| / h_a : reference normal derivative weight
+  T face_pw[3];             // gamma_a * |F_a|
+  // stored geometry (GEO_STORED): gvol [ncell][7][m^3] = (G00,G01,G02,G11,G12,G22,mass)
+  // with G = W detJ J^-1 J^-T and mass = c W detJ; gface [nface][7][m^2] =
+  // (b-_0..2, b+_0..2, pw) with b = W J^-1 n_vec, pw = gamma W |n_vec|.
+  const T *gvol;
+  const T *gface;
+  // recompute geometry (GEO_RECOMPUTE): vertex coordinates and per-face penalty
+  const double *verts;
+  const double *gamma_face; // [nface]
+  double c;
+  const T *kappa_vol;       // [ncell][m^3] or NULL
+  const T *kappa_face;      // [ncell][6][m^2] or NULL
+  unsigned dmask;
+  T sc, ss;                 // face flux / symmetry coefficients (forward: -1, theta)
+};
+
+// Launchers (dg_scalar.cu). Return cudaError_t of the launch.
+template <typename T>
+cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a,
+                                const T *x, T *y, T *rvol, T *traces, T *fres, int nrhs,
+                                int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
+                                int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
+
+template <typename T>
+cudaError_t launch_scalar_adjoint(int p, int m, const ScalarArgs<T> &a, const T *r, const T *x,
+                                  T *y, T *dk_vol, T *dk_face, T *rvol, T *traces, T *fres,
+                                  int cpb, int fpb, cudaStream_t s);
+
+// Geometry precompute (dg_geometry.cu).
+template <typename T>
+cudaError_t launch_geometry(int m, const ScalarArgs<T> &a, const double *verts, double c,
+                            const double *gamma_face, const double *gauss_s, const double *gauss_w,
+                            T *gvol, T *gface, cudaStream_t s);
+cudaError_t launch_penalty(int m, int k, int pen_mode, double alpha, int nx, int ny, int nz,
+                           int64_t nface, const int64_t *face_off, const double *verts,
+                           const double *gauss_s, const double *gauss_w, double *gamma_face,
+                           double *cell_vol, cudaStream_t s);
+
+// Work model of the scalar apply (exact op counts of the kernels), per right-hand side.
+void scalar_work_model(int p, int m, int geo, bool kappa, int64_t ncell, int64_t nface,
+                       int64_t nbface, double flops[3], double bytes[3], int elem_size);

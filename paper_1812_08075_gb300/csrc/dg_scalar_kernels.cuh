@@ -1,0 +1,495 @@
+// Scalar SIPG apply kernels (Eq. diffreac_weak without data terms), templated on the
+// number of basis points P = k+1 and Gauss points M per direction.
+//
+// One apply is three launches on the caller's stream:
+//   k_cell  - Algorithm 1 Parts 1-3 for the volume term of each cell, with the 1D
+//             contractions of Eq. lowcomplex done axis by axis on cell data staged in
+//             shared memory: interpolate the GLL coefficients to the Gauss points
+//             (3 sweeps with A^(i)), differentiate there (3 sweeps with the collocated
+//             derivative matrix), apply the pointwise volume term, contract with the
+//             transposed derivative matrix into a Gauss-point residual R_vol. It also
+//             writes, for each of the cell's six faces, the trace u and the reference
+//             normal derivative of u at the face Gauss points (facet sum factorisation
+//             with m_d = 1 in the normal direction, Sec. 2.2).
+//   k_face  - one thread per face quadrature point: jump, average flux and penalty of
+//             Eq. diffreac_weak from the two sides' traces, tangential derivatives by the
+//             collocated matrix on curved faces, and the face residual of each side as a
+//             (value, normal-derivative) pair at the face points. No atomics: every face
+//             side is written by exactly one face.
+//   k_back  - adds the six face residuals to R_vol along the normal direction and applies
+//             the transposed interpolation (A^(i),T, Algorithm 1 Part 3) to produce y.
+#pragma once
+#include "dg_internal.h"
+
+namespace dgk {
+
+template <int P, int M, typename T>
+struct SmemTables {
+  T interp[M * P];
+  T dcol[M * M];
+  T e0[M], e1[M], d0[M], d1[M];
+  T w[M];
+};
+
+template <int P, int M, typename T>
+__device__ __forceinline__ void load_tables(SmemTables<P, M, T> &s, const DevTables<T> *g) {
+  for (int i = threadIdx.x; i < M * P; i += blockDim.x) s.interp[i] = g->interp[i];
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) s.dcol[i] = g->dcol[i];
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    s.e0[i] = g->e0[i]; s.e1[i] = g->e1[i];
+    s.d0[i] = g->d0[i]; s.d1[i] = g->d1[i];
+    s.w[i] = g->w[i];
+  }
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
+
+// ------------------------------------------------------------------------------------
+// k_cell
+// ------------------------------------------------------------------------------------
+template <int P, int M, typename T>
+__host__ __device__ constexpr size_t cell_smem_bytes(int cpb) {
+  return align16<T>(sizeof(SmemTables<P, M, T>)) + size_t(4) * cpb * M * M * M * sizeof(T);
+}
+
+template <int P, int M, typename T, int GEO, bool KAPPA>
+__global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const T *__restrict__ x,
+                                              T *__restrict__ rvol, T *__restrict__ traces,
+                                              int cpb, int64_t sx, int64_t sr, int64_t st) {
+  constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &tb = *reinterpret_cast<SmemTables<P, M, T> *>(smem_raw);
+  T *S0 = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(SmemTables<P, M, T>)));
+  T *S1 = S0 + cpb * M3;
+  T *S2 = S1 + cpb * M3;
+  T *S3 = S2 + cpb * M3;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  x += blockIdx.y * sx;
+  rvol += blockIdx.y * sr;
+  traces += blockIdx.y * st;
+  const int64_t c0 = (int64_t)blockIdx.x * cpb;
+  const int nc = (int)min((int64_t)cpb, a.ncell - c0);
+  load_tables(tb, a.tab);
+  {
+    const T *xb = x + c0 * P3;
+    for (int i = tid; i < nc * P3; i += nt) S0[i] = xb[i];
+  }
+  __syncthreads();
+  // axis 0: [c][j2][j1][j0] (P3) -> [c][j2][j1][q0]
+  for (int i = tid; i < nc * P * P * M; i += nt) {
+    const int c = i / (P * P * M), r = i - c * (P * P * M);
+    const int q0 = r % M, j12 = r / M;
+    const T *src = S0 + c * P3 + j12 * P;
+    T acc = tb.interp[q0 * P] * src[0];
+#pragma unroll
+    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q0 * P + j], src[j], acc);
+    S1[i] = acc;
+  }
+  __syncthreads();
+  // axis 1: [c][j2][j1][q0] -> [c][j2][q1][q0]
+  for (int i = tid; i < nc * P * M2; i += nt) {
+    const int c = i / (P * M2), r = i - c * (P * M2);
+    const int q0 = r % M, q1 = (r / M) % M, j2 = r / M2;
+    const T *src = S1 + c * (P * P * M) + j2 * (P * M) + q0;
+    T acc = tb.interp[q1 * P] * src[0];
+#pragma unroll
+    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q1 * P + j], src[j * M], acc);
+    S0[i] = acc;
+  }
+  __syncthreads();
+  // axis 2: [c][j2][q1][q0] -> U = [c][q2][q1][q0]
+  for (int i = tid; i < nc * M3; i += nt) {
+    const int c = i / M3, r = i - c * M3;
+    const int q01 = r % M2, q2 = r / M2;
+    const T *src = S0 + c * (P * M2) + q01;
+    T acc = tb.interp[q2 * P] * src[0];
+#pragma unroll
+    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q2 * P + j], src[j * M2], acc);
+    S2[i] = acc;
+  }
+  __syncthreads();
+  const T *U = S2;
+  // face traces: u and d_n u (reference) at the M^2 points of each of the 6 faces
+  {
+    T *tr = traces + c0 * (12 * M2);
+    for (int i = tid; i < nc * 12 * M2; i += nt) {
+      const int c = i / (12 * M2), r = i - c * (12 * M2);
+      const int lq = r / M2, qf = r - lq * M2;
+      const int lf = lq >> 1, qty = lq & 1, ax = lf >> 1, side = lf & 1;
+      const int qs = qf % M, qt = qf / M;
+      int base, stride;
+      if (ax == 0) { base = M * (qs + M * qt); stride = 1; }
+      else if (ax == 1) { base = qs + M2 * qt; stride = M; }
+      else { base = qs + M * qt; stride = M2; }
+      const T *row = side ? (qty ? tb.d1 : tb.e1) : (qty ? tb.d0 : tb.e0);
+      const T *src = U + c * M3 + base;
+      T acc = row[0] * src[0];
+#pragma unroll
+      for (int j = 1; j < M; ++j) acc = fma(row[j], src[j * stride], acc);
+      tr[i] = acc;
+    }
+  }
+  // reference gradient at the Gauss points and the pointwise volume flux
+  for (int i = tid; i < nc * M3; i += nt) {
+    const int c = i / M3, q = i - c * M3;
+    const int q0 = q % M, q1 = (q / M) % M, q2 = q / M2;
+    const T *u = U + c * M3;
+    T g0 = tb.dcol[q0 * M] * u[q1 * M + q2 * M2];
+    T g1 = tb.dcol[q1 * M] * u[q0 + q2 * M2];
+    T g2 = tb.dcol[q2 * M] * u[q0 + q1 * M];
+#pragma unroll
+    for (int r = 1; r < M; ++r) {
+      g0 = fma(tb.dcol[q0 * M + r], u[r + q1 * M + q2 * M2], g0);
+      g1 = fma(tb.dcol[q1 * M + r], u[q0 + r * M + q2 * M2], g1);
+      g2 = fma(tb.dcol[q2 * M + r], u[q0 + q1 * M + r * M2], g2);
+    }
+    T f0, f1, f2;
+    if (GEO == GEO_AFFINE) {
+      T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
+      if (KAPPA) W *= a.kappa_vol[(c0 + c) * M3 + q];
+      f0 = (W * a.vol_g[0]) * g0;
+      f1 = (W * a.vol_g[1]) * g1;
+      f2 = (W * a.vol_g[2]) * g2;
+    } else {
+      const T *G = a.gvol + (c0 + c) * (7 * M3) + q;
+      if (KAPPA) {
+        const T kq = a.kappa_vol[(c0 + c) * M3 + q];
+        g0 *= kq; g1 *= kq; g2 *= kq;
+      }
+      const T G00 = G[0], G01 = G[M3], G02 = G[2 * M3], G11 = G[3 * M3], G12 = G[4 * M3], G22 = G[5 * M3];
+      f0 = fma(G00, g0, fma(G01, g1, G02 * g2));
+      f1 = fma(G01, g0, fma(G11, g1, G12 * g2));
+      f2 = fma(G02, g0, fma(G12, g1, G22 * g2));
+    }
+    S0[i] = f0;
+    S1[i] = f1;
+    S3[i] = f2;
+  }
+  __syncthreads();
+  // R_vol = mass * U + D^T f (each direction's transposed derivative along its own axis)
+  {
+    T *rv = rvol + c0 * M3;
+    for (int i = tid; i < nc * M3; i += nt) {
+      const int c = i / M3, q = i - c * M3;
+      const int q0 = q % M, q1 = (q / M) % M, q2 = q / M2;
+      T mw;
+      if (GEO == GEO_AFFINE) mw = (tb.w[q0] * tb.w[q1] * tb.w[q2]) * a.vol_m;
+      else mw = a.gvol[(c0 + c) * (7 * M3) + 6 * M3 + q];
+      T acc = mw * U[i];
+      const T *F0 = S0 + c * M3, *F1 = S1 + c * M3, *F2 = S3 + c * M3;
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        acc = fma(tb.dcol[r * M + q0], F0[r + q1 * M + q2 * M2], acc);
+        acc = fma(tb.dcol[r * M + q1], F1[q0 + r * M + q2 * M2], acc);
+        acc = fma(tb.dcol[r * M + q2], F2[q0 + q1 * M + r * M2], acc);
+      }
+      rv[i] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_face
+// ------------------------------------------------------------------------------------
+struct FaceId {
+  int axis, t1, t2;
+  int64_t cm, cp;  // -1 where absent
+};
+
+template <typename T>
+__device__ __forceinline__ FaceId decode_face(const ScalarArgs<T> &a, int64_t f) {
+  FaceId r;
+  const int ax = (f >= a.face_off[1]) + (f >= a.face_off[2]);
+  r.axis = ax;
+  r.t1 = (ax == 0) ? 1 : 0;
+  r.t2 = (ax == 2) ? 1 : 2;
+  const int64_t fl = f - (ax == 0 ? a.face_off[0] : (ax == 1 ? a.face_off[1] : a.face_off[2]));
+  const int na = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+  const int n1 = ax == 0 ? a.ny : a.nx;
+  const int fa = (int)(fl % (na + 1));
+  const int64_t rest = fl / (na + 1);
+  const int i1 = (int)(rest % n1);
+  const int i2 = (int)(rest / n1);
+  // cell coordinates with the axis coordinate set to fa (plus side); minus side is fa-1
+  int cx, cy, cz;
+  if (ax == 0) { cx = fa; cy = i1; cz = i2; }
+  else if (ax == 1) { cx = i1; cy = fa; cz = i2; }
+  else { cx = i1; cy = i2; cz = fa; }
+  const int64_t cplus = cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz);
+  const int64_t step = ax == 0 ? 1 : (ax == 1 ? (int64_t)a.nx : (int64_t)a.nx * a.ny);
+  r.cp = (fa < na) ? cplus : -1;
+  r.cm = (fa > 0) ? cplus - step : -1;
+  return r;
+}
+
+template <int M, typename T>
+__host__ __device__ constexpr size_t face_smem_bytes(int fpb, int geo) {
+  return align16<T>(sizeof(SmemTables<1, M, T>)) + (geo == GEO_AFFINE ? 0 : size_t(9) * fpb * M * M * sizeof(T));
+}
+
+// trace / face-residual addressing: [cell][lf][qty][M^2]
+template <int M>
+__device__ __forceinline__ int64_t tr_idx(int64_t cell, int lf, int qty, int qf) {
+  return ((cell * 6 + lf) * 2 + qty) * (M * M) + qf;
+}
+
+template <int M, typename T, int GEO, bool KAPPA>
+__global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__restrict__ traces,
+                                              T *__restrict__ fres, int fpb, int64_t st) {
+  constexpr int M2 = M * M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &tb = *reinterpret_cast<SmemTables<1, M, T> *>(smem_raw);
+  T *SM = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(SmemTables<1, M, T>)));
+  const int tid = threadIdx.x, nt = blockDim.x;
+  traces += blockIdx.y * st;
+  fres += blockIdx.y * st;
+  const int64_t f0 = (int64_t)blockIdx.x * fpb;
+  const int nf = (int)min((int64_t)fpb, a.nface - f0);
+  // tables: only the weights are needed here (dcol on curved faces)
+  for (int i = tid; i < M * M; i += nt) tb.dcol[i] = a.tab->dcol[i];
+  for (int i = tid; i < M; i += nt) tb.w[i] = a.tab->w[i];
+  __syncthreads();
+  const T sc = a.sc, ss = a.ss, half = T(0.5);
+  if (GEO == GEO_AFFINE) {
+    for (int i = tid; i < nf * M2; i += nt) {
+      const int lfc = i / M2, qf = i - lfc * M2;
+      const FaceId F = decode_face(a, f0 + lfc);
+      const int ax = F.axis;
+      const int qs = qf % M, qt = qf / M;
+      const T W = tb.w[qs] * tb.w[qt];
+      const T bW = W * a.face_b[ax], pw = W * a.face_pw[ax];
+      if (F.cm >= 0 && F.cp >= 0) {
+        const T um = traces[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)];
+        const T dm = traces[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)];
+        const T up = traces[tr_idx<M>(F.cp, 2 * ax, 0, qf)];
+        const T dp = traces[tr_idx<M>(F.cp, 2 * ax, 1, qf)];
+        T km = T(1), kp = T(1);
+        if (KAPPA) {
+          km = a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf];
+          kp = a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf];
+        }
+        const T J = um - up;
+        const T flux = half * bW * fma(km, dm, kp * dp);
+        const T Rv = fma(sc, flux, pw * J);
+        const T sJ = ss * half * J * bW;
+        fres[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)] = Rv;
+        fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = KAPPA ? sJ * km : sJ;
+        fres[tr_idx<M>(F.cp, 2 * ax, 0, qf)] = -Rv;
+        fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = KAPPA ? sJ * kp : sJ;
+      } else {
+        const int side = F.cm >= 0 ? 1 : 0;
+        const int64_t cb = side ? F.cm : F.cp;
+        const int lf = 2 * ax + side;
+        T Rv = T(0), Rn = T(0);
+        if ((a.dmask >> lf) & 1u) {
+          const T u = traces[tr_idx<M>(cb, lf, 0, qf)];
+          const T d = traces[tr_idx<M>(cb, lf, 1, qf)];
+          const T kb = KAPPA ? a.kappa_face[(cb * 6 + lf) * M2 + qf] : T(1);
+          const T b = side ? bW : -bW;  // outward normal
+          Rv = fma(sc * kb, b * d, pw * u);
+          Rn = ss * kb * u * b;
+        }
+        fres[tr_idx<M>(cb, lf, 0, qf)] = Rv;
+        fres[tr_idx<M>(cb, lf, 1, qf)] = Rn;
+      }
+    }
+    return;
+  }
+  // curved faces (stored geometry): stage traces, pointwise terms, tangential back-projection
+  T *sU = SM;                   // [face][4][M2]: u-, dn-, u+, dn+
+  T *sR = SM + 4 * fpb * M2;    // [face][5][M2]: Rv, Rt1-, Rt2-, Rt1+, Rt2+
+  for (int i = tid; i < nf * 4 * M2; i += nt) {
+    const int lfc = i / (4 * M2), r = i - lfc * (4 * M2);
+    const int slot = r / M2, qf = r - slot * M2;
+    const FaceId F = decode_face(a, f0 + lfc);
+    const int ax = F.axis;
+    T v = T(0);
+    if (slot < 2) {
+      if (F.cm >= 0) v = traces[tr_idx<M>(F.cm, 2 * ax + 1, slot, qf)];
+      else v = traces[tr_idx<M>(F.cp, 2 * ax, slot, qf)];  // boundary face at the lower end
+    } else if (F.cm >= 0 && F.cp >= 0) {
+      v = traces[tr_idx<M>(F.cp, 2 * ax, slot - 2, qf)];
+    }
+    sU[i] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < nf * M2; i += nt) {
+    const int lfc = i / M2, qf = i - lfc * M2;
+    const int64_t f = f0 + lfc;
+    const FaceId F = decode_face(a, f);
+    const int ax = F.axis, t1 = F.t1, t2 = F.t2;
+    const int qs = qf % M, qt = qf / M;
+    const T *gf = a.gface + f * (7 * M2) + qf;
+    const T *u0 = sU + lfc * 4 * M2;
+    T *R = sR + lfc * 5 * M2;
+    // tangential reference derivatives of side "-" (slot 0) or the single boundary side
+    T ds1 = tb.dcol[qs * M] * u0[qt * M], ds2 = tb.dcol[qt * M] * u0[qs];
+#pragma unroll
+    for (int r = 1; r < M; ++r) {
+      ds1 = fma(tb.dcol[qs * M + r], u0[r + qt * M], ds1);
+      ds2 = fma(tb.dcol[qt * M + r], u0[qs + r * M], ds2);
+    }
+    const T bm[3] = {gf[0], gf[M2], gf[2 * M2]};
+    const T gm = fma(bm[ax], u0[M2 + qf], fma(bm[t1], ds1, bm[t2] * ds2));
+    const T pw = gf[6 * M2];
+    if (F.cm >= 0 && F.cp >= 0) {
+      const T *u1 = u0 + 2 * M2;
+      T es1 = tb.dcol[qs * M] * u1[qt * M], es2 = tb.dcol[qt * M] * u1[qs];
+#pragma unroll
+      for (int r = 1; r < M; ++r) {
+        es1 = fma(tb.dcol[qs * M + r], u1[r + qt * M], es1);
+        es2 = fma(tb.dcol[qt * M + r], u1[qs + r * M], es2);
+      }
+      const T bp[3] = {gf[3 * M2], gf[4 * M2], gf[5 * M2]};
+      const T gp = fma(bp[ax], u1[M2 + qf], fma(bp[t1], es1, bp[t2] * es2));
+      T km = T(1), kp = T(1);
+      if (KAPPA) {
+        km = a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf];
+        kp = a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf];
+      }
+      const T J = u0[qf] - u1[qf];
+      const T flux = half * fma(km, gm, kp * gp);
+      const T Rv = fma(sc, flux, pw * J);
+      const T sJ = ss * half * J;
+      const T sm = KAPPA ? sJ * km : sJ, sp = KAPPA ? sJ * kp : sJ;
+      R[qf] = Rv;
+      R[M2 + qf] = sm * bm[t1];
+      R[2 * M2 + qf] = sm * bm[t2];
+      R[3 * M2 + qf] = sp * bp[t1];
+      R[4 * M2 + qf] = sp * bp[t2];
+      fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = sm * bm[ax];
+      fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = sp * bp[ax];
+    } else {
+      const int side = F.cm >= 0 ? 1 : 0;
+      const int64_t cb = side ? F.cm : F.cp;
+      const int lf = 2 * ax + side;
+      T Rv = T(0), s1 = T(0), s2 = T(0), sn = T(0);
+      if ((a.dmask >> lf) & 1u) {
+        const T kb = KAPPA ? a.kappa_face[(cb * 6 + lf) * M2 + qf] : T(1);
+        const T u = u0[qf];
+        Rv = fma(sc * kb, gm, pw * u);
+        const T su = ss * kb * u;
+        s1 = su * bm[t1];
+        s2 = su * bm[t2];
+        sn = su * bm[ax];
+      }
+      R[qf] = Rv;
+      R[M2 + qf] = s1;
+      R[2 * M2 + qf] = s2;
+      fres[tr_idx<M>(cb, lf, 1, qf)] = sn;
+    }
+  }
+  __syncthreads();
+  // value residual of each side: Rv + dcol^T (tangential terms)
+  for (int i = tid; i < nf * M2; i += nt) {
+    const int lfc = i / M2, qf = i - lfc * M2;
+    const FaceId F = decode_face(a, f0 + lfc);
+    const int ax = F.axis;
+    const int qs = qf % M, qt = qf / M;
+    const T *R = sR + lfc * 5 * M2;
+    T vm = R[qf], vp = -R[qf];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      vm = fma(tb.dcol[r * M + qs], R[M2 + r + qt * M], vm);
+      vm = fma(tb.dcol[r * M + qt], R[2 * M2 + qs + r * M], vm);
+    }
+    if (F.cm >= 0 && F.cp >= 0) {
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        vp = fma(tb.dcol[r * M + qs], R[3 * M2 + r + qt * M], vp);
+        vp = fma(tb.dcol[r * M + qt], R[4 * M2 + qs + r * M], vp);
+      }
+      fres[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)] = vm;
+      fres[tr_idx<M>(F.cp, 2 * ax, 0, qf)] = vp;
+    } else {
+      const int side = F.cm >= 0 ? 1 : 0;
+      fres[tr_idx<M>(side ? F.cm : F.cp, 2 * ax + side, 0, qf)] = vm;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_back
+// ------------------------------------------------------------------------------------
+template <int P, int M, typename T>
+__host__ __device__ constexpr size_t back_smem_bytes(int cpb) {
+  return align16<T>(sizeof(SmemTables<P, M, T>)) + size_t(cpb) * (2 * M * M * M + 12 * M * M) * sizeof(T);
+}
+
+template <int P, int M, typename T>
+__global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__restrict__ rvol,
+                                              const T *__restrict__ fres, T *__restrict__ y, int cpb,
+                                              int64_t sy, int64_t sr, int64_t st) {
+  constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto &tb = *reinterpret_cast<SmemTables<P, M, T> *>(smem_raw);
+  T *S0 = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(SmemTables<P, M, T>)));
+  T *S1 = S0 + cpb * M3;
+  T *SF = S1 + cpb * M3;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  y += blockIdx.y * sy;
+  rvol += blockIdx.y * sr;
+  fres += blockIdx.y * st;
+  const int64_t c0 = (int64_t)blockIdx.x * cpb;
+  const int nc = (int)min((int64_t)cpb, a.ncell - c0);
+  load_tables(tb, a.tab);
+  for (int i = tid; i < nc * M3; i += nt) S0[i] = rvol[c0 * M3 + i];
+  for (int i = tid; i < nc * 12 * M2; i += nt) SF[i] = fres[c0 * 12 * M2 + i];
+  __syncthreads();
+  for (int i = tid; i < nc * M3; i += nt) {
+    const int c = i / M3, q = i - c * M3;
+    const int qv[3] = {q % M, (q / M) % M, q / M2};
+    const T *sf = SF + c * 12 * M2;
+    T acc = S0[i];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int qa = qv[ax];
+      const int qf = (ax == 0) ? qv[1] + M * qv[2] : (ax == 1 ? qv[0] + M * qv[2] : qv[0] + M * qv[1]);
+      const T *lo = sf + (2 * ax) * 2 * M2, *hi = sf + (2 * ax + 1) * 2 * M2;
+      acc = fma(tb.e0[qa], lo[qf], acc);
+      acc = fma(tb.d0[qa], lo[M2 + qf], acc);
+      acc = fma(tb.e1[qa], hi[qf], acc);
+      acc = fma(tb.d1[qa], hi[M2 + qf], acc);
+    }
+    S1[i] = acc;
+  }
+  __syncthreads();
+  // transposed interpolation, axis 0: [c][q2][q1][q0] -> [c][q2][q1][j0]
+  for (int i = tid; i < nc * M2 * P; i += nt) {
+    const int c = i / (M2 * P), r = i - c * (M2 * P);
+    const int j0 = r % P, q12 = r / P;
+    const T *src = S1 + c * M3 + q12 * M;
+    T acc = tb.interp[j0] * src[0];
+#pragma unroll
+    for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j0], src[q], acc);
+    S0[i] = acc;
+  }
+  __syncthreads();
+  // axis 1: [c][q2][q1][j0] -> [c][q2][j1][j0]
+  for (int i = tid; i < nc * M * P * P; i += nt) {
+    const int c = i / (M * P * P), r = i - c * (M * P * P);
+    const int j0 = r % P, j1 = (r / P) % P, q2 = r / (P * P);
+    const T *src = S0 + c * (M2 * P) + q2 * (M * P) + j0;
+    T acc = tb.interp[j1] * src[0];
+#pragma unroll
+    for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j1], src[q * P], acc);
+    S1[i] = acc;
+  }
+  __syncthreads();
+  // axis 2: [c][q2][j1][j0] -> y [c][j2][j1][j0]
+  {
+    T *yb = y + c0 * P3;
+    for (int i = tid; i < nc * P3; i += nt) {
+      const int c = i / P3, r = i - c * P3;
+      const int j01 = r % (P * P), j2 = r / (P * P);
+      const T *src = S1 + c * (M * P * P) + j01;
+      T acc = tb.interp[j2] * src[0];
+#pragma unroll
+      for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j2], src[q * P * P], acc);
+      yb[i] = acc;
+    }
+  }
+}
+
+}  // namespace dgk

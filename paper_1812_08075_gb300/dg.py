@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libdg's C ABI (include/dg.h).
+
+Functions named like the C entry points marshal arguments and raise ``DGError`` on a
+non-zero status; every step of an apply runs in the library's CUDA kernels. ``Mesh``
+and ``Operator`` wrap the handles for PyTorch callers (device memory and streams come
+from torch). Importing this module does not build or load anything; the first call
+loads ``_build/libdg_sm103a.so`` and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdg_sm103a.so")
+
+DG_OK, DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED, DG_ERR_TIMEOUT = range(7)
+DG_PEN_CONFIG, DG_PEN_PAPER = 0, 1
+DG_SCALAR, DG_STOKES = 0, 1
+DG_FP64, DG_FP32 = 0, 1
+DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
+
+EXPORTED = [
+    "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
+    "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
+    "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
+]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+class dg_penalty(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("alpha", ctypes.c_double)]
+
+
+class dg_coefficients(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_int32), ("precision", ctypes.c_int32), ("dirichlet_mask", ctypes.c_int32),
+                ("max_rhs", ctypes.c_int32), ("geometry", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("c", ctypes.c_double), ("mu", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+class dg_stats(ctypes.Structure):
+    _fields_ = [("ndofs", ctypes.c_int64), ("ncell", ctypes.c_int64), ("nface", ctypes.c_int64),
+                ("flops", ctypes.c_double * 3), ("bytes", ctypes.c_double * 3), ("dofs_bytes", ctypes.c_double),
+                ("cells_per_block", ctypes.c_int32), ("faces_per_block", ctypes.c_int32),
+                ("threads_cell", ctypes.c_int32), ("threads_face", ctypes.c_int32),
+                ("geometry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libdg (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdg is not built ({LIB_PATH} missing); run paper_1812_08075_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        L.dg_status_string.restype = ctypes.c_char_p
+        L.dg_status_string.argtypes = [i32]
+        L.dg_get_last_error.restype = i32
+        L.dg_mesh_create.argtypes = [i32, i32, i32, vp, ctypes.POINTER(vp)]
+        L.dg_mesh_destroy.argtypes = [vp]
+        L.dg_operator_create.argtypes = [vp, i32, i32, ctypes.POINTER(dg_penalty), ctypes.POINTER(dg_coefficients),
+                                         ctypes.POINTER(vp)]
+        L.dg_operator_destroy.argtypes = [vp]
+        L.dg_operator_ndofs.argtypes = [vp, ctypes.POINTER(i64)]
+        L.dg_operator_stats.argtypes = [vp, ctypes.POINTER(dg_stats)]
+        L.dg_operator_set_kappa.argtypes = [vp, vp, vp]
+        L.dg_apply.argtypes = [vp, vp, vp, i32, vp]
+        L.dg_apply_host.argtypes = [vp, vp, vp, i32, vp]
+        L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.dg_operator_profile.argtypes = [vp, i32]
+        L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
+        for name in EXPORTED:
+            if name not in ("dg_status_string",):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != DG_OK:
+        raise DGError(status, where)
+
+
+def status_string(status: int) -> str:
+    return lib().dg_status_string(status).decode()
+
+
+# ------------------------------------------------------------ C-ABI named wrappers
+
+def dg_mesh_create(nx: int, ny: int, nz: int, vertices: Optional[np.ndarray] = None) -> int:
+    h = ctypes.c_void_p()
+    v = None
+    if vertices is not None:
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        if v.shape != ((nx + 1) * (ny + 1) * (nz + 1), 3):
+            raise ValueError("vertices must have shape [(nx+1)(ny+1)(nz+1), 3]")
+    _check(lib().dg_mesh_create(nx, ny, nz, None if v is None else v.ctypes.data, ctypes.byref(h)), "dg_mesh_create")
+    return h.value
+
+
+def dg_mesh_destroy(mesh: int):
+    lib().dg_mesh_destroy(mesh)
+
+
+def dg_operator_create(mesh: int, degree: int, quad_points_1d: int, penalty: dg_penalty,
+                       coef: dg_coefficients) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().dg_operator_create(mesh, degree, quad_points_1d, ctypes.byref(penalty), ctypes.byref(coef),
+                                    ctypes.byref(h)), "dg_operator_create")
+    return h.value
+
+
+def dg_operator_destroy(op: int):
+    lib().dg_operator_destroy(op)
+
+
+def dg_operator_ndofs(op: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().dg_operator_ndofs(op, ctypes.byref(n)), "dg_operator_ndofs")
+    return n.value
+
+
+def dg_operator_stats(op: int) -> dg_stats:
+    s = dg_stats()
+    _check(lib().dg_operator_stats(op, ctypes.byref(s)), "dg_operator_stats")
+    return s
+
+
+def dg_operator_set_kappa(op: int, kappa_vol_ptr: Optional[int], kappa_face_ptr: Optional[int]):
+    _check(lib().dg_operator_set_kappa(op, kappa_vol_ptr, kappa_face_ptr), "dg_operator_set_kappa")
+
+
+def dg_apply(op: int, x_ptr: int, y_ptr: int, nrhs: int, stream: Optional[int]):
+    _check(lib().dg_apply(op, x_ptr, y_ptr, nrhs, stream), "dg_apply")
+
+
+def dg_apply_host(op: int, x_ptr: int, y_ptr: int, nrhs: int, stream: Optional[int]):
+    _check(lib().dg_apply_host(op, x_ptr, y_ptr, nrhs, stream), "dg_apply_host")
+
+
+def dg_apply_adjoint(op: int, r_ptr: int, x_ptr: Optional[int], y_ptr: int, dk_vol_ptr: Optional[int],
+                     dk_face_ptr: Optional[int], stream: Optional[int]):
+    _check(lib().dg_apply_adjoint(op, r_ptr, x_ptr, y_ptr, dk_vol_ptr, dk_face_ptr, stream), "dg_apply_adjoint")
+
+
+def dg_operator_profile(op: int, enable: bool):
+    _check(lib().dg_operator_profile(op, int(enable)), "dg_operator_profile")
+
+
+def dg_operator_kernel_times(op: int):
+    """(milliseconds per kernel summed over the recorded applies, number of applies)."""
+    ms = (ctypes.c_double * 3)()
+    n = ctypes.c_int64()
+    _check(lib().dg_operator_kernel_times(op, ctypes.byref(ms), ctypes.byref(n)), "dg_operator_kernel_times")
+    return list(ms), n.value
+
+
+def dg_reference_tables(degree: int, m: int = 0):
+    m = m or degree + 1
+    out = {k: np.zeros(n) for k, n in (("gauss_nodes", m), ("gauss_weights", m), ("gll_nodes", degree + 1),
+                                       ("interp", m * (degree + 1)), ("dcol", m * m), ("end_val", 2 * m),
+                                       ("end_der", 2 * m))}
+    _check(lib().dg_reference_tables(degree, m, *(out[k].ctypes.data for k in
+                                                  ("gauss_nodes", "gauss_weights", "gll_nodes", "interp", "dcol",
+                                                   "end_val", "end_der"))), "dg_reference_tables")
+    out["interp"] = out["interp"].reshape(m, degree + 1)
+    out["dcol"] = out["dcol"].reshape(m, m)
+    out["end_val"] = out["end_val"].reshape(2, m)
+    out["end_der"] = out["end_der"].reshape(2, m)
+    return out
+
+
+# ------------------------------------------------------------ torch-facing wrappers
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
+class Mesh:
+    """Structured nx x ny x nz hexahedral mesh (vertices None: affine unit cube)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, vertices: Optional[np.ndarray] = None):
+        self.shape = (nx, ny, nz)
+        self.handle = dg_mesh_create(nx, ny, nz, vertices)
+
+    @property
+    def ncell(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            dg_mesh_destroy(h)
+            self.handle = None
+
+
+class Operator:
+    """y = A x of the SIPG operator on a Mesh (see dg_operator_create)."""
+
+    def __init__(self, mesh: Mesh, degree: int, *, quad_points: int = 0, c: float = 1.0, mu: float = 1.0,
+                 theta: float = -1.0, penalty_mode: int = DG_PEN_CONFIG, penalty_alpha: float = 2.0,
+                 dirichlet_mask: int = 0b111111, precision: int = DG_FP64, max_rhs: int = 1,
+                 problem: int = DG_SCALAR, geometry: int = DG_GEOM_AUTO):
+        import torch
+        self.mesh = mesh
+        self.degree = degree
+        self.precision = precision
+        self.dtype = torch.float64 if precision == DG_FP64 else torch.float32
+        self.max_rhs = max_rhs
+        pen = dg_penalty(penalty_mode, 0, penalty_alpha)
+        co = dg_coefficients(problem, precision, dirichlet_mask, max_rhs, geometry, 0, c, mu, theta)
+        self.handle = dg_operator_create(mesh.handle, degree, quad_points, pen, co)
+        self.ndofs = dg_operator_ndofs(self.handle)
+        self._kappa = (None, None)
+
+    def stats(self) -> dg_stats:
+        return dg_operator_stats(self.handle)
+
+    def set_kappa(self, kappa_vol=None, kappa_face=None):
+        """Per-quadrature-point kappa as device tensors of the operator's dtype (None = 1)."""
+        pv = None if kappa_vol is None else _dev_ptr(kappa_vol, self.dtype, "kappa_vol")
+        pf = None if kappa_face is None else _dev_ptr(kappa_face, self.dtype, "kappa_face")
+        dg_operator_set_kappa(self.handle, pv, pf)
+        self._kappa = (kappa_vol, kappa_face)  # keep alive while the operator reads them
+
+    def apply(self, x, y=None, stream=None):
+        """y = A x for x of shape [ndofs] or [nrhs, ndofs] (CUDA tensors)."""
+        import torch
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if x.numel() != nrhs * self.ndofs:
+            raise ValueError("x has the wrong size")
+        if y is None:
+            y = torch.empty_like(x)
+        dg_apply(self.handle, _dev_ptr(x, self.dtype, "x"), _dev_ptr(y, self.dtype, "y"), nrhs, _stream_ptr(stream))
+        return y
+
+    def apply_host(self, x, y, stream=None):
+        """y = A x through host buffers (numpy arrays or CPU tensors, ideally pinned)."""
+        nrhs = 1 if x.ndim == 1 else x.shape[0]
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        yp = y.ctypes.data if isinstance(y, np.ndarray) else y.data_ptr()
+        dg_apply_host(self.handle, xp, yp, nrhs, _stream_ptr(stream))
+        return y
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            dg_operator_destroy(h)
+            self.handle = None

@@ -1,0 +1,146 @@
+"""GPU parity of the scalar SIPG apply (C ABI, FP64 and FP32) against the CPU oracle.
+
+Error metric: max_i |y_i - y_ref,i| / max_i |y_ref,i|. FP64 must agree to 1e-12, FP32
+(storage and accumulation) to 1e-5, on identical seeded inputs. Small cases span several
+thread blocks with a ragged last block; the full 64^3 trilinear configuration is checked
+on sampled cells that the oracle evaluates one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_08075_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1812_08075_gb300 import build as libbuild, dg  # noqa: E402
+
+libbuild.build()
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def relerr(y, ref):
+    return float(np.abs(y - ref).max() / np.abs(ref).max())
+
+
+def run_case(n, k, geom="affine", theta=-1.0, c=1.0, mask=0b111111, pen_mode=0, alpha=2.0, kappa=False,
+             precision=dg.DG_FP64, nrhs=1, seed=0):
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    mesh = dg.Mesh(*n, verts)
+    op = dg.Operator(mesh, k, c=c, theta=theta, dirichlet_mask=mask, penalty_mode=pen_mode, penalty_alpha=alpha,
+                     precision=precision, max_rhs=nrhs)
+    ncell = mesh.ncell
+    orc = oracle.Problem(*n, k, vertices=verts, c=c, theta=theta, dirichlet_mask=mask, pen_mode=pen_mode,
+                         pen_alpha=alpha)
+    if kappa:
+        kv, kf = wl.lognormal_kappa(ncell, k + 1, seed=2)
+        orc.kappa_vol, orc.kappa_face = kv, kf
+        tkv = torch.from_numpy(kv).to("cuda", op.dtype)
+        tkf = torch.from_numpy(kf).to("cuda", op.dtype)
+        op.set_kappa(tkv, tkf)
+    xs = np.stack([wl.uniform_vector(op.ndofs, seed + r) for r in range(nrhs)])
+    xd = torch.from_numpy(xs).to("cuda", op.dtype)
+    y = op.apply(xd if nrhs > 1 else xd[0]).double().cpu().numpy().reshape(nrhs, -1)
+    torch.cuda.synchronize()
+    refs = np.stack([orc.apply(xs[r]) for r in range(nrhs)])
+    return max(relerr(y[r], refs[r]) for r in range(nrhs))
+
+
+# config 1: 4^3 affine cells, Q2, c = 1, SIPG, penalty 2k(k+1)/h, Dirichlet, x ~ U[-1,1] seed 0
+def test_config1_affine_q2_fp64():
+    assert run_case((4, 4, 4), 2) <= TOL64
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_degrees_ragged_mesh_fp64(k, geom):
+    # 5 x 3 x 4 cells: several blocks per launch and a ragged last block for every degree
+    assert run_case((5, 3, 4), k, geom) <= TOL64
+
+
+@pytest.mark.parametrize("theta,mask,pen_mode,c", [(1.0, 0b101101, 0, 0.5), (0.0, 0b010110, 1, 0.0),
+                                                   (-1.0, 0, 1, 2.0)])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_theta_masks_penalty_modes(theta, mask, pen_mode, c, geom):
+    assert run_case((3, 4, 2), 2, geom, theta=theta, c=c, mask=mask, pen_mode=pen_mode, alpha=3.0) <= TOL64
+
+
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+@pytest.mark.parametrize("k", [2, 3])
+def test_pointwise_kappa(geom, k):
+    assert run_case((4, 3, 3), k, geom, kappa=True) <= TOL64
+
+
+def test_single_cell_and_thin_meshes():
+    assert run_case((1, 1, 1), 3, "trilinear") <= TOL64
+    assert run_case((7, 1, 1), 2) <= TOL64
+    assert run_case((1, 2, 9), 4, "trilinear") <= TOL64
+
+
+def test_multiple_rhs_fp64():
+    assert run_case((3, 3, 4), 3, "trilinear", nrhs=5) <= TOL64
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_fp32_against_fp64_oracle(k, geom):
+    err = run_case((4, 3, 5), k, geom, precision=dg.DG_FP32, nrhs=2)
+    print(f"FP32 Q{k} {geom}: rel err {err:.2e}")
+    assert err <= TOL32
+
+
+def test_apply_host_matches_device():
+    n, k = (4, 4, 3), 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=2)
+    x = np.stack([wl.uniform_vector(op.ndofs, s) for s in (0, 1)])
+    yh = np.zeros_like(x)
+    op.apply_host(x, yh)
+    yd = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.array_equal(yh, yd)
+
+
+def test_apply_is_deterministic():
+    n, k = (6, 5, 4), 4
+    op = dg.Operator(dg.Mesh(*n, wl.perturbed_vertices(*n, seed=1)), k)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    y1 = op.apply(x)
+    y2 = op.apply(x)
+    assert torch.equal(y1, y2)
+
+
+def test_argument_errors_on_device():
+    op = dg.Operator(dg.Mesh(2, 2, 2), 2, max_rhs=2)
+    x = torch.zeros(op.ndofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DGError):
+        dg.dg_apply(op.handle, x.data_ptr(), x.data_ptr(), 1, None)  # aliased
+    with pytest.raises(dg.DGError):
+        dg.dg_apply(op.handle, x.data_ptr(), x.data_ptr() + 8, 1, None)  # misaligned
+    with pytest.raises(dg.DGError):
+        dg.dg_apply(op.handle, x.data_ptr(), 0, 1, None)
+    y = torch.empty(3 * op.ndofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DGError):
+        dg.dg_apply(op.handle, y.data_ptr(), y[op.ndofs:].data_ptr(), 3, None)  # nrhs > max_rhs
+    with pytest.raises(TypeError):
+        op.apply(x.float())
+
+
+# config 2 at full size: 64^3 trilinear-perturbed cells, FP64, sampled cells vs the oracle
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_config2_full_size_sampled(k):
+    n = (64, 64, 64)
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k)
+    x = wl.uniform_vector(op.ndofs, 0)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy().reshape(op.mesh.ncell, -1)
+    cells = wl.sample_cells(op.mesh.ncell, 96, seed=7 + k)
+    orc = oracle.Problem(*n, k, vertices=verts)
+    ref = orc.apply_cells(x, cells, nthreads=0)
+    err = float(np.abs(y[cells] - ref).max() / np.abs(ref).max())
+    assert err <= TOL64, err
