@@ -53,10 +53,12 @@ def peaks():
 
 
 def workload_config(k: int):
+    l2 = ("inputs larger than L2 (x 134 MB, stored geometry 1.6 GB at Q3), no flush" if N_CELLS >= 64
+          else "smaller profiling case")
     return {"workload": f"scalar SIPG diffusion-reaction, {N_CELLS}^3 trilinear-perturbed cells (0.1h, seed 1), "
                         f"Q{k}, {k + 1}^3 Gauss points, c=1, penalty 2k(k+1)/h, Dirichlet, FP64 apply",
             "cells": N_CELLS ** 3, "degree": k, "ndofs": N_CELLS ** 3 * (k + 1) ** 3,
-            "l2": "inputs larger than L2 (x 134 MB, stored geometry 1.6 GB at Q3), no flush",
+            "l2": l2,
             "parallelism": "replicas (independent problem per GPU)"}
 
 
@@ -308,7 +310,10 @@ def main():
     ap.add_argument("--sweep", dest="sweep", action="store_true", default=True)
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=64, help="cells per axis (64 is the benchmark workload)")
     args = ap.parse_args()
+    global N_CELLS
+    N_CELLS = args.cells
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
