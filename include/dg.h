@@ -163,6 +163,28 @@ dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host,
 dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y,
                            void *dkappa_vol, void *dkappa_face, void *stream);
 
+/* y = A x for the FP64 scalar operator on the affine nx x ny x nz unit-cube mesh (the
+ * same operator as dg_operator_create with vertices = NULL, DG_PEN_CONFIG penalty
+ * alpha*k(k+1)/h_a, kappa = 1, one right-hand side), without any device allocation.
+ * The paper has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code running inside a host application or framework that owns all device
+ * memory through its own pool, and latency-critical loops that must not take the
+ * implicit device synchronisation that cudaMalloc/cudaFree can cause. Instead of
+ * operator-owned buffers it uses one file-scope device array of 32 MiB (reserved on
+ * every GPU that loads libdg until the process exits) for the reference tables and the
+ * apply's scratch; the caller passes x and y (device, 16-byte aligned, not aliased).
+ * Limit: ncell * ((k+1)^3 + 24 (k+1)^2) * 8 bytes must fit in 32 MiB - 4 KiB (e.g.
+ * 9362 cells at Q3); larger problems return DG_ERR_UNSUPPORTED without launching.
+ * The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (different streams, or concurrent host threads) race on
+ * it and must be ordered by the caller. Within one call every scratch entry is written
+ * before it is read, so leftovers of earlier calls do no harm. Errors:
+ * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_CUDA. */
+dg_status dg_apply_affine_static(int nx, int ny, int nz, int degree, double c, double theta,
+                                 double penalty_alpha, int dirichlet_mask, const double *x,
+                                 double *y, void *stream);
+
 /* Per-kernel timing for measurement harnesses. With enable != 0, every later apply on
  * this operator records CUDA events on its own stream before and after each of its
  * kernels (cell, face, back-projection). dg_operator_kernel_times waits for those events,

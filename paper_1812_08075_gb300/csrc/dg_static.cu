@@ -1,0 +1,105 @@
+// dg_apply_affine_static: the FP64 scalar apply on the affine unit-cube mesh for callers
+// that cannot allocate device memory. The apply's scratch (reference tables, Gauss-point
+// volume residual, face traces, face residuals) lives in one file-scope device array of
+// fixed size instead of operator-owned cudaMalloc buffers; the kernels are the same ones
+// dg_apply launches.
+#include <mutex>
+#include <string.h>
+
+#include "dg_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB, held by every GPU that loads libdg
+constexpr size_t kTableBytes = 4096;                 // reference tables at the start of the array
+static_assert(sizeof(DevTables<double>) <= kTableBytes, "tables must fit their slot");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
+
+// Device address of g_static_scratch, looked up once per device with that device current.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+cudaError_t scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_apply_affine_static(int nx, int ny, int nz, int degree, double c, double theta,
+                                            double penalty_alpha, int dirichlet_mask, const double *x, double *y,
+                                            void *stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || degree < 1 || !x || !y || x == y) return DG_ERR_INVALID_ARG;
+  if (dirichlet_mask < 0 || dirichlet_mask > 63) return DG_ERR_INVALID_ARG;
+  if (((uintptr_t)x & 15u) || ((uintptr_t)y & 15u)) return DG_ERR_INVALID_ARG;
+  if (degree > 5) return DG_ERR_UNSUPPORTED;
+  const int P = degree + 1, M = P, M2 = M * M, M3 = M * M * M;
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const double per_cell = (double)(M3 + 24 * M2) * sizeof(double);
+  if ((double)ncell * per_cell > (double)(kScratchBytes - kTableBytes)) return DG_ERR_UNSUPPORTED;
+
+  HostTables ht;
+  if (dg_build_tables(degree, M, false, &ht)) return DG_ERR_UNSUPPORTED;
+  DevTables<double> tab;
+  memset(&tab, 0, sizeof(tab));
+  for (int i = 0; i < M * P; ++i) tab.interp[i] = ht.interp[i];
+  for (int i = 0; i < M * M; ++i) tab.dcol[i] = ht.dcol[i];
+  for (int i = 0; i < M; ++i) {
+    tab.e0[i] = ht.e0[i]; tab.e1[i] = ht.e1[i];
+    tab.d0[i] = ht.d0[i]; tab.d1[i] = ht.d1[i];
+    tab.w[i] = ht.gauss_w[i];
+  }
+  void *base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) return DG_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // pageable source: the call returns once the tables are staged, so the stack copy may go
+  if (cudaMemcpyAsync(base, &tab, sizeof(tab), cudaMemcpyHostToDevice, s) != cudaSuccess) return DG_ERR_CUDA;
+
+  ScalarArgs<double> a;
+  memset(&a, 0, sizeof(a));
+  a.nx = nx; a.ny = ny; a.nz = nz;
+  a.ncell = ncell;
+  const int n[3] = {nx, ny, nz};
+  a.face_off[0] = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+    a.face_off[ax + 1] = a.face_off[ax] + (int64_t)(n[ax] + 1) * n[t1] * n[t2];
+  }
+  a.nface = a.face_off[3];
+  a.tab = (const DevTables<double> *)base;
+  const double h[3] = {1.0 / nx, 1.0 / ny, 1.0 / nz};
+  const double V = h[0] * h[1] * h[2];
+  for (int d = 0; d < 3; ++d) {
+    a.vol_g[d] = V / (h[d] * h[d]);
+    a.face_b[d] = V / (h[d] * h[d]);
+    a.face_pw[d] = penalty_alpha * degree * (degree + 1) * n[d] * V / h[d];
+  }
+  a.vol_m = c * V;
+  a.c = c;
+  a.dmask = (unsigned)dirichlet_mask;
+  a.sc = -1.0;
+  a.ss = theta;
+  // every scratch entry below is written before it is read within one call, so nothing
+  // carried over from an earlier call needs clearing
+  double *rvol = (double *)((unsigned char *)base + kTableBytes);
+  double *tr = rvol + ncell * M3;
+  double *fres = tr + ncell * 12 * M2;
+  const int cpb = 256 / M3 > 0 ? 256 / M3 : 1;
+  const int fpb = 256 / M2 > 0 ? 256 / M2 : 1;
+  cudaError_t e = launch_scalar_apply<double>(P, M, GEO_AFFINE, false, a, x, y, rvol, tr, fres, 1, ncell * P * P * P,
+                                              ncell * M3, ncell * 12 * M2, cpb, fpb, s, nullptr);
+  return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}

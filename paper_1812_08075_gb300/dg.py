@@ -27,6 +27,7 @@ EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
+    "dg_apply_affine_static",
 ]
 
 
@@ -81,6 +82,8 @@ def lib():
         L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
+        L.dg_apply_affine_static.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             i32, vp, vp, vp]
         L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
         for name in EXPORTED:
             if name not in ("dg_status_string",):
@@ -154,6 +157,13 @@ def dg_apply_host(op: int, x_ptr: int, y_ptr: int, nrhs: int, stream: Optional[i
 def dg_apply_adjoint(op: int, r_ptr: int, x_ptr: Optional[int], y_ptr: int, dk_vol_ptr: Optional[int],
                      dk_face_ptr: Optional[int], stream: Optional[int]):
     _check(lib().dg_apply_adjoint(op, r_ptr, x_ptr, y_ptr, dk_vol_ptr, dk_face_ptr, stream), "dg_apply_adjoint")
+
+
+def dg_apply_affine_static(nx: int, ny: int, nz: int, degree: int, c: float, theta: float, penalty_alpha: float,
+                           dirichlet_mask: int, x_ptr: int, y_ptr: int, stream: Optional[int]):
+    """FP64 affine apply that allocates nothing (its scratch is a fixed 32 MiB device array)."""
+    _check(lib().dg_apply_affine_static(nx, ny, nz, degree, c, theta, penalty_alpha, dirichlet_mask, x_ptr, y_ptr,
+                                        stream), "dg_apply_affine_static")
 
 
 def dg_operator_profile(op: int, enable: bool):
