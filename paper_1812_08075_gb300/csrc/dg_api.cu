@@ -51,6 +51,7 @@ struct dg_operator {
   void *d_gvol = nullptr, *d_gface = nullptr;
   void *d_rvol = nullptr, *d_tr = nullptr, *d_fres = nullptr;
   void *d_xh = nullptr, *d_yh = nullptr;  // staging for dg_apply_host
+  void *d_tr2 = nullptr;                  // traces of x in the adjoint (allocated on first use)
   const void *kappa_vol = nullptr, *kappa_face = nullptr;
   int cpb = 1, fpb = 1;
   double gamma_axis[3];
@@ -111,7 +112,7 @@ dg_status dg_mesh_destroy(dg_mesh *mesh) {
 static void free_op(dg_operator *o) {
   if (!o) return;
   void *ptrs[] = {o->d_tab, o->d_verts, o->d_gamma, o->d_cellvol, o->d_gvol, o->d_gface,
-                  o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh};
+                  o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh, o->d_tr2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
@@ -128,7 +129,10 @@ static void fill_devtables(const HostTables &h, DevTables<T> &d) {
     d.e0[i] = (T)h.e0[i]; d.e1[i] = (T)h.e1[i];
     d.d0[i] = (T)h.d0[i]; d.d1[i] = (T)h.d1[i];
     d.w[i] = (T)h.gauss_w[i];
+    d.s[i] = (T)h.gauss_s[i];
   }
+  for (int q = 0; q < h.m; ++q)
+    for (int j = 0; j < h.pp; ++j) d.interp_p[q * h.pp + j] = (T)h.interp_p[q * h.pp + j];
 }
 
 template <typename T>
@@ -146,6 +150,7 @@ static ScalarArgs<T> scalar_args(const dg_operator *o, bool transpose) {
     a.vol_g[d] = (T)(V / (h[d] * h[d]));
     a.face_b[d] = (T)(V / (h[d] * h[d]));
     a.face_pw[d] = (T)(o->gamma_axis[d] * V / h[d]);
+    a.face_area[d] = (T)(V / h[d]);
   }
   a.vol_m = (T)(o->c * V);
   a.gvol = (const T *)o->d_gvol;
@@ -179,7 +184,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   if (m < degree + 1) return fail(DG_ERR_INVALID_ARG);
   if (m != degree + 1) return fail(DG_ERR_UNSUPPORTED);
   if (co->problem != DG_SCALAR && co->problem != DG_STOKES) return fail(DG_ERR_INVALID_ARG);
-  if (co->problem == DG_STOKES) return fail(DG_ERR_UNSUPPORTED);
+  if (co->problem == DG_STOKES && (degree < 2 || !mesh->affine)) return fail(DG_ERR_UNSUPPORTED);
   if (co->precision != DG_FP64 && co->precision != DG_FP32) return fail(DG_ERR_INVALID_ARG);
   if (co->max_rhs < 1 || co->max_rhs > 16) return fail(DG_ERR_INVALID_ARG);
   if (pen->mode != DG_PEN_CONFIG && pen->mode != DG_PEN_PAPER) return fail(DG_ERR_INVALID_ARG);
@@ -208,11 +213,12 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   }
   o->nface = o->face_off[3];
   const int P3 = o->p * o->p * o->p, M2 = m * m, M3 = m * m * m;
-  o->ndofs = o->ncell * P3;
+  const bool stokes = o->problem == DG_STOKES;
+  o->ndofs = stokes ? o->ncell * (3 * P3 + degree * degree * degree) : o->ncell * P3;
   for (int a = 0; a < 3; ++a)
     o->gamma_axis[a] = pen->mode == DG_PEN_CONFIG ? pen->alpha * degree * (degree + 1) * n[a]
                                                   : pen->alpha * degree * (degree + 2) * n[a];
-  if (dg_build_tables(degree, m, false, &o->ht)) { free_op(o); return fail(DG_ERR_UNSUPPORTED); }
+  if (dg_build_tables(degree, m, stokes, &o->ht)) { free_op(o); return fail(DG_ERR_UNSUPPORTED); }
   default_blocking(o);
   const size_t es = o->precision == DG_FP64 ? sizeof(double) : sizeof(float);
 
@@ -259,9 +265,10 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
     if (e != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
   }
   const size_t R = (size_t)o->max_rhs;
-  ALLOC(o->d_rvol, R * o->ncell * M3 * es);
-  ALLOC(o->d_tr, R * o->ncell * 12 * M2 * es);
-  ALLOC(o->d_fres, R * o->ncell * 12 * M2 * es);
+  const size_t nrv = stokes ? 4 : 1, ntr = stokes ? 42 : 12;
+  ALLOC(o->d_rvol, R * o->ncell * nrv * M3 * es);
+  ALLOC(o->d_tr, R * o->ncell * ntr * M2 * es);
+  ALLOC(o->d_fres, R * o->ncell * ntr * M2 * es);
 #undef ALLOC
   *out = o;
   return DG_OK;
@@ -295,8 +302,11 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   out->ncell = op->ncell;
   out->nface = op->nface;
   const int es = op->precision == DG_FP64 ? 8 : 4;
-  scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, out->flops,
-                    out->bytes, es);
+  if (op->problem == DG_STOKES)
+    stokes_work_model(op->p, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
+  else
+    scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, out->flops,
+                      out->bytes, es);
   out->dofs_bytes = 2.0 * es * (double)op->ndofs;
   out->cells_per_block = op->cpb;
   out->faces_per_block = op->fpb;
@@ -325,9 +335,22 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   dg_operator *op = const_cast<dg_operator *>(op_c);
   const cudaEvent_t *ev = next_events(op);
   const int M2 = op->m * op->m, M3 = op->m * op->m * op->m;
+  cudaError_t e;
+  if (op->problem == DG_STOKES) {
+    const int64_t sdof = op->ndofs, srv = op->ncell * 4 * M3, str = op->ncell * 42 * M2;
+    if (op->precision == DG_FP64)
+      e = launch_stokes_apply<double>(op->p, scalar_args<double>(op, transpose), op->mu, (const double *)x,
+                                      (double *)y, (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_fres,
+                                      nrhs, sdof, srv, str, op->cpb, op->fpb, s, ev);
+    else
+      e = launch_stokes_apply<float>(op->p, scalar_args<float>(op, transpose), (float)op->mu, (const float *)x,
+                                     (float *)y, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres, nrhs,
+                                     sdof, srv, str, op->cpb, op->fpb, s, ev);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+    return DG_OK;
+  }
   const int64_t sdof = op->ndofs, srv = op->ncell * M3, str = op->ncell * 12 * M2;
   const bool kap = op->kappa_vol != nullptr;
-  cudaError_t e;
   if (op->precision == DG_FP64)
     e = launch_scalar_apply<double>(op->p, op->m, op->geo, kap, scalar_args<double>(op, transpose), (const double *)x,
                                     (double *)y, (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_fres, nrhs,
@@ -371,11 +394,30 @@ dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_hos
   return DG_OK;
 }
 
-dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y, void *dkappa_vol,
+dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x, void *y, void *dkappa_vol,
                            void *dkappa_face, void *stream) {
-  if (!op || !r || !y) return fail(DG_ERR_INVALID_ARG);
-  (void)x; (void)dkappa_vol; (void)dkappa_face; (void)stream;
-  return fail(DG_ERR_UNSUPPORTED);
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !r || !y || r == y || (x && x == y)) return fail(DG_ERR_INVALID_ARG);
+  if (!aligned16(r) || !aligned16(y) || (x && !aligned16(x))) return fail(DG_ERR_INVALID_ARG);
+  if ((dkappa_vol == nullptr) != (dkappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
+  if (dkappa_vol && (!x || !aligned16(dkappa_vol) || !aligned16(dkappa_face))) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR || op->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED);
+  const int M2 = op->m * op->m;
+  if (dkappa_vol && !op->d_tr2) {
+    if (cudaMalloc(&op->d_tr2, (size_t)op->ncell * 12 * M2 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DG_ERR_OOM);
+    }
+  }
+  const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
+  const cudaEvent_t *ev = next_events(op);
+  cudaError_t e = launch_scalar_adjoint(op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, true), op->theta,
+                                        (const double *)r, dkappa_vol ? (const double *)x : nullptr, (double *)y,
+                                        (double *)dkappa_vol, (double *)dkappa_face, (double *)op->d_rvol,
+                                        (double *)op->d_tr, (double *)op->d_tr2, (double *)op->d_fres, op->cpb,
+                                        op->fpb, (cudaStream_t)stream, ev);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  return DG_OK;
 }
 
 dg_status dg_operator_profile(dg_operator *op, int enable) {
@@ -455,4 +497,22 @@ void scalar_work_model(int P, int M, int geo, bool kappa, int64_t ncell, int64_t
   bytes[1] = es * (ninner * (8.0 * M2 + geo_face + (kappa ? 2.0 * M2 : 0.0)) +
                    (double)nbface * (4.0 * M2 + geo_face + (kappa ? M2 : 0.0)));
   bytes[2] = es * (double)ncell * (M3 + 12.0 * M2 + P3);
+}
+
+void stokes_work_model(int P, int64_t ncell, int64_t nface, int64_t nbface, double flops[3], double bytes[3], int es) {
+  const int M = P, PP = P - 1;
+  const double M2 = M * M, M3 = M * M * M, P3 = P * P * P, PP3 = PP * PP * PP;
+  const double cP = 2.0 * P - 1.0, cPP = 2.0 * PP - 1.0, cM = 2.0 * M - 1.0;
+  double cell = (M * PP * PP + M2 * PP + M3) * cPP;  // pressure to the Gauss points
+  cell += 3.0 * ((P * P * M + P * M2 + M3) * cP + 12.0 * M2 * cM + 3.0 * M3 * cM + 15.0 * M3 + (6.0 * M - 1.0) * M3);
+  cell += 6.0 * M2 * cM + 4.0 * M3;
+  const double ninner = (double)(nface - nbface);
+  const double face = ninner * M2 * (2.0 + 3.0 * 11.0 + 3.0) + (double)nbface * M2 * (3.0 * 9.0 + 5.0);
+  double back = 3.0 * (24.0 * M3 + (M2 * P + M * P * P + P3) * cM) + 12.0 * M3 + (M2 * PP + M * PP * PP + PP3) * cM;
+  flops[0] = cell * (double)ncell;
+  flops[1] = face;
+  flops[2] = back * (double)ncell;
+  bytes[0] = es * (double)ncell * (3 * P3 + PP3 + 4 * M3 + 42 * M2);
+  bytes[1] = es * (ninner * 2.0 * 2.0 * 42 * M2 + (double)nbface * 2.0 * 42 * M2) / 2.0;
+  bytes[2] = es * (double)ncell * (4 * M3 + 42 * M2 + 3 * P3 + PP3);
 }

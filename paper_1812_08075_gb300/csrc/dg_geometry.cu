@@ -8,74 +8,15 @@
 // element) oriented from T- to T+ (outward on boundary faces), b = W J^-1 n_vec for each
 // side, so that n . grad u ds = b . grad_ref u, and pw = gamma_F W |n_vec|.
 #include "dg_scalar_kernels.cuh"
+#include "dg_geo_device.cuh"
 
 namespace {
+
+using namespace dgg;
 
 struct Rule {
   double s[DG_MAXM], w[DG_MAXM];
 };
-
-__device__ void cell_corners(const double *verts, int nx, int ny, int64_t cell, double V[8][3]) {
-  const int cx = (int)(cell % nx);
-  const int cy = (int)((cell / nx) % ny);
-  const int cz = (int)(cell / ((int64_t)nx * ny));
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int64_t v = (cx + (a & 1)) + (int64_t)(nx + 1) * ((cy + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (cz + (a >> 2)));
-#pragma unroll
-    for (int d = 0; d < 3; ++d) V[a][d] = verts[3 * v + d];
-  }
-}
-
-// J[i][d] = d x_i / d xi_d of the trilinear map at (x0, x1, x2).
-__device__ void trilinear_jacobian(const double V[8][3], double x0, double x1, double x2, double J[3][3]) {
-  const double f[3][2] = {{1.0 - x0, x0}, {1.0 - x1, x1}, {1.0 - x2, x2}};
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) J[i][d] = 0.0;
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int b0 = a & 1, b1 = (a >> 1) & 1, b2 = a >> 2;
-    const double s0 = b0 ? 1.0 : -1.0, s1 = b1 ? 1.0 : -1.0, s2 = b2 ? 1.0 : -1.0;
-    const double dN0 = s0 * f[1][b1] * f[2][b2];
-    const double dN1 = f[0][b0] * s1 * f[2][b2];
-    const double dN2 = f[0][b0] * f[1][b1] * s2;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      J[i][0] += dN0 * V[a][i];
-      J[i][1] += dN1 * V[a][i];
-      J[i][2] += dN2 * V[a][i];
-    }
-  }
-}
-
-// Adjugate (transpose of the cofactor matrix) and determinant: J^-1 = adj / det.
-__device__ double adjugate(const double J[3][3], double A[3][3]) {
-  A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-  A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-  A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-  A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-  A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-  A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
-}
-
-// Area vector of the face xi_a = const of a cell at its point with Jacobian J: the cross
-// product of the tangential columns (t1 < t2), oriented along +xi_a (dir = +1) or -xi_a.
-__device__ void area_vector(const double J[3][3], int a, int dir, double n[3]) {
-  const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-  const double u0 = J[0][t1], u1 = J[1][t1], u2 = J[2][t1];
-  const double v0 = J[0][t2], v1 = J[1][t2], v2 = J[2][t2];
-  // (a, t1, t2) is an even permutation of (0,1,2) for a = 0, 2 and odd for a = 1
-  const double sg = (a == 1 ? -1.0 : 1.0) * dir;
-  n[0] = sg * (u1 * v2 - u2 * v1);
-  n[1] = sg * (u2 * v0 - u0 * v2);
-  n[2] = sg * (u0 * v1 - u1 * v0);
-}
 
 template <typename T>
 __global__ void k_geo_vol(int m, int nx, int ny, int64_t ncell, const double *__restrict__ verts, double c,

@@ -19,6 +19,8 @@ struct DevTables {
   T e0[DG_MAXM], e1[DG_MAXM];   // Gauss-Lagrange basis at xi = 0, 1
   T d0[DG_MAXM], d1[DG_MAXM];   // its derivative at xi = 0, 1
   T w[DG_MAXM];                 // Gauss weights on [0,1]
+  T s[DG_MAXM];                 // Gauss nodes on [0,1]
+  T interp_p[DG_MAXM * DG_MAXP];  // [q][l] pressure GLL basis (degree k-1) at Gauss point q
 };
 
 struct HostTables {
@@ -53,6 +55,7 @@ struct ScalarArgs {
   T vol_m;                  // c * detJ
   T face_b[3];              // |F_a| / h_a : reference normal derivative weight
   T face_pw[3];             // gamma_a * |F_a|
+  T face_area[3];           // |F_a| (face area element of the affine lattice)
   // stored geometry (GEO_STORED): gvol [ncell][7][m^3] = (G00,G01,G02,G11,G12,G22,mass)
   // with G = W detJ J^-1 J^-T and mass = c W detJ; gface [nface][7][m^2] =
   // (b-_0..2, b+_0..2, pw) with b = W J^-1 n_vec, pw = gamma W |n_vec|.
@@ -75,10 +78,21 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
                                 int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
 
+// Adjoint of the scalar operator (dg_adjoint.cu, FP64): y = A^T r with a.sc/a.ss set for
+// the transpose, and, when x is non-NULL, dkappa at every volume and face point for the
+// forward form's theta (passed separately). Geometry is affine or recomputed from
+// a.verts (geo = GEO_AFFINE or GEO_RECOMPUTE).
+cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<double> &a, double theta,
+                                  const double *r, const double *x, double *y, double *dk_vol,
+                                  double *dk_face, double *rvol, double *tr_r, double *tr_x,
+                                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
+
+// Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
+// scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
-cudaError_t launch_scalar_adjoint(int p, int m, const ScalarArgs<T> &a, const T *r, const T *x,
-                                  T *y, T *dk_vol, T *dk_face, T *rvol, T *traces, T *fres,
-                                  int cpb, int fpb, cudaStream_t s);
+cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const T *x, T *y, T *rvol, T *traces,
+                                T *fres, int nrhs, int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
+                                int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
 
 // Geometry precompute (dg_geometry.cu).
 template <typename T>
@@ -89,6 +103,10 @@ cudaError_t launch_penalty(int m, int k, int pen_mode, double alpha, int nx, int
                            int64_t nface, const int64_t *face_off, const double *verts,
                            const double *gauss_s, const double *gauss_w, double *gamma_face,
                            double *cell_vol, cudaStream_t s);
+
+// Work model of the Stokes apply (op counts of the kernels), per right-hand side.
+void stokes_work_model(int p, int64_t ncell, int64_t nface, int64_t nbface, double flops[3], double bytes[3],
+                       int elem_size);
 
 // Work model of the scalar apply (exact op counts of the kernels), per right-hand side.
 void scalar_work_model(int p, int m, int geo, bool kappa, int64_t ncell, int64_t nface,

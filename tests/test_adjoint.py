@@ -1,0 +1,140 @@
+"""GPU adjoint of the scalar SIPG apply (dg_apply_adjoint and the autograd wrapper):
+y = A^T r against the oracle's transposed apply and its assembled matrix, dL/dkappa
+against the oracle's pointwise derivative, and both against central finite differences
+(step 1e-6) of L = 0.5 ||A(kappa) x - b||^2 on the full 64^3 Q3 configuration."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_08075_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1812_08075_gb300 import build as libbuild, dg  # noqa: E402
+from paper_1812_08075_gb300.autograd import dg_apply as dg_apply_ad  # noqa: E402
+
+libbuild.build()
+TOL64 = 1e-12
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def setup(n, k, geom, theta=-1.0, kappa=True, mask=0b111111):
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    op = dg.Operator(dg.Mesh(*n, verts), k, theta=theta, dirichlet_mask=mask)
+    orc = oracle.Problem(*n, k, vertices=verts, theta=theta, dirichlet_mask=mask)
+    kv = kf = None
+    if kappa:
+        kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+        orc.kappa_vol, orc.kappa_face = kv, kf
+        op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    return op, orc, kv, kf
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+@pytest.mark.parametrize("theta", [-1.0, 1.0])
+def test_transpose_and_dkappa_vs_oracle(k, geom, theta):
+    n = (4, 3, 5)
+    op, orc, kv, kf = setup(n, k, geom, theta=theta, mask=0b101111)
+    x = wl.uniform_vector(op.ndofs, 3)
+    r = wl.uniform_vector(op.ndofs, 4)
+    xd, rd = torch.from_numpy(x).cuda(), torch.from_numpy(r).cuda()
+    y = torch.empty_like(xd)
+    dkv = torch.empty(kv.size, dtype=torch.float64, device="cuda")
+    dkf = torch.empty(kf.size, dtype=torch.float64, device="cuda")
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert relerr(y.cpu().numpy(), orc.apply(r, transpose=True)) <= TOL64
+    rv, rf = orc.dkappa(x, r)
+    assert relerr(dkv.cpu().numpy(), rv) <= TOL64
+    assert relerr(dkf.cpu().numpy(), rf) <= TOL64
+    # transpose only (no x): same y
+    y2 = torch.empty_like(xd)
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y2.data_ptr(), None, None, None)
+    assert torch.equal(y, y2)
+
+
+def test_adjoint_without_kappa_equals_forward_for_sipg():
+    op, orc, _, _ = setup((3, 4, 3), 3, "trilinear", kappa=False)
+    r = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    y = torch.empty_like(r)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, y.data_ptr(), None, None, None)
+    fwd = op.apply(r)
+    assert relerr(y.cpu().numpy(), fwd.cpu().numpy()) <= TOL64
+
+
+def test_autograd_gradients_on_8cubed_vs_assembled_matrix():
+    # config 5's 8^3 sub-case: trilinear Q3, log-normal kappa, L = 0.5||A x - b||^2
+    n, k = (8, 8, 8), 3
+    op, orc, kv, kf = setup(n, k, "trilinear")
+    x0 = wl.uniform_vector(op.ndofs, 3)
+    b = wl.uniform_vector(op.ndofs, 4)
+    x = torch.from_numpy(x0).cuda().requires_grad_(True)
+    tkv = torch.from_numpy(kv).cuda().requires_grad_(True)
+    tkf = torch.from_numpy(kf).cuda().requires_grad_(True)
+    y = dg_apply_ad(op, x, tkv, tkf)
+    L = 0.5 * ((y - torch.from_numpy(b).cuda()) ** 2).sum()
+    L.backward()
+    A = orc.assemble()
+    r = A @ x0 - b
+    assert relerr(x.grad.cpu().numpy(), A.T @ r) <= TOL64
+    rv, rf = orc.dkappa(x0, r)
+    assert relerr(tkv.grad.cpu().numpy(), rv) <= TOL64
+    assert relerr(tkf.grad.cpu().numpy(), rf) <= TOL64
+
+
+def test_finite_differences_full_config5():
+    # 64^3 trilinear Q3, kappa log-normal (seed 2), x, b ~ U[-1,1] (seeds 3, 4). The change
+    # of L under +-h is formed from y+ - y- so that no large numbers cancel.
+    n, k = (64, 64, 64), 3
+    op, _, _, _ = setup(n, k, "trilinear", kappa=False)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 3)).cuda()
+    b = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    tkv = torch.from_numpy(kv).cuda()
+    tkf = torch.from_numpy(kf).cuda()
+    op.set_kappa(tkv, tkf)
+    r = op.apply(x) - b
+    gx = torch.empty_like(x)
+    gkv = torch.empty_like(tkv)
+    gkf = torch.empty_like(tkf)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), gx.data_ptr(), gkv.data_ptr(), gkf.data_ptr(), None)
+    h = 1e-6
+    rng = np.random.default_rng(9)
+
+    def dL(yp, ym):
+        return float(0.5 * ((yp - ym) * (yp + ym - 2 * b)).sum() / (2 * h))
+
+    worst = 0.0
+    for idx in rng.choice(op.ndofs, 12, replace=False):
+        xp, xm = x.clone(), x.clone()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = dL(op.apply(xp), op.apply(xm))
+        g = float(gx[idx])
+        worst = max(worst, abs(fd - g) / max(abs(g), 1e-3 * float(gx.abs().max())))
+    for arr, grad in ((tkv, gkv), (tkf, gkf)):
+        nz = torch.nonzero(grad.abs() > 1e-3 * grad.abs().max()).flatten().cpu().numpy()
+        for idx in rng.choice(nz, 12, replace=False):
+            kp, km = arr.clone(), arr.clone()
+            kp[idx] += h
+            km[idx] -= h
+            if arr is tkv:
+                op.set_kappa(kp, tkf); yp = op.apply(x)
+                op.set_kappa(km, tkf); ym = op.apply(x)
+            else:
+                op.set_kappa(tkv, kp); yp = op.apply(x)
+                op.set_kappa(tkv, km); ym = op.apply(x)
+            op.set_kappa(tkv, tkf)
+            fd = dL(yp, ym)
+            g = float(grad[idx])
+            worst = max(worst, abs(fd - g) / max(abs(g), 1e-3 * float(grad.abs().max())))
+    print(f"worst FD relative error {worst:.2e}")
+    assert worst <= 1e-6
