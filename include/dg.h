@@ -163,6 +163,51 @@ dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host,
 dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y,
                            void *dkappa_vol, void *dkappa_face, void *stream);
 
+/* Options of the conjugate-gradient solves (the paper has no solver; these are the
+ * solves the matrix-free apply serves).
+ *   rtol       stop a right-hand side when ||b - A x||_2 <= rtol ||b||_2
+ *   max_iters  iteration limit (rounded up to a multiple of chunk)
+ *   chunk      iterations enqueued between host convergence checks (0 = 25)
+ *   use_graph  1: capture one chunk into a CUDA graph on the first call and replay it */
+typedef struct {
+  double rtol;
+  int32_t max_iters;
+  int32_t chunk;
+  int32_t use_graph;
+  int32_t reserved;
+} dg_cg_options;
+
+/* Per right-hand-side result of a solve. iters: CG iterations (summed over the inner
+ * solves of a refinement); outer: refinement steps; relres: final ||b - A x|| / ||b||
+ * (for refinement recomputed in FP64); breakdown: CG met p.Ap <= 0. */
+typedef struct {
+  int32_t iters;
+  int32_t outer;
+  int32_t converged;
+  int32_t breakdown;
+  double relres;
+} dg_solve_info;
+
+/* Batched unpreconditioned conjugate gradients on A x = b (scalar operator, SPD for
+ * theta = -1 with penalty large enough): nrhs (1..max_rhs) independent solves advanced
+ * together, vectors in the operator's precision, dot products accumulated in FP64,
+ * per right-hand-side scalars kept on the device. x (device [nrhs][ndofs]) holds the
+ * initial guess and receives the solution; b and x must not alias. info has nrhs
+ * entries. Workspace (4 vectors x max_rhs) is allocated on the first call and kept by
+ * the operator. Synchronises the stream before returning. Errors: DG_ERR_INVALID_ARG,
+ * DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED (info filled). */
+dg_status dg_cg_solve(const dg_operator *op, const void *b, void *x, int nrhs,
+                      const dg_cg_options *opt, dg_solve_info *info, void *stream);
+
+/* Mixed-precision iterative refinement: repeat r = b - A64 x (FP64), stop when
+ * ||r|| <= rtol ||b|| for every right-hand side, else solve A32 d = (float) r by the
+ * batched FP32 CG above to inner->rtol and update x += d in FP64. op64 (DG_FP64) and
+ * op32 (DG_FP32) must discretise the same operator. b, x: FP64 device [nrhs][ndofs];
+ * x holds the initial guess. Errors as dg_cg_solve. */
+dg_status dg_refine_solve(const dg_operator *op64, const dg_operator *op32, const double *b,
+                          double *x, int nrhs, double rtol, int max_outer,
+                          const dg_cg_options *inner, dg_solve_info *info, void *stream);
+
 /* y = A x for the FP64 scalar operator on the affine nx x ny x nz unit-cube mesh (the
  * same operator as dg_operator_create with vertices = NULL, DG_PEN_CONFIG penalty
  * alpha*k(k+1)/h_a, kappa = 1, one right-hand side), without any device allocation.

@@ -28,39 +28,6 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
-struct dg_mesh {
-  int nx, ny, nz;
-  bool affine;
-  std::vector<double> verts;
-};
-
-struct dg_operator {
-  int nx, ny, nz;
-  int k, p, m;
-  int problem, precision, max_rhs, geo;
-  unsigned dmask;
-  double c, mu, theta;
-  dg_penalty pen;
-  int64_t ncell, nface, nbface, ndofs;
-  int64_t face_off[4];
-  HostTables ht;
-  void *d_tab = nullptr;
-  double *d_verts = nullptr;
-  double *d_gamma = nullptr;
-  double *d_cellvol = nullptr;
-  void *d_gvol = nullptr, *d_gface = nullptr;
-  void *d_rvol = nullptr, *d_tr = nullptr, *d_fres = nullptr;
-  void *d_xh = nullptr, *d_yh = nullptr;  // staging for dg_apply_host
-  void *d_tr2 = nullptr;                  // traces of x in the adjoint (allocated on first use)
-  const void *kappa_vol = nullptr, *kappa_face = nullptr;
-  int cpb = 1, fpb = 1;
-  double gamma_axis[3];
-  // per-kernel event timing (dg_operator_profile)
-  bool prof = false;
-  std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded apply
-  size_t prof_used = 0;              // applies recorded since the last read
-};
-
 extern "C" {
 
 const char *dg_status_string(dg_status s) {
@@ -116,6 +83,7 @@ static void free_op(dg_operator *o) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
+  dg_solver_release(o);
   delete o;
 }
 
@@ -331,6 +299,10 @@ static const cudaEvent_t *next_events(dg_operator *op) {
   return op->prof_ev.data() + 4 * op->prof_used++;
 }
 
+dg_status dg_record_error(dg_status s) { return fail(s); }
+
+dg_status dg_apply_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose);
+
 static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   const cudaEvent_t *ev = next_events(op);
@@ -361,6 +333,14 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
                                    srv, str, op->cpb, op->fpb, s, ev);
   if (e != cudaSuccess) return fail(DG_ERR_CUDA);
   return DG_OK;
+}
+
+extern "C" {
+
+}  // extern "C"
+
+dg_status dg_apply_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose) {
+  return apply_impl(op, x, y, nrhs, s, transpose);
 }
 
 extern "C" {

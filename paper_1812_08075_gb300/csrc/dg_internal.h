@@ -111,3 +111,52 @@ void stokes_work_model(int p, int64_t ncell, int64_t nface, int64_t nbface, doub
 // Work model of the scalar apply (exact op counts of the kernels), per right-hand side.
 void scalar_work_model(int p, int m, int geo, bool kappa, int64_t ncell, int64_t nface,
                        int64_t nbface, double flops[3], double bytes[3], int elem_size);
+
+#include <vector>
+
+struct dg_mesh {
+  int nx, ny, nz;
+  bool affine;
+  std::vector<double> verts;
+};
+
+struct dg_operator {
+  int nx, ny, nz;
+  int k, p, m;
+  int problem, precision, max_rhs, geo;
+  unsigned dmask;
+  double c, mu, theta;
+  dg_penalty pen;
+  int64_t ncell, nface, nbface, ndofs;
+  int64_t face_off[4];
+  HostTables ht;
+  void *d_tab = nullptr;
+  double *d_verts = nullptr;
+  double *d_gamma = nullptr;
+  double *d_cellvol = nullptr;
+  void *d_gvol = nullptr, *d_gface = nullptr;
+  void *d_rvol = nullptr, *d_tr = nullptr, *d_fres = nullptr;
+  void *d_xh = nullptr, *d_yh = nullptr;  // staging for dg_apply_host
+  void *d_tr2 = nullptr;                  // traces of x in the adjoint (allocated on first use)
+  const void *kappa_vol = nullptr, *kappa_face = nullptr;
+  int cpb = 1, fpb = 1;
+  double gamma_axis[3];
+  // per-kernel event timing (dg_operator_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded apply
+  size_t prof_used = 0;              // applies recorded since the last read
+  // solver workspace (dg_solve.cu), allocated on the first solve and kept
+  void *sv_vec = nullptr;   // vectors in the operator's precision
+  size_t sv_vec_bytes = 0;
+  void *sv_aux = nullptr;   // FP64 vectors of the refinement loop
+  size_t sv_aux_bytes = 0;
+  void *sv_scal = nullptr;  // per right-hand-side scalars
+  void *sv_graph = nullptr; // cached CUDA graph of a chunk of CG iterations (cudaGraphExec_t)
+  void *sv_graph_key = nullptr;
+};
+
+
+// Shared by the API and the solver (dg_api.cu).
+dg_status dg_record_error(dg_status s);
+dg_status dg_apply_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose);
+void dg_solver_release(dg_operator *op);

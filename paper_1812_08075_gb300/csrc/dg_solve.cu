@@ -1,0 +1,408 @@
+// Krylov solves on top of the matrix-free apply: batched conjugate gradients for up to
+// 16 right-hand sides at once (each right-hand side its own independent CG with its
+// own scalars), and FP64 iterative refinement around an FP32 inner CG.
+//
+// CG on A d = r: dot products accumulate in FP64 whatever the vector precision; the
+// per-right-hand-side scalars (alpha, beta, r.z, convergence flag) live on the device,
+// so a chunk of iterations runs without host round trips and is captured once into a
+// CUDA graph and replayed. A right-hand side that has converged gets alpha = 0 and stops
+// changing while the others continue. Refinement keeps the residual b - A x, the update
+// x += d and all inner products in FP64 and uses the FP32 operator only inside CG.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace {
+
+struct Scalars {  // device, one entry per right-hand side
+  double rz[16], rz_new[16], pAp[16], rr[16], alpha[16], beta[16], tol2[16], bb[16];
+  int active[16], iters[16], breakdown[16];
+};
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v into *out (atomic, one add per block).
+__device__ __forceinline__ void block_add(double v, double *out) {
+  __shared__ double part[kThreads / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) atomicAdd(out, w);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void k_residual(const T *__restrict__ b, const T *__restrict__ Ax, T *__restrict__ r, int64_t n) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[off + i] = b[off + i] - Ax[off + i];
+}
+
+// out[rhs] += u . v (FP64 accumulation); the caller zeroes out beforehand
+template <typename T>
+__global__ void k_dot(const T *__restrict__ u, const T *__restrict__ v, double *out, int64_t n) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma((double)u[off + i], (double)v[off + i], s);
+  block_add(s, out + blockIdx.y);
+}
+
+// Start of CG: z = r (no preconditioner), p = z, rz = r.r, rr = r.r accumulated.
+template <typename T>
+__global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, Scalars *S, int64_t n) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = r[off + i];
+    p[off + i] = v;
+    s = fma((double)v, (double)v, s);
+  }
+  block_add(s, &S->rz[blockIdx.y]);
+}
+
+__global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  S->rr[r] = S->rz[r];
+  S->tol2[r] = rtol * rtol * S->bb[r];
+  S->active[r] = S->rr[r] > S->tol2[r] ? 1 : 0;
+  S->pAp[r] = 0.0;
+  S->iters[r] = 0;
+  S->breakdown[r] = 0;
+}
+
+__global__ void k_alpha(Scalars *S, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  double a = 0.0;
+  if (S->active[r]) {
+    if (S->pAp[r] > 0.0) {
+      a = S->rz[r] / S->pAp[r];
+    } else {  // A not positive definite in this direction (or roundoff): stop this rhs
+      S->active[r] = 0;
+      S->breakdown[r] = 1;
+    }
+  }
+  S->alpha[r] = a;
+  S->rz_new[r] = 0.0;
+}
+
+// x += alpha p, r -= alpha Ap, and r.r into rz_new
+template <typename T>
+__global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ Ap,
+                         Scalars *S, int64_t n) {
+  const int rhs = blockIdx.y;
+  const int64_t off = (int64_t)rhs * n;
+  const double ad = S->alpha[rhs];
+  double s = 0.0;
+  if (ad != 0.0) {
+    const T a = (T)ad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      x[off + i] = fma(a, p[off + i], x[off + i]);
+      const T v = fma(-a, Ap[off + i], r[off + i]);
+      r[off + i] = v;
+      s = fma((double)v, (double)v, s);
+    }
+  }
+  block_add(s, &S->rz_new[rhs]);
+}
+
+__global__ void k_beta(Scalars *S, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  if (S->active[r]) {
+    S->iters[r] += 1;
+    S->beta[r] = S->rz_new[r] / S->rz[r];
+    S->rz[r] = S->rz_new[r];
+    S->rr[r] = S->rz_new[r];
+    if (S->rr[r] <= S->tol2[r]) S->active[r] = 0;
+  } else {
+    S->beta[r] = 0.0;
+  }
+  S->pAp[r] = 0.0;
+}
+
+template <typename T>
+__global__ void k_direction(T *__restrict__ p, const T *__restrict__ r, const Scalars *S, int64_t n) {
+  const int rhs = blockIdx.y;
+  if (!S->active[rhs]) return;
+  const int64_t off = (int64_t)rhs * n;
+  const T b = (T)S->beta[rhs];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[off + i] = fma(b, p[off + i], r[off + i]);
+}
+
+__global__ void k_zero_scalars(Scalars *S) {
+  double *d = reinterpret_cast<double *>(S);
+  for (int i = threadIdx.x; i < 8 * 16; i += blockDim.x) d[i] = 0.0;
+}
+
+// x64 += (double) d32
+__global__ void k_add_correction(double *__restrict__ x, const float *__restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+__global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+unsigned grid_for(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  return (unsigned)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
+}
+
+#define SCK(call)                                          \
+  do {                                                     \
+    if ((call) != cudaSuccess) return dg_record_error(DG_ERR_CUDA); \
+  } while (0)
+
+void drop_graph(dg_operator *op) {
+  if (op->sv_graph) cudaGraphExecDestroy((cudaGraphExec_t)op->sv_graph);
+  op->sv_graph = nullptr;
+  op->sv_graph_key = nullptr;
+}
+
+// Workspace in op: vectors r, p, Ap (and d) of the operator's precision, max_rhs each.
+dg_status ensure_workspace(dg_operator *op, size_t es) {
+  const size_t need = 4 * (size_t)op->max_rhs * op->ndofs * es;
+  if (op->sv_vec_bytes < need) {
+    drop_graph(op);
+    if (op->sv_vec) cudaFree(op->sv_vec);
+    op->sv_vec = nullptr;
+    op->sv_vec_bytes = 0;
+    if (cudaMalloc(&op->sv_vec, need) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+    op->sv_vec_bytes = need;
+  }
+  if (!op->sv_scal) {
+    if (cudaMalloc(&op->sv_scal, sizeof(Scalars)) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+  }
+  return DG_OK;
+}
+
+// Enqueue `iters` CG iterations on x, r, p, Ap (device, [nrhs][n]) with scalars S.
+template <typename T>
+dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Scalars *S, int nrhs, int iters,
+                             cudaStream_t s) {
+  const int64_t n = op->ndofs;
+  const dim3 g(grid_for(n), nrhs);
+  for (int it = 0; it < iters; ++it) {
+    dg_status st = dg_apply_internal(op, p, Ap, nrhs, s, false);
+    if (st != DG_OK) return st;
+    k_dot<T><<<g, kThreads, 0, s>>>(p, Ap, S->pAp, n);
+    k_alpha<<<1, 32, 0, s>>>(S, nrhs);
+    k_update<T><<<g, kThreads, 0, s>>>(x, r, p, Ap, S, n);
+    k_beta<<<1, 32, 0, s>>>(S, nrhs);
+    k_direction<T><<<g, kThreads, 0, s>>>(p, r, S, n);
+  }
+  SCK(cudaGetLastError());
+  return DG_OK;
+}
+
+// CG on A x = b for nrhs right-hand sides; x holds the initial guess (x_zero: it is 0
+// and b is the initial residual). Fills info[] and returns the status.
+template <typename T>
+dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_options &o, bool x_zero,
+                 dg_solve_info *info, cudaStream_t s) {
+  const size_t es = sizeof(T);
+  dg_status st = ensure_workspace(op, es);
+  if (st != DG_OK) return st;
+  const int64_t n = op->ndofs;
+  T *r = (T *)op->sv_vec, *p = r + op->max_rhs * n, *Ap = p + op->max_rhs * n;
+  Scalars *S = (Scalars *)op->sv_scal;
+  const dim3 g(grid_for(n), nrhs);
+  k_zero_scalars<<<1, 128, 0, s>>>(S);
+  if (x_zero) {
+    SCK(cudaMemcpyAsync(r, b, (size_t)nrhs * n * es, cudaMemcpyDeviceToDevice, s));
+  } else {
+    st = dg_apply_internal(op, x, Ap, nrhs, s, false);
+    if (st != DG_OK) return st;
+    k_residual<T><<<g, kThreads, 0, s>>>(b, Ap, r, n);
+  }
+  k_dot<T><<<g, kThreads, 0, s>>>(b, b, S->bb, n);
+  k_init_dir<T><<<g, kThreads, 0, s>>>(r, p, S, n);
+  k_init_scalars<<<1, 32, 0, s>>>(S, nrhs, o.rtol);
+  SCK(cudaGetLastError());
+  const int chunk = o.chunk > 0 ? o.chunk : 25;
+  // the graph depends on the buffers, nrhs and chunk: rebuild when any of them changes
+  void *key = (void *)((uintptr_t)x ^ ((uintptr_t)b << 1) ^ ((uintptr_t)op->kappa_vol << 2) ^
+                       ((uintptr_t)op->kappa_face << 3) ^ ((uintptr_t)nrhs << 48) ^ ((uintptr_t)chunk << 56));
+  cudaStream_t cs = s;
+  bool own_stream = false;
+  if (o.use_graph && s == 0) {  // the legacy stream cannot be captured
+    SCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    own_stream = true;
+    SCK(cudaStreamSynchronize(0));
+  }
+  if (o.use_graph && (op->sv_graph == nullptr || op->sv_graph_key != key)) {
+    drop_graph(op);
+    const bool prof = op->prof;
+    const_cast<dg_operator *>(op)->prof = false;
+    cudaGraph_t graph;
+    SCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    dg_status est = enqueue_iterations<T>(op, x, r, p, Ap, S, nrhs, chunk, cs);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    op->prof = prof;
+    if (est != DG_OK) return est;
+    if (ce != cudaSuccess) return dg_record_error(DG_ERR_CUDA);
+    cudaGraphExec_t exec;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return dg_record_error(DG_ERR_CUDA);
+    op->sv_graph = (void *)exec;
+    op->sv_graph_key = key;
+  }
+  Scalars h;
+  int done = 0;
+  dg_status result = DG_ERR_NOT_CONVERGED;
+  while (done < o.max_iters) {
+    if (o.use_graph) {
+      SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
+    } else {
+      st = enqueue_iterations<T>(op, x, r, p, Ap, S, nrhs, chunk, cs);
+      if (st != DG_OK) return st;
+    }
+    done += chunk;
+    SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+    SCK(cudaStreamSynchronize(cs));
+    int any = 0;
+    for (int i = 0; i < nrhs; ++i) any |= h.active[i];
+    if (!any) {
+      result = DG_OK;
+      break;
+    }
+  }
+  if (result != DG_OK) {
+    SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+    SCK(cudaStreamSynchronize(cs));
+  }
+  for (int i = 0; i < nrhs; ++i) {
+    info[i].iters = h.iters[i];
+    info[i].outer = 0;
+    info[i].converged = h.rr[i] <= h.tol2[i] && !h.breakdown[i];
+    info[i].breakdown = h.breakdown[i];
+    info[i].relres = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
+    if (!info[i].converged) result = DG_ERR_NOT_CONVERGED;
+  }
+  if (own_stream) {
+    SCK(cudaStreamSynchronize(cs));
+    cudaStreamDestroy(cs);
+  }
+  return result;
+}
+
+}  // namespace
+
+void dg_solver_release(dg_operator *op) {
+  drop_graph(op);
+  if (op->sv_vec) cudaFree(op->sv_vec);
+  if (op->sv_aux) cudaFree(op->sv_aux);
+  if (op->sv_scal) cudaFree(op->sv_scal);
+  op->sv_vec = op->sv_aux = op->sv_scal = nullptr;
+}
+
+extern "C" {
+
+dg_status dg_cg_solve(const dg_operator *op_c, const void *b, void *x, int nrhs, const dg_cg_options *opt,
+                      dg_solve_info *info, void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !b || !x || !opt || !info || b == x) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op->max_rhs || opt->max_iters < 1 || !(opt->rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  cudaStream_t s = (cudaStream_t)stream;
+  dg_status st;
+  if (op->precision == DG_FP64) st = cg_run<double>(op, (const double *)b, (double *)x, nrhs, *opt, false, info, s);
+  else st = cg_run<float>(op, (const float *)b, (float *)x, nrhs, *opt, false, info, s);
+  return st == DG_OK ? DG_OK : dg_record_error(st);
+}
+
+dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, const double *b, double *x, int nrhs,
+                          double rtol, int max_outer, const dg_cg_options *inner, dg_solve_info *info, void *stream) {
+  dg_operator *op64 = const_cast<dg_operator *>(op64_c), *op32 = const_cast<dg_operator *>(op32_c);
+  if (!op64 || !op32 || !b || !x || !inner || !info || (const void *)b == (const void *)x) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op64->precision != DG_FP64 || op32->precision != DG_FP32 || op64->ndofs != op32->ndofs) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op64->max_rhs || nrhs > op32->max_rhs || max_outer < 1 || !(rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op64->problem != DG_SCALAR || op32->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  const int64_t n = op64->ndofs;
+  const size_t nv = (size_t)nrhs * n;
+  // FP64 residual and A x; FP32 right-hand side and correction of the inner solve
+  const size_t need = nv * (2 * sizeof(double) + 2 * sizeof(float));
+  if (op64->sv_aux_bytes < need) {
+    if (op64->sv_aux) cudaFree(op64->sv_aux);
+    op64->sv_aux = nullptr;
+    op64->sv_aux_bytes = 0;
+    if (cudaMalloc(&op64->sv_aux, need) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+    op64->sv_aux_bytes = need;
+  }
+  if (!op64->sv_scal && cudaMalloc(&op64->sv_scal, sizeof(Scalars)) != cudaSuccess) {
+    cudaGetLastError();
+    return dg_record_error(DG_ERR_OOM);
+  }
+  double *r64 = (double *)op64->sv_aux, *ax64 = r64 + nv;
+  float *r32 = (float *)(ax64 + nv), *d32 = r32 + nv;
+  Scalars *S = (Scalars *)op64->sv_scal;
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 g(grid_for(n), nrhs);
+  Scalars h;
+  std::vector<int> inner_iters(nrhs, 0);
+  dg_solve_info sub[16];
+  int outer = 0;
+  bool ok = false;
+  for (;;) {
+    // r = b - A x and its norm, in FP64
+    dg_status st = dg_apply_internal(op64, x, ax64, nrhs, s, false);
+    if (st != DG_OK) return dg_record_error(st);
+    k_residual<double><<<g, kThreads, 0, s>>>(b, ax64, r64, n);
+    k_zero_scalars<<<1, 128, 0, s>>>(S);
+    k_dot<double><<<g, kThreads, 0, s>>>(b, b, S->bb, n);
+    k_dot<double><<<g, kThreads, 0, s>>>(r64, r64, S->rr, n);
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    SCK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int i = 0; i < nrhs; ++i) {
+      info[i].relres = h.bb[i] > 0 ? sqrt(h.rr[i] / h.bb[i]) : 0.0;
+      info[i].converged = info[i].relres <= rtol;
+      all = all && info[i].converged;
+    }
+    if (all) { ok = true; break; }
+    if (outer >= max_outer) break;
+    // inner FP32 CG on A d = r from d = 0; converged right-hand sides get r = 0
+    for (int i = 0; i < nrhs; ++i) {
+      if (info[i].converged) SCK(cudaMemsetAsync(r64 + (size_t)i * n, 0, n * sizeof(double), s));
+    }
+    k_to_float<<<grid_for((int64_t)nv), kThreads, 0, s>>>(r64, r32, (int64_t)nv);
+    SCK(cudaMemsetAsync(d32, 0, nv * sizeof(float), s));
+    st = cg_run<float>(op32, r32, d32, nrhs, *inner, true, sub, s);
+    if (st != DG_OK && st != DG_ERR_NOT_CONVERGED) return dg_record_error(st);
+    for (int i = 0; i < nrhs; ++i) inner_iters[i] += sub[i].iters;
+    k_add_correction<<<grid_for((int64_t)nv), kThreads, 0, s>>>(x, d32, (int64_t)nv);
+    SCK(cudaGetLastError());
+    ++outer;
+  }
+  for (int i = 0; i < nrhs; ++i) {
+    info[i].iters = inner_iters[i];
+    info[i].outer = outer;
+    info[i].breakdown = 0;
+  }
+  return ok ? DG_OK : dg_record_error(DG_ERR_NOT_CONVERGED);
+}
+
+}  // extern "C"

@@ -27,7 +27,7 @@ EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
-    "dg_apply_affine_static",
+    "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve",
 ]
 
 
@@ -45,6 +45,16 @@ class dg_coefficients(ctypes.Structure):
     _fields_ = [("problem", ctypes.c_int32), ("precision", ctypes.c_int32), ("dirichlet_mask", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("geometry", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("c", ctypes.c_double), ("mu", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+class dg_cg_options(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class dg_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("breakdown", ctypes.c_int32), ("relres", ctypes.c_double)]
 
 
 class dg_stats(ctypes.Structure):
@@ -82,6 +92,9 @@ def lib():
         L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
+        L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
+        L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
+                                      ctypes.POINTER(dg_solve_info), vp]
         L.dg_apply_affine_static.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              i32, vp, vp, vp]
         L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
@@ -164,6 +177,29 @@ def dg_apply_affine_static(nx: int, ny: int, nz: int, degree: int, c: float, the
     """FP64 affine apply that allocates nothing (its scratch is a fixed 32 MiB device array)."""
     _check(lib().dg_apply_affine_static(nx, ny, nz, degree, c, theta, penalty_alpha, dirichlet_mask, x_ptr, y_ptr,
                                         stream), "dg_apply_affine_static")
+
+
+def _solve_result(status, infos, where):
+    out = [dict(iters=i.iters, outer=i.outer, converged=bool(i.converged), breakdown=bool(i.breakdown),
+                relres=i.relres) for i in infos]
+    if status not in (DG_OK, DG_ERR_NOT_CONVERGED):
+        raise DGError(status, where)
+    return status == DG_OK, out
+
+
+def dg_cg_solve(op: int, b_ptr: int, x_ptr: int, nrhs: int, opt: dg_cg_options, stream: Optional[int]):
+    """Returns (all converged, per right-hand-side info dicts)."""
+    infos = (dg_solve_info * nrhs)()
+    st = lib().dg_cg_solve(op, b_ptr, x_ptr, nrhs, ctypes.byref(opt), infos, stream)
+    return _solve_result(st, infos, "dg_cg_solve")
+
+
+def dg_refine_solve(op64: int, op32: int, b_ptr: int, x_ptr: int, nrhs: int, rtol: float, max_outer: int,
+                    inner: dg_cg_options, stream: Optional[int]):
+    """Returns (all converged, per right-hand-side info dicts)."""
+    infos = (dg_solve_info * nrhs)()
+    st = lib().dg_refine_solve(op64, op32, b_ptr, x_ptr, nrhs, rtol, max_outer, ctypes.byref(inner), infos, stream)
+    return _solve_result(st, infos, "dg_refine_solve")
 
 
 def dg_operator_profile(op: int, enable: bool):

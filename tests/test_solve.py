@@ -1,0 +1,111 @@
+"""GPU solves through the C ABI: batched CG (FP64 and FP32 vectors, FP64 dot products,
+CUDA-graph chunks) and FP64 iterative refinement around FP32 CG, checked against scipy on
+the oracle's assembled matrix and by residuals the oracle recomputes in FP64."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import oracle
+from paper_1812_08075_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1812_08075_gb300 import build as libbuild, dg  # noqa: E402
+
+libbuild.build()
+
+
+def opts(rtol, max_iters=5000, chunk=20, graph=1):
+    return dg.dg_cg_options(rtol, max_iters, chunk, graph, 0)
+
+
+def rhs(n, k, nrhs):
+    return wl.refinement_rhs(*n, (k + 1) ** 3, seeds=range(nrhs))
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_cg_fp64_matches_scipy(graph):
+    n, k, nrhs = (6, 5, 4), 2, 3
+    op = dg.Operator(dg.Mesh(*n), k, max_rhs=nrhs)
+    b = rhs(n, k, nrhs)
+    x = torch.zeros(nrhs, op.ndofs, dtype=torch.float64, device="cuda")
+    bd = torch.from_numpy(b).cuda()
+    ok, info = dg.dg_cg_solve(op.handle, bd.data_ptr(), x.data_ptr(), nrhs, opts(1e-10, chunk=15, graph=graph), None)
+    assert ok and all(i["converged"] for i in info)
+    A = oracle.Problem(*n, k).assemble()
+    for r in range(nrhs):
+        xr = spla.spsolve(A.tocsc(), b[r])
+        got = x[r].cpu().numpy()
+        assert np.linalg.norm(b[r] - A @ got) <= 1.01e-10 * np.linalg.norm(b[r])
+        assert np.abs(got - xr).max() <= 1e-7 * np.abs(xr).max()
+        assert info[r]["relres"] <= 1e-10
+
+
+def test_cg_graph_and_plain_agree():
+    n, k = (5, 4, 4), 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=2)
+    b = torch.from_numpy(rhs(n, k, 2)).cuda()
+    xs, its = [], []
+    for graph in (0, 1, 1):  # the second graph solve replays the cached graph
+        x = torch.zeros_like(b)
+        ok, info = dg.dg_cg_solve(op.handle, b.data_ptr(), x.data_ptr(), 2, opts(1e-9, chunk=10, graph=graph), None)
+        assert ok
+        xs.append(x)
+        its.append([i["iters"] for i in info])
+    assert its[0] == its[1] == its[2]
+    assert torch.allclose(xs[0], xs[1], rtol=0, atol=1e-12 * float(xs[0].abs().max()))
+    assert torch.equal(xs[1], xs[2])
+
+
+def test_cg_reports_non_convergence_and_zero_rhs():
+    n, k = (6, 6, 6), 2
+    op = dg.Operator(dg.Mesh(*n), k, max_rhs=2)
+    b = rhs(n, k, 2)
+    b[1] = 0.0
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    ok, info = dg.dg_cg_solve(op.handle, bd.data_ptr(), x.data_ptr(), 2, opts(1e-12, max_iters=10, chunk=5), None)
+    assert not ok
+    assert not info[0]["converged"] and info[0]["iters"] == 10
+    assert info[1]["converged"] and info[1]["iters"] == 0
+    assert float(x[1].abs().max()) == 0.0
+
+
+def test_cg_fp32_vectors_reach_fp32_level():
+    n, k = (6, 5, 4), 2
+    op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=2)
+    b = rhs(n, k, 2)
+    bd = torch.from_numpy(b).float().cuda()
+    x = torch.zeros_like(bd)
+    ok, info = dg.dg_cg_solve(op.handle, bd.data_ptr(), x.data_ptr(), 2, opts(1e-4), None)
+    assert ok
+    A = oracle.Problem(*n, k).assemble()
+    for r in range(2):
+        got = x[r].double().cpu().numpy()
+        assert np.linalg.norm(b[r] - A @ got) <= 2e-4 * np.linalg.norm(b[r])
+
+
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_refinement_reaches_1e10_with_fp32_inner_solves(geom):
+    n, k, nrhs = (8, 8, 8), 2, 16
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    mesh = dg.Mesh(*n, verts)
+    op64 = dg.Operator(mesh, k, max_rhs=nrhs)
+    op32 = dg.Operator(mesh, k, precision=dg.DG_FP32, max_rhs=nrhs)
+    b = rhs(n, k, nrhs)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    ok, info = dg.dg_refine_solve(op64.handle, op32.handle, bd.data_ptr(), x.data_ptr(), nrhs, 1e-10, 20,
+                                  opts(1e-4), None)
+    assert ok, info
+    assert all(i["outer"] >= 2 for i in info)  # FP32 alone cannot reach 1e-10
+    orc = oracle.Problem(*n, k, vertices=verts)
+    xs = x.cpu().numpy()
+    for r in range(nrhs):
+        res = np.linalg.norm(b[r] - orc.apply(xs[r])) / np.linalg.norm(b[r])
+        assert res <= 1.05e-10, (r, res)
