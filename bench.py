@@ -212,6 +212,75 @@ def time_applies(op, x, y, steps, warmup, dist, profile=False):
     return ms, kt, (t0, t1)
 
 
+def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
+    """Config 4's operator (affine 128^3, Q2): the FP32 apply of 16 right-hand sides in one
+    persistent launch, next to the FP64 apply of the same 16 vectors."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    mesh = dg.Mesh(n_cells, n_cells, n_cells)
+    res = {"workload": f"scalar SIPG, {n_cells}^3 affine cells, Q{k}, {nrhs} right-hand sides "
+                       f"(sin-product source + U[-1,1] noise, seeds 0-{nrhs - 1})"}
+    b = torch.from_numpy(wl.refinement_rhs(n_cells, n_cells, n_cells, (k + 1) ** 3, range(nrhs))).cuda()
+    for prec, tag in ((dg.DG_FP32, "fp32"), (dg.DG_FP64, "fp64")):
+        op = dg.Operator(mesh, k, precision=prec, max_rhs=nrhs)
+        xx = b.to(op.dtype)
+        yy = torch.empty_like(xx)
+        ms, kt, _ = time_applies(op, xx, yy, 10, 3, None, profile=True)
+        st = op.stats()
+        f = sum(st.flops) * nrhs
+        peak = pk["fp32_tflops"] if prec == dg.DG_FP32 else pk["fp64_tflops"]
+        byt = st.dofs_bytes * nrhs
+        res[tag] = {"dof_s": nrhs * op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "variant":
+                    "fused persistent" if st.variant == dg.DG_VARIANT_FUSED else "three-kernel",
+                    "persistent_grid": st.persistent_grid, "tflops": f / (ms * 1e-3) / 1e12,
+                    "frac_alu_peak": f / (ms * 1e-3) / 1e12 / peak,
+                    "hbm_gbs_algorithmic": byt / (ms * 1e-3) / 1e9,
+                    "frac_hbm": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "kernel_ms": kt}
+        del op, xx, yy
+    return res
+
+
+def run_solve(args):
+    """Config 4: 16 right-hand sides, FP64 CG against FP64 refinement around FP32 CG."""
+    import torch
+    from paper_1812_08075_gb300 import build as libbuild, dg
+    libbuild.build()
+    n, k, nrhs = args.solve_cells, args.solve_degree, args.solve_rhs
+    mesh = dg.Mesh(n, n, n)
+    op64 = dg.Operator(mesh, k, max_rhs=nrhs)
+    op32 = dg.Operator(mesh, k, precision=dg.DG_FP32, max_rhs=nrhs)
+    b = torch.from_numpy(wl.refinement_rhs(n, n, n, (k + 1) ** 3, range(nrhs))).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {"mode": "solve", "workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides",
+           "ndofs": op64.ndofs, "rtol": args.solve_rtol}
+
+    def check(x):
+        r = b - op64.apply(x)
+        return [float(torch.linalg.norm(r[i]) / torch.linalg.norm(b[i])) for i in range(nrhs)]
+
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ok, info = dg.dg_refine_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, args.solve_rtol, 30,
+                                  dg.dg_cg_options(args.inner_rtol, 100000, 50, 1, 0), stream)
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t
+    out["mixed"] = {"seconds": t_mixed, "converged": ok, "outer": max(i["outer"] for i in info),
+                    "inner_iters_max": max(i["iters"] for i in info), "relres_max": max(check(x)),
+                    "inner_rtol": args.inner_rtol}
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ok, info = dg.dg_cg_solve(op64.handle, b.data_ptr(), x.data_ptr(), nrhs,
+                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, 0), stream)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t
+    out["fp64_cg"] = {"seconds": t64, "converged": ok, "iters_max": max(i["iters"] for i in info),
+                      "relres_max": max(check(x))}
+    out["speedup_mixed_over_fp64"] = t64 / t_mixed
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1812_08075_gb300 import build as libbuild, dg
@@ -288,6 +357,8 @@ def run_ours(args, rank, world, dist):
                                          "kernel_ms": kt_k}
                 del o, xx, yy
         out["sweep"] = sweep
+    if args.mixed and rank == 0:
+        out["mixed_apply"] = mixed_apply(pk)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -311,6 +382,14 @@ def main():
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=64, help="cells per axis (64 is the benchmark workload)")
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false", default=True)
+    ap.add_argument("--solve-cells", type=int, default=128)
+    ap.add_argument("--solve-degree", type=int, default=2)
+    ap.add_argument("--solve-rhs", type=int, default=16)
+    ap.add_argument("--solve-rtol", type=float, default=1e-10)
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--fp64-max-iters", type=int, default=20000)
     args = ap.parse_args()
     global N_CELLS
     N_CELLS = args.cells
@@ -324,7 +403,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl" if args.impl == "ours" else "gloo")
         dist = tdist
-    if args.impl == "reference":
+    if args.mode == "solve":
+        if rank == 0:
+            run_solve(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, dist)

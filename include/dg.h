@@ -47,6 +47,7 @@ enum { DG_PEN_CONFIG = 0, DG_PEN_PAPER = 1 };
 enum { DG_SCALAR = 0, DG_STOKES = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
+enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2 };
 
 /* Interior-penalty factor gamma_F (Sec. 5.2).
  *   DG_PEN_CONFIG: gamma_F = alpha * k * (k+1) / h_a with h_a = 1/n_a the nominal cell
@@ -100,6 +101,8 @@ typedef struct {
   int32_t threads_cell;
   int32_t threads_face;
   int32_t geometry;       /* DG_GEOM_* in effect (0 = affine fast path) */
+  int32_t variant;        /* DG_VARIANT_THREE_KERNEL or DG_VARIANT_FUSED */
+  int32_t persistent_grid;/* blocks of the last fused (persistent) launch, 0 if none yet */
   int32_t reserved;
 } dg_stats;
 
@@ -133,6 +136,19 @@ dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n);
 
 /* Work model and launch configuration currently in effect (host only). */
 dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
+
+/* Kernel variant and blocking of later applies (the search space of the tuner).
+ *   DG_VARIANT_THREE_KERNEL: cell kernel (volume terms and face traces), face kernel,
+ *     back-projection kernel, with scratch for traces and residuals; any geometry.
+ *   DG_VARIANT_FUSED: one persistent launch (one wave of blocks looping over
+ *     (right-hand side, row of cells) items) in which each cell evaluates its faces from
+ *     its own side with the neighbour's trace gathered from its coefficients; affine
+ *     scalar operators without kappa only; no scratch.
+ *   DG_VARIANT_AUTO: fused for FP32 affine scalar operators, three-kernel otherwise.
+ * cells_per_block (cells per block, or cells per row tile of the fused kernel) and
+ * faces_per_block: 0 keeps the default. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED
+ * (fused variant on an operator it does not cover, blocking over the shared-memory limit). */
+dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block);
 
 /* Per-quadrature-point diffusion coefficient kappa (scalar problem): device arrays of
  * the operator's precision, kappa_vol [ncell][m^3] (points q0 + m(q1 + m q2)) and

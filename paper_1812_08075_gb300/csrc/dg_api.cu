@@ -99,6 +99,10 @@ static void fill_devtables(const HostTables &h, DevTables<T> &d) {
     d.w[i] = (T)h.gauss_w[i];
     d.s[i] = (T)h.gauss_s[i];
   }
+  for (int j = 0; j < h.p; ++j) {
+    d.gd0[j] = (T)h.gd0[j];
+    d.gd1[j] = (T)h.gd1[j];
+  }
   for (int q = 0; q < h.m; ++q)
     for (int j = 0; j < h.pp; ++j) d.interp_p[q * h.pp + j] = (T)h.interp_p[q * h.pp + j];
 }
@@ -138,6 +142,16 @@ static void default_blocking(dg_operator *o) {
   const int M3 = o->m * o->m * o->m, M2 = o->m * o->m;
   o->cpb = 256 / M3 > 0 ? 256 / M3 : 1;
   o->fpb = 256 / M2 > 0 ? 256 / M2 : 1;
+  o->tile = o->p <= 3 ? 8 : (o->p == 4 ? 4 : 2);
+}
+
+static bool fused_ok(const dg_operator *o) {
+  return o->problem == DG_SCALAR && o->geo == GEO_AFFINE && o->kappa_vol == nullptr;
+}
+
+static int resolve_variant(const dg_operator *o, int v) {
+  if (v == DG_VARIANT_AUTO) return (o->precision == DG_FP32 && fused_ok(o)) ? DG_VARIANT_FUSED : DG_VARIANT_THREE_KERNEL;
+  return v;
 }
 
 extern "C" {
@@ -188,6 +202,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
                                                   : pen->alpha * degree * (degree + 2) * n[a];
   if (dg_build_tables(degree, m, stokes, &o->ht)) { free_op(o); return fail(DG_ERR_UNSUPPORTED); }
   default_blocking(o);
+  o->variant = resolve_variant(o, DG_VARIANT_AUTO);
   const size_t es = o->precision == DG_FP64 ? sizeof(double) : sizeof(float);
 
 #define ALLOC(ptr, bytes)                                       \
@@ -260,6 +275,7 @@ dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const vo
   if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
   op->kappa_vol = kappa_vol;
   op->kappa_face = kappa_face;
+  if (op->variant == DG_VARIANT_FUSED && !fused_ok(op)) op->variant = DG_VARIANT_THREE_KERNEL;
   return DG_OK;
 }
 
@@ -272,6 +288,8 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   const int es = op->precision == DG_FP64 ? 8 : 4;
   if (op->problem == DG_STOKES)
     stokes_work_model(op->p, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
+  else if (op->variant == DG_VARIANT_FUSED)
+    fused_work_model(op->p, op->ncell, op->nbface, out->flops, out->bytes, es);
   else
     scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, out->flops,
                       out->bytes, es);
@@ -283,6 +301,14 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   out->threads_cell = thr(op->cpb * M3);
   out->threads_face = thr(op->fpb * M2);
   out->geometry = op->geo;
+  out->variant = op->variant;
+  out->persistent_grid = op->fused_grid;
+  if (op->variant == DG_VARIANT_FUSED) {
+    out->cells_per_block = op->tile;
+    out->threads_cell = 256;
+    out->faces_per_block = 0;
+    out->threads_face = 0;
+  }
   return DG_OK;
 }
 
@@ -323,6 +349,16 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   }
   const int64_t sdof = op->ndofs, srv = op->ncell * M3, str = op->ncell * 12 * M2;
   const bool kap = op->kappa_vol != nullptr;
+  if (op->variant == DG_VARIANT_FUSED && fused_ok(op)) {
+    if (op->precision == DG_FP64)
+      e = launch_fused_apply<double>(op->p, scalar_args<double>(op, transpose), (const double *)x, (double *)y, nrhs,
+                                     sdof, op->tile, s, ev, &op->fused_grid);
+    else
+      e = launch_fused_apply<float>(op->p, scalar_args<float>(op, transpose), (const float *)x, (float *)y, nrhs,
+                                    sdof, op->tile, s, ev, &op->fused_grid);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+    return DG_OK;
+  }
   if (op->precision == DG_FP64)
     e = launch_scalar_apply<double>(op->p, op->m, op->geo, kap, scalar_args<double>(op, transpose), (const double *)x,
                                     (double *)y, (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_fres, nrhs,
@@ -397,6 +433,29 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
                                         (double *)op->d_tr, (double *)op->d_tr2, (double *)op->d_fres, op->cpb,
                                         op->fpb, (cudaStream_t)stream, ev);
   if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  return DG_OK;
+}
+
+dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block) {
+  if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_FUSED || cells_per_block < 0 || faces_per_block < 0)
+    return fail(DG_ERR_INVALID_ARG);
+  const int v = resolve_variant(op, variant);
+  if (v == DG_VARIANT_FUSED && !fused_ok(op)) return fail(DG_ERR_UNSUPPORTED);
+  const size_t es = op->precision == DG_FP64 ? 8 : 4;
+  const int M = op->m, P = op->p;
+  if (cells_per_block > 0) {
+    const size_t per = v == DG_VARIANT_FUSED ? (size_t)(8 * P * P * P + 60 * P * P) * es
+                                             : (size_t)(op->problem == DG_STOKES ? 12 : 4) * M * M * M * es;
+    if (cells_per_block * per + 4096 > 200 * 1024) return fail(DG_ERR_UNSUPPORTED);
+  }
+  if (faces_per_block > 0 && (size_t)faces_per_block * 13 * M * M * es + 4096 > 200 * 1024) return fail(DG_ERR_UNSUPPORTED);
+  op->variant = v;
+  if (v == DG_VARIANT_FUSED) {
+    if (cells_per_block > 0) op->tile = cells_per_block;
+  } else {
+    if (cells_per_block > 0) op->cpb = cells_per_block;
+    if (faces_per_block > 0) op->fpb = faces_per_block;
+  }
   return DG_OK;
 }
 
@@ -495,4 +554,21 @@ void stokes_work_model(int P, int64_t ncell, int64_t nface, int64_t nbface, doub
   bytes[0] = es * (double)ncell * (3 * P3 + PP3 + 4 * M3 + 42 * M2);
   bytes[1] = es * (ninner * 2.0 * 2.0 * 42 * M2 + (double)nbface * 2.0 * 42 * M2) / 2.0;
   bytes[2] = es * (double)ncell * (4 * M3 + 42 * M2 + 3 * P3 + PP3);
+}
+
+// Fused single-pass variant: per cell, the neighbours' face data, interpolation, traces,
+// gradient, pointwise flux, transposed derivative, the six own-side face terms, lifting
+// and transposed interpolation; all of it in kernel 0. Bytes: x read and y written.
+void fused_work_model(int P, int64_t ncell, int64_t nbface, double flops[3], double bytes[3], int es) {
+  const double M = P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  const double cP = 2.0 * P - 1.0, cM = 2.0 * M - 1.0;
+  const double nbfaces = 6.0 * (double)ncell - (double)nbface;  // own faces with a neighbour
+  double f = nbfaces * P2 * cP;                                // neighbour normal derivative
+  f += (double)ncell * 12.0 * (P * M + M2) * cP;               // neighbour tangential sweeps
+  double cell = (P2 * M + P * M2 + M3) * cP + 12.0 * M2 * cM + 3.0 * M3 * cM + 8.0 * M3 + (4.0 + 6.0 * M) * M3;
+  cell += 6.0 * M2 * 12.0 + 24.0 * M3 + (M2 * P + M * P2 + P3) * cM;
+  flops[0] = f + cell * (double)ncell;
+  flops[1] = flops[2] = 0.0;
+  bytes[0] = es * (double)ncell * 2.0 * P3;
+  bytes[1] = bytes[2] = 0.0;
 }

@@ -20,6 +20,7 @@ struct DevTables {
   T d0[DG_MAXM], d1[DG_MAXM];   // its derivative at xi = 0, 1
   T w[DG_MAXM];                 // Gauss weights on [0,1]
   T s[DG_MAXM];                 // Gauss nodes on [0,1]
+  T gd0[DG_MAXP], gd1[DG_MAXP]; // derivative of the GLL basis at xi = 0, 1
   T interp_p[DG_MAXM * DG_MAXP];  // [q][l] pressure GLL basis (degree k-1) at Gauss point q
 };
 
@@ -30,6 +31,7 @@ struct HostTables {
   double interp[DG_MAXM * DG_MAXP];
   double dcol[DG_MAXM * DG_MAXM];
   double e0[DG_MAXM], e1[DG_MAXM], d0[DG_MAXM], d1[DG_MAXM];
+  double gd0[DG_MAXP], gd1[DG_MAXP];  // GLL basis derivative at xi = 0, 1
   // pressure space of the Stokes problem (degree k-1): GLL basis at the Gauss points
   int pp;
   double interp_p[DG_MAXM * DG_MAXP];
@@ -87,6 +89,13 @@ cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<d
                                   double *dk_face, double *rvol, double *tr_r, double *tr_x,
                                   double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
 
+// Persistent single-pass apply for affine meshes (dg_fused.cu): one launch of one wave of
+// blocks that loop over (right-hand side, row of cells) work items; each cell gathers its
+// neighbours' face data from their coefficients, so no scratch memory is used.
+template <typename T>
+cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t stride_dofs,
+                               int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out);
+
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
@@ -103,6 +112,9 @@ cudaError_t launch_penalty(int m, int k, int pen_mode, double alpha, int nx, int
                            int64_t nface, const int64_t *face_off, const double *verts,
                            const double *gauss_s, const double *gauss_w, double *gamma_face,
                            double *cell_vol, cudaStream_t s);
+
+// Work model of the fused single-pass variant, per right-hand side (all in flops[0]).
+void fused_work_model(int p, int64_t ncell, int64_t nbface, double flops[3], double bytes[3], int elem_size);
 
 // Work model of the Stokes apply (op counts of the kernels), per right-hand side.
 void stokes_work_model(int p, int64_t ncell, int64_t nface, int64_t nbface, double flops[3], double bytes[3],
@@ -140,6 +152,9 @@ struct dg_operator {
   void *d_tr2 = nullptr;                  // traces of x in the adjoint (allocated on first use)
   const void *kappa_vol = nullptr, *kappa_face = nullptr;
   int cpb = 1, fpb = 1;
+  int variant = DG_VARIANT_THREE_KERNEL;  // resolved (never AUTO)
+  int tile = 8;                          // cells per row tile of the fused kernel
+  int fused_grid = 0;
   double gamma_axis[3];
   // per-kernel event timing (dg_operator_profile)
   bool prof = false;

@@ -23,6 +23,13 @@ struct Scalars {  // device, one entry per right-hand side
 };
 
 constexpr int kThreads = 256;
+constexpr int kMaxBlocks = 152 * 16;  // grid of the vector kernels (fixed per size: fixed reduction order)
+
+// Scalars followed by per-block partial sums [16 rhs][kMaxBlocks] of the reductions.
+struct Workspace {
+  Scalars S;
+  double partial[16 * kMaxBlocks];
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -30,8 +37,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of v into *out (atomic, one add per block).
-__device__ __forceinline__ void block_add(double v, double *out) {
+// Block sum of v written to partial[rhs * kMaxBlocks + block] (no atomics: the final sum
+// in k_reduce runs in a fixed order, so reductions are bitwise reproducible).
+__device__ __forceinline__ void block_partial(double v, double *partial) {
   __shared__ double part[kThreads / 32];
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
@@ -39,9 +47,24 @@ __device__ __forceinline__ void block_add(double v, double *out) {
   if (threadIdx.x < 32) {
     double w = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
     w = warp_sum(w);
-    if (threadIdx.x == 0) atomicAdd(out, w);
+    if (threadIdx.x == 0) partial[blockIdx.y * kMaxBlocks + blockIdx.x] = w;
   }
   __syncthreads();
+}
+
+// out[rhs] = sum of the nblocks partials of rhs (one block per rhs, fixed order)
+__global__ void k_reduce(const double *__restrict__ partial, double *out, int nblocks) {
+  __shared__ double sh[kThreads];
+  const int rhs = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partial[rhs * kMaxBlocks + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[rhs] = sh[0];
 }
 
 template <typename T>
@@ -51,19 +74,19 @@ __global__ void k_residual(const T *__restrict__ b, const T *__restrict__ Ax, T 
     r[off + i] = b[off + i] - Ax[off + i];
 }
 
-// out[rhs] += u . v (FP64 accumulation); the caller zeroes out beforehand
+// partials of u . v per rhs (FP64 accumulation); k_reduce finishes the sum
 template <typename T>
-__global__ void k_dot(const T *__restrict__ u, const T *__restrict__ v, double *out, int64_t n) {
+__global__ void k_dot(const T *__restrict__ u, const T *__restrict__ v, double *partial, int64_t n) {
   const int64_t off = (int64_t)blockIdx.y * n;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s = fma((double)u[off + i], (double)v[off + i], s);
-  block_add(s, out + blockIdx.y);
+  block_partial(s, partial);
 }
 
-// Start of CG: z = r (no preconditioner), p = z, rz = r.r, rr = r.r accumulated.
+// Start of CG: z = r (no preconditioner), p = z, partials of r.r.
 template <typename T>
-__global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, Scalars *S, int64_t n) {
+__global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, double *partial, int64_t n) {
   const int64_t off = (int64_t)blockIdx.y * n;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -71,7 +94,7 @@ __global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, Scalars *
     p[off + i] = v;
     s = fma((double)v, (double)v, s);
   }
-  block_add(s, &S->rz[blockIdx.y]);
+  block_partial(s, partial);
 }
 
 __global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
@@ -98,13 +121,12 @@ __global__ void k_alpha(Scalars *S, int nrhs) {
     }
   }
   S->alpha[r] = a;
-  S->rz_new[r] = 0.0;
 }
 
 // x += alpha p, r -= alpha Ap, and r.r into rz_new
 template <typename T>
 __global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ Ap,
-                         Scalars *S, int64_t n) {
+                         const Scalars *S, double *partial, int64_t n) {
   const int rhs = blockIdx.y;
   const int64_t off = (int64_t)rhs * n;
   const double ad = S->alpha[rhs];
@@ -118,7 +140,7 @@ __global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restri
       s = fma((double)v, (double)v, s);
     }
   }
-  block_add(s, &S->rz_new[rhs]);
+  block_partial(s, partial);
 }
 
 __global__ void k_beta(Scalars *S, int nrhs) {
@@ -133,7 +155,6 @@ __global__ void k_beta(Scalars *S, int nrhs) {
   } else {
     S->beta[r] = 0.0;
   }
-  S->pAp[r] = 0.0;
 }
 
 template <typename T>
@@ -190,23 +211,26 @@ dg_status ensure_workspace(dg_operator *op, size_t es) {
     op->sv_vec_bytes = need;
   }
   if (!op->sv_scal) {
-    if (cudaMalloc(&op->sv_scal, sizeof(Scalars)) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+    if (cudaMalloc(&op->sv_scal, sizeof(Workspace)) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
   }
   return DG_OK;
 }
 
 // Enqueue `iters` CG iterations on x, r, p, Ap (device, [nrhs][n]) with scalars S.
 template <typename T>
-dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Scalars *S, int nrhs, int iters,
+dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Workspace *W, int nrhs, int iters,
                              cudaStream_t s) {
   const int64_t n = op->ndofs;
   const dim3 g(grid_for(n), nrhs);
+  Scalars *S = &W->S;
   for (int it = 0; it < iters; ++it) {
     dg_status st = dg_apply_internal(op, p, Ap, nrhs, s, false);
     if (st != DG_OK) return st;
-    k_dot<T><<<g, kThreads, 0, s>>>(p, Ap, S->pAp, n);
+    k_dot<T><<<g, kThreads, 0, s>>>(p, Ap, W->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
     k_alpha<<<1, 32, 0, s>>>(S, nrhs);
-    k_update<T><<<g, kThreads, 0, s>>>(x, r, p, Ap, S, n);
+    k_update<T><<<g, kThreads, 0, s>>>(x, r, p, Ap, S, W->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz_new, g.x);
     k_beta<<<1, 32, 0, s>>>(S, nrhs);
     k_direction<T><<<g, kThreads, 0, s>>>(p, r, S, n);
   }
@@ -224,7 +248,8 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   if (st != DG_OK) return st;
   const int64_t n = op->ndofs;
   T *r = (T *)op->sv_vec, *p = r + op->max_rhs * n, *Ap = p + op->max_rhs * n;
-  Scalars *S = (Scalars *)op->sv_scal;
+  Workspace *W = (Workspace *)op->sv_scal;
+  Scalars *S = &W->S;
   const dim3 g(grid_for(n), nrhs);
   k_zero_scalars<<<1, 128, 0, s>>>(S);
   if (x_zero) {
@@ -234,8 +259,10 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     if (st != DG_OK) return st;
     k_residual<T><<<g, kThreads, 0, s>>>(b, Ap, r, n);
   }
-  k_dot<T><<<g, kThreads, 0, s>>>(b, b, S->bb, n);
-  k_init_dir<T><<<g, kThreads, 0, s>>>(r, p, S, n);
+  k_dot<T><<<g, kThreads, 0, s>>>(b, b, W->partial, n);
+  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->bb, g.x);
+  k_init_dir<T><<<g, kThreads, 0, s>>>(r, p, W->partial, n);
+  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz, g.x);
   k_init_scalars<<<1, 32, 0, s>>>(S, nrhs, o.rtol);
   SCK(cudaGetLastError());
   const int chunk = o.chunk > 0 ? o.chunk : 25;
@@ -255,7 +282,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     const_cast<dg_operator *>(op)->prof = false;
     cudaGraph_t graph;
     SCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    dg_status est = enqueue_iterations<T>(op, x, r, p, Ap, S, nrhs, chunk, cs);
+    dg_status est = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     op->prof = prof;
     if (est != DG_OK) return est;
@@ -274,7 +301,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     if (o.use_graph) {
       SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
     } else {
-      st = enqueue_iterations<T>(op, x, r, p, Ap, S, nrhs, chunk, cs);
+      st = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
       if (st != DG_OK) return st;
     }
     done += chunk;
@@ -351,13 +378,14 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
     if (cudaMalloc(&op64->sv_aux, need) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
     op64->sv_aux_bytes = need;
   }
-  if (!op64->sv_scal && cudaMalloc(&op64->sv_scal, sizeof(Scalars)) != cudaSuccess) {
+  if (!op64->sv_scal && cudaMalloc(&op64->sv_scal, sizeof(Workspace)) != cudaSuccess) {
     cudaGetLastError();
     return dg_record_error(DG_ERR_OOM);
   }
   double *r64 = (double *)op64->sv_aux, *ax64 = r64 + nv;
   float *r32 = (float *)(ax64 + nv), *d32 = r32 + nv;
-  Scalars *S = (Scalars *)op64->sv_scal;
+  Workspace *W = (Workspace *)op64->sv_scal;
+  Scalars *S = &W->S;
   cudaStream_t s = (cudaStream_t)stream;
   const dim3 g(grid_for(n), nrhs);
   Scalars h;
@@ -371,8 +399,10 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
     if (st != DG_OK) return dg_record_error(st);
     k_residual<double><<<g, kThreads, 0, s>>>(b, ax64, r64, n);
     k_zero_scalars<<<1, 128, 0, s>>>(S);
-    k_dot<double><<<g, kThreads, 0, s>>>(b, b, S->bb, n);
-    k_dot<double><<<g, kThreads, 0, s>>>(r64, r64, S->rr, n);
+    k_dot<double><<<g, kThreads, 0, s>>>(b, b, W->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->bb, g.x);
+    k_dot<double><<<g, kThreads, 0, s>>>(r64, r64, W->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rr, g.x);
     SCK(cudaGetLastError());
     SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     SCK(cudaStreamSynchronize(s));

@@ -142,6 +142,10 @@ int dg_build_tables(int k, int m, bool with_pressure, HostTables *T) {
     lagrange_at(k + 1, z, lam, s[q], val, der);
     for (int j = 0; j <= k; ++j) T->interp[q * T->p + j] = (double)val[j];
   }
+  lagrange_at(k + 1, z, lam, 0.0L, val, der);
+  for (int j = 0; j <= k; ++j) T->gd0[j] = (double)der[j];
+  lagrange_at(k + 1, z, lam, 1.0L, val, der);
+  for (int j = 0; j <= k; ++j) T->gd1[j] = (double)der[j];
   ld lg[DG_MAXM], vg[DG_MAXM], dg[DG_MAXM];
   bary_weights(m, s, lg);
   for (int q = 0; q < m; ++q) {

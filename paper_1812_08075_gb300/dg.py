@@ -22,12 +22,13 @@ DG_PEN_CONFIG, DG_PEN_PAPER = 0, 1
 DG_SCALAR, DG_STOKES = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
+DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED = 0, 1, 2
 
 EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
-    "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve",
+    "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
 ]
 
 
@@ -62,7 +63,8 @@ class dg_stats(ctypes.Structure):
                 ("flops", ctypes.c_double * 3), ("bytes", ctypes.c_double * 3), ("dofs_bytes", ctypes.c_double),
                 ("cells_per_block", ctypes.c_int32), ("faces_per_block", ctypes.c_int32),
                 ("threads_cell", ctypes.c_int32), ("threads_face", ctypes.c_int32),
-                ("geometry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("geometry", ctypes.c_int32), ("variant", ctypes.c_int32), ("persistent_grid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +94,7 @@ def lib():
         L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
+        L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
                                       ctypes.POINTER(dg_solve_info), vp]
@@ -202,6 +205,10 @@ def dg_refine_solve(op64: int, op32: int, b_ptr: int, x_ptr: int, nrhs: int, rto
     return _solve_result(st, infos, "dg_refine_solve")
 
 
+def dg_operator_set_variant(op: int, variant: int, cells_per_block: int = 0, faces_per_block: int = 0):
+    _check(lib().dg_operator_set_variant(op, variant, cells_per_block, faces_per_block), "dg_operator_set_variant")
+
+
 def dg_operator_profile(op: int, enable: bool):
     _check(lib().dg_operator_profile(op, int(enable)), "dg_operator_profile")
 
@@ -286,6 +293,9 @@ class Operator:
 
     def stats(self) -> dg_stats:
         return dg_operator_stats(self.handle)
+
+    def set_variant(self, variant: int, cells_per_block: int = 0, faces_per_block: int = 0):
+        dg_operator_set_variant(self.handle, variant, cells_per_block, faces_per_block)
 
     def set_kappa(self, kappa_vol=None, kappa_face=None):
         """Per-quadrature-point kappa as device tensors of the operator's dtype (None = 1)."""

@@ -144,3 +144,57 @@ def test_config2_full_size_sampled(k):
     ref = orc.apply_cells(x, cells, nthreads=0)
     err = float(np.abs(y[cells] - ref).max() / np.abs(ref).max())
     assert err <= TOL64, err
+
+
+# ---------------------------------------------------------------- fused persistent variant
+
+def run_fused(n, k, precision, nrhs=1, tile=0, theta=-1.0, mask=0b111111, c=1.0):
+    op = dg.Operator(dg.Mesh(*n), k, precision=precision, max_rhs=nrhs, theta=theta, dirichlet_mask=mask, c=c)
+    op.set_variant(dg.DG_VARIANT_FUSED, tile)
+    assert op.stats().variant == dg.DG_VARIANT_FUSED
+    orc = oracle.Problem(*n, k, theta=theta, dirichlet_mask=mask, c=c)
+    xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(nrhs)])
+    y = op.apply(torch.from_numpy(xs).to("cuda", op.dtype)).double().cpu().numpy()
+    assert op.stats().persistent_grid > 0
+    return max(relerr(y[r], orc.apply(xs[r])) for r in range(nrhs))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_fused_fp64_matches_oracle(k):
+    # rows of 8/4/2 cells along x: 11 cells leave a ragged last tile
+    assert run_fused((11, 3, 4), k, dg.DG_FP64) <= TOL64
+
+
+@pytest.mark.parametrize("tile", [1, 3, 16])
+def test_fused_tiles_theta_masks_and_rhs(tile):
+    assert run_fused((5, 4, 3), 2, dg.DG_FP64, nrhs=3, tile=tile, theta=1.0, mask=0b100111, c=0.5) <= TOL64
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_fused_fp32(k):
+    err = run_fused((9, 4, 5), k, dg.DG_FP32, nrhs=4)
+    print(f"fused FP32 Q{k}: rel err {err:.2e}")
+    assert err <= TOL32
+
+
+def test_fused_is_the_fp32_affine_default_and_rejected_elsewhere():
+    assert dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32).stats().variant == dg.DG_VARIANT_FUSED
+    assert dg.Operator(dg.Mesh(3, 3, 3), 2).stats().variant == dg.DG_VARIANT_THREE_KERNEL
+    op = dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, precision=dg.DG_FP32)
+    assert op.stats().variant == dg.DG_VARIANT_THREE_KERNEL
+    with pytest.raises(dg.DGError) as e:
+        op.set_variant(dg.DG_VARIANT_FUSED)
+    assert e.value.status == dg.DG_ERR_UNSUPPORTED
+
+
+def test_config4_fp32_16rhs_full_size_sampled():
+    # 128^3 affine cells, Q2, FP32, 16 right-hand sides in one persistent launch
+    n, k, nrhs = (128, 128, 128), 2, 16
+    op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    b = wl.refinement_rhs(*n, 27, seeds=range(nrhs), dtype=np.float32)
+    y = op.apply(torch.from_numpy(b).cuda()).cpu().numpy().reshape(nrhs, op.mesh.ncell, 27)
+    cells = wl.sample_cells(op.mesh.ncell, 48, seed=17)
+    orc = oracle.Problem(*n, k)
+    for r in (0, 7, 15):
+        ref = orc.apply_cells(b[r].astype(np.float64), cells)
+        assert float(np.abs(y[r][cells] - ref).max() / np.abs(ref).max()) <= TOL32

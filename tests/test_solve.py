@@ -57,9 +57,9 @@ def test_cg_graph_and_plain_agree():
         assert ok
         xs.append(x)
         its.append([i["iters"] for i in info])
+    # reductions run in a fixed order, so graph replays and plain launches agree bitwise
     assert its[0] == its[1] == its[2]
-    assert torch.allclose(xs[0], xs[1], rtol=0, atol=1e-12 * float(xs[0].abs().max()))
-    assert torch.equal(xs[1], xs[2])
+    assert torch.equal(xs[0], xs[1]) and torch.equal(xs[1], xs[2])
 
 
 def test_cg_reports_non_convergence_and_zero_rhs():
