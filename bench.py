@@ -223,6 +223,7 @@ def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
     b = torch.from_numpy(wl.refinement_rhs(n_cells, n_cells, n_cells, (k + 1) ** 3, range(nrhs))).cuda()
     for prec, tag in ((dg.DG_FP32, "fp32"), (dg.DG_FP64, "fp64")):
         op = dg.Operator(mesh, k, precision=prec, max_rhs=nrhs)
+        res.setdefault("tuning", {})[tag] = op.autotune(nrhs)
         xx = b.to(op.dtype)
         yy = torch.empty_like(xx)
         ms, kt, _ = time_applies(op, xx, yy, 10, 3, None, profile=True)
@@ -292,6 +293,7 @@ def run_ours(args, rank, world, dist):
     verts = wl.perturbed_vertices(*n, seed=1)
     mesh = dg.Mesh(*n, verts)
     op = dg.Operator(mesh, k)
+    tuning = op.autotune(1) if args.autotune else None
     x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
     y = torch.empty_like(x)
     pk = peaks()
@@ -326,7 +328,8 @@ def run_ours(args, rank, world, dist):
     out = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
-           "roofline": roofline, "apply": whole, "gpu_launches": 3 * args.steps, "clocks": clocks}
+           "roofline": roofline, "apply": whole, "gpu_launches": 3 * args.steps, "clocks": clocks,
+           "tuning": tuning}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -358,7 +361,7 @@ def run_ours(args, rank, world, dist):
                 del o, xx, yy
         out["sweep"] = sweep
     if args.mixed and rank == 0:
-        out["mixed_apply"] = mixed_apply(pk)
+        out["mixed_apply"] = mixed_apply(pk, n_cells=args.mixed_cells)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -384,6 +387,8 @@ def main():
     ap.add_argument("--cells", type=int, default=64, help="cells per axis (64 is the benchmark workload)")
     ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", default=True)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
+    ap.add_argument("--mixed-cells", type=int, default=128, help="cells per axis of the mixed-precision apply")
     ap.add_argument("--solve-cells", type=int, default=128)
     ap.add_argument("--solve-degree", type=int, default=2)
     ap.add_argument("--solve-rhs", type=int, default=16)

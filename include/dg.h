@@ -150,6 +150,26 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
  * (fused variant on an operator it does not cover, blocking over the shared-memory limit). */
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block);
 
+/* Result of dg_operator_autotune. ms_* are CUDA-event times of one apply of nrhs
+ * right-hand sides; candidates counts the configurations timed. */
+typedef struct {
+  int32_t variant;
+  int32_t cells_per_block;
+  int32_t faces_per_block;
+  int32_t candidates;
+  double ms_best;
+  double ms_default;
+} dg_tune_result;
+
+/* Measured tuning of the variant and blocking (Sec. 4's autotuning cost function, with
+ * its divide-and-conquer search adapted): the cell-side blocking (cell and
+ * back-projection kernels) and the face blocking are independent subproblems, each timed
+ * per kernel with CUDA events over a few applies and minimised separately, then combined
+ * and compared with the fused variant where it applies; the fastest is kept (as with
+ * dg_operator_set_variant). Allocates and frees two scratch vectors of nrhs x ndofs;
+ * synchronises the stream. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_result *out);
+
 /* Per-quadrature-point diffusion coefficient kappa (scalar problem): device arrays of
  * the operator's precision, kappa_vol [ncell][m^3] (points q0 + m(q1 + m q2)) and
  * kappa_face [ncell][6][m^2] (each cell's own side of faces -x,+x,-y,+y,-z,+z, points

@@ -459,6 +459,115 @@ dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_bl
   return DG_OK;
 }
 
+// Mean per-kernel milliseconds of `reps` applies after `warm` untimed ones.
+static dg_status time_kernels(dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, int warm, int reps,
+                              double ms[3]) {
+  for (int i = 0; i < warm; ++i) {
+    dg_status st = apply_impl(op, x, y, nrhs, s, false);
+    if (st != DG_OK) return st;
+  }
+  const bool prof = op->prof;
+  op->prof = true;
+  op->prof_used = 0;
+  for (int i = 0; i < reps; ++i) {
+    dg_status st = apply_impl(op, x, y, nrhs, s, false);
+    if (st != DG_OK) { op->prof = prof; return st; }
+  }
+  int64_t n = 0;
+  dg_status st = dg_operator_kernel_times(op, ms, &n);
+  op->prof = prof;
+  if (st != DG_OK) return st;
+  for (int k = 0; k < 3; ++k) ms[k] /= (double)(n > 0 ? n : 1);
+  return DG_OK;
+}
+
+dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_result *out) {
+  if (!op || !out || nrhs < 1 || nrhs > op->max_rhs) return fail(DG_ERR_INVALID_ARG);
+  memset(out, 0, sizeof(*out));
+  const size_t es = op->precision == DG_FP64 ? 8 : 4;
+  const size_t bytes = (size_t)nrhs * op->ndofs * es;
+  void *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (x) cudaFree(x);
+    return fail(DG_ERR_OOM);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  dg_status st = DG_OK;
+  const int M = op->m, M2 = M * M, M3 = M * M * M;
+  const int save_v = op->variant, save_c = op->cpb, save_f = op->fpb, save_t = op->tile;
+  double ms[3];
+  auto fits = [&](size_t smem) { return smem + 4096 <= 160 * 1024; };
+  const bool stokes = op->problem == DG_STOKES;
+  do {
+    if (cudaMemsetAsync(x, 0, bytes, s) != cudaSuccess) { st = fail(DG_ERR_CUDA); break; }
+    // default configuration, for reference
+    op->variant = resolve_variant(op, DG_VARIANT_AUTO);
+    default_blocking(op);
+    if ((st = time_kernels(op, x, y, nrhs, s, 2, 5, ms)) != DG_OK) break;
+    out->ms_default = ms[0] + ms[1] + ms[2];
+    // subproblem 1: cells per block of the cell-side kernels; subproblem 2: faces per block
+    op->variant = DG_VARIANT_THREE_KERNEL;
+    default_blocking(op);
+    double best_cell = 1e30, best_face = 1e30;
+    int bc = op->cpb, bf = op->fpb;
+    const int cand_c[] = {1, 2, 4, 8, 16, 32};
+    const int cand_f[] = {2, 4, 8, 16, 32, 64};
+    for (int i = 0; i < 6 && st == DG_OK; ++i) {
+      const int c = cand_c[i];
+      const size_t per = (size_t)(stokes ? 12 : 4) * M3 * es + (stokes ? 42 : 12) * M2 * es;
+      if (!fits(c * per) || c * M3 > 8192) continue;
+      op->cpb = c;
+      if ((st = time_kernels(op, x, y, nrhs, s, 1, 3, ms)) != DG_OK) break;
+      ++out->candidates;
+      if (ms[0] + ms[2] < best_cell) { best_cell = ms[0] + ms[2]; bc = c; }
+    }
+    op->cpb = bc;
+    for (int i = 0; i < 6 && st == DG_OK; ++i) {
+      const int f = cand_f[i];
+      if (!fits((size_t)f * 13 * M2 * es) || f * M2 > 8192) continue;
+      op->fpb = f;
+      if ((st = time_kernels(op, x, y, nrhs, s, 1, 3, ms)) != DG_OK) break;
+      ++out->candidates;
+      if (ms[1] < best_face) { best_face = ms[1]; bf = f; }
+    }
+    if (st != DG_OK) break;
+    op->fpb = bf;
+    if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
+    double best = ms[0] + ms[1] + ms[2];
+    int bv = DG_VARIANT_THREE_KERNEL, btile = save_t;
+    if (fused_ok(op)) {
+      op->variant = DG_VARIANT_FUSED;
+      const int cand_t[] = {1, 2, 4, 8, 16};
+      const int P = op->p;
+      for (int i = 0; i < 5 && st == DG_OK; ++i) {
+        const int t = cand_t[i];
+        if (!fits((size_t)t * (8 * P * P * P + 60 * P * P) * es)) continue;
+        op->tile = t;
+        if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
+        ++out->candidates;
+        if (ms[0] + ms[1] + ms[2] < best) { best = ms[0] + ms[1] + ms[2]; bv = DG_VARIANT_FUSED; btile = t; }
+      }
+    }
+    if (st != DG_OK) break;
+    op->variant = bv;
+    op->cpb = bc;
+    op->fpb = bf;
+    op->tile = btile;
+    out->variant = bv;
+    out->cells_per_block = bv == DG_VARIANT_FUSED ? btile : bc;
+    out->faces_per_block = bv == DG_VARIANT_FUSED ? 0 : bf;
+    out->ms_best = best;
+  } while (0);
+  if (st != DG_OK) {
+    op->variant = save_v; op->cpb = save_c; op->fpb = save_f; op->tile = save_t;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(x);
+  cudaFree(y);
+  return st;
+}
+
 dg_status dg_operator_profile(dg_operator *op, int enable) {
   if (!op) return fail(DG_ERR_INVALID_ARG);
   op->prof = enable != 0;

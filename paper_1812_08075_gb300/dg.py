@@ -29,6 +29,7 @@ EXPORTED = [
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
+    "dg_operator_autotune",
 ]
 
 
@@ -56,6 +57,11 @@ class dg_cg_options(ctypes.Structure):
 class dg_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("breakdown", ctypes.c_int32), ("relres", ctypes.c_double)]
+
+
+class dg_tune_result(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("cells_per_block", ctypes.c_int32), ("faces_per_block", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
 
 
 class dg_stats(ctypes.Structure):
@@ -95,6 +101,7 @@ def lib():
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
         L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
+        L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
                                       ctypes.POINTER(dg_solve_info), vp]
@@ -209,6 +216,12 @@ def dg_operator_set_variant(op: int, variant: int, cells_per_block: int = 0, fac
     _check(lib().dg_operator_set_variant(op, variant, cells_per_block, faces_per_block), "dg_operator_set_variant")
 
 
+def dg_operator_autotune(op: int, nrhs: int, stream: Optional[int]) -> dict:
+    r = dg_tune_result()
+    _check(lib().dg_operator_autotune(op, nrhs, stream, ctypes.byref(r)), "dg_operator_autotune")
+    return {f: getattr(r, f) for f, _ in dg_tune_result._fields_}
+
+
 def dg_operator_profile(op: int, enable: bool):
     _check(lib().dg_operator_profile(op, int(enable)), "dg_operator_profile")
 
@@ -293,6 +306,9 @@ class Operator:
 
     def stats(self) -> dg_stats:
         return dg_operator_stats(self.handle)
+
+    def autotune(self, nrhs: int = 1, stream=None) -> dict:
+        return dg_operator_autotune(self.handle, nrhs, _stream_ptr(stream))
 
     def set_variant(self, variant: int, cells_per_block: int = 0, faces_per_block: int = 0):
         dg_operator_set_variant(self.handle, variant, cells_per_block, faces_per_block)

@@ -198,3 +198,20 @@ def test_config4_fp32_16rhs_full_size_sampled():
     for r in (0, 7, 15):
         ref = orc.apply_cells(b[r].astype(np.float64), cells)
         assert float(np.abs(y[r][cells] - ref).max() / np.abs(ref).max()) <= TOL32
+
+
+@pytest.mark.parametrize("precision,geom", [(dg.DG_FP64, "trilinear"), (dg.DG_FP32, "affine")])
+def test_autotune_keeps_parity(precision, geom):
+    n, k = (6, 5, 7), 3
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    op = dg.Operator(dg.Mesh(*n, verts), k, precision=precision, max_rhs=2)
+    res = op.autotune(nrhs=2)
+    assert res["candidates"] > 3 and res["ms_best"] > 0 and res["ms_best"] <= res["ms_default"] * 1.5
+    st = op.stats()
+    assert st.variant == res["variant"]
+    xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(2)])
+    y = op.apply(torch.from_numpy(xs).to("cuda", op.dtype)).double().cpu().numpy()
+    orc = oracle.Problem(*n, k, vertices=verts)
+    tol = TOL64 if precision == dg.DG_FP64 else TOL32
+    for r in range(2):
+        assert relerr(y[r], orc.apply(xs[r])) <= tol
