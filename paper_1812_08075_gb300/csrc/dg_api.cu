@@ -142,7 +142,8 @@ static void default_blocking(dg_operator *o) {
   const int M3 = o->m * o->m * o->m, M2 = o->m * o->m;
   o->cpb = 256 / M3 > 0 ? 256 / M3 : 1;
   o->fpb = 256 / M2 > 0 ? 256 / M2 : 1;
-  o->tile = o->p <= 3 ? 8 : (o->p == 4 ? 4 : 2);
+  const int lines = o->p * o->p;  // threads per cell of the fused kernel
+  o->tile = 256 / lines > 0 ? 256 / lines : 1;
 }
 
 static bool fused_ok(const dg_operator *o) {
@@ -444,7 +445,8 @@ dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_bl
   const size_t es = op->precision == DG_FP64 ? 8 : 4;
   const int M = op->m, P = op->p;
   if (cells_per_block > 0) {
-    const size_t per = v == DG_VARIANT_FUSED ? (size_t)(8 * P * P * P + 60 * P * P) * es
+    if (v == DG_VARIANT_FUSED && cells_per_block * P * P > 1024) return fail(DG_ERR_UNSUPPORTED);
+    const size_t per = v == DG_VARIANT_FUSED ? (size_t)(4 * P * P * P + 60 * P * P) * es
                                              : (size_t)(op->problem == DG_STOKES ? 12 : 4) * M * M * M * es;
     if (cells_per_block * per + 4096 > 200 * 1024) return fail(DG_ERR_UNSUPPORTED);
   }
@@ -538,11 +540,11 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     int bv = DG_VARIANT_THREE_KERNEL, btile = save_t;
     if (fused_ok(op)) {
       op->variant = DG_VARIANT_FUSED;
-      const int cand_t[] = {1, 2, 4, 8, 16};
+      const int cand_t[] = {2, 4, 8, 16, 32, 64};
       const int P = op->p;
-      for (int i = 0; i < 5 && st == DG_OK; ++i) {
+      for (int i = 0; i < 6 && st == DG_OK; ++i) {
         const int t = cand_t[i];
-        if (!fits((size_t)t * (8 * P * P * P + 60 * P * P) * es)) continue;
+        if (!fits((size_t)t * (4 * P * P * P + 60 * P * P) * es) || t * P * P > 1024) continue;
         op->tile = t;
         if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
         ++out->candidates;

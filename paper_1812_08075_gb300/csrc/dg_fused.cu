@@ -28,36 +28,45 @@ struct FTab {
 template <int P, typename T>
 constexpr size_t fused_smem(int tile) {
   constexpr int P2 = P * P, P3 = P * P * P;
-  return align16<T>(sizeof(FTab<P, T>)) + size_t(tile) * (P3 + 7 * P3 + 36 * P2 + 12 * P2 + 12 * P2) * sizeof(T);
+  return align16<T>(sizeof(FTab<P, T>)) + size_t(tile) * (4 * P3 + 60 * P2) * sizeof(T);
 }
 
+// Thread layout: (k+1)^2 threads per cell; in every pass a thread owns one tensor line
+// of its cell (index l = l1 + P l2 over the two directions the line does not run along),
+// so the contraction along the line runs in registers and the index arithmetic is done
+// once per work item. Affine cells have a diagonal G, so each direction's gradient,
+// pointwise flux and transposed derivative run on lines of that direction alone.
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_fused(const ScalarArgs<T> a, const T *__restrict__ x, T *__restrict__ y,
-                                               int64_t sdof, int tile, int tiles_x, int64_t nitems) {
-  constexpr int M = P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+__global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *__restrict__ x, T *__restrict__ y,
+                                                int64_t sdof, int tile, int tiles_x, int64_t nitems) {
+  constexpr int M = P, L = P * P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &tb = *reinterpret_cast<FTab<P, T> *>(smem_raw);
-  T *X = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(FTab<P, T>)));
-  T *T1 = X + tile * P3, *T2 = T1 + tile * M3, *U = T2 + tile * M3;
-  T *F0 = U + tile * M3, *F1 = F0 + tile * M3, *F2 = F1 + tile * M3, *R = F2 + tile * M3;
-  T *TRo = R + tile * M3;       // own traces [c][lf][qty][M2]
-  T *FR = TRo + tile * 12 * M2;  // own face residuals [c][lf][qty][M2]
-  T *NBq = FR + tile * 12 * M2;  // neighbour traces at the face Gauss points
-  T *NBg = NBq + tile * 12 * M2; // neighbour face data at the GLL nodes [c][lq][P2]
-  T *NB1 = NBg + tile * 12 * P2; // after the first tangential sweep [c][lq][n2][q1]
-  const int tid = threadIdx.x, nt = blockDim.x;
+  T *T1 = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(FTab<P, T>)));
+  T *T2 = T1 + tile * M3, *U = T2 + tile * M3, *R = U + tile * M3;
+  T *TRo = R + tile * M3;         // own traces [c][lf][qty][M2]
+  T *FR = TRo + tile * 12 * M2;   // own face residuals [c][lf][qty][M2]
+  T *NBq = FR + tile * 12 * M2;   // neighbour traces at the face Gauss points [c][lq][M2]
+  T *NBg = NBq + tile * 12 * M2;  // neighbour face data at the GLL nodes [c][lq][P2]
+  T *NB1 = NBg + tile * 12 * P2;  // after the first tangential sweep [c][lq][n2][q1]
+  const int tid = threadIdx.x;
   {
     const DevTables<T> *g = a.tab;
-    for (int i = tid; i < P * P; i += nt) { tb.interp[i] = g->interp[i]; tb.dcol[i] = g->dcol[i]; }
-    for (int i = tid; i < P; i += nt) {
+    for (int i = tid; i < P * P; i += blockDim.x) { tb.interp[i] = g->interp[i]; tb.dcol[i] = g->dcol[i]; }
+    for (int i = tid; i < P; i += blockDim.x) {
       tb.e0[i] = g->e0[i]; tb.e1[i] = g->e1[i]; tb.d0[i] = g->d0[i]; tb.d1[i] = g->d1[i];
       tb.w[i] = g->w[i]; tb.gd0[i] = g->gd0[i]; tb.gd1[i] = g->gd1[i];
     }
   }
   __syncthreads();
+  const int c = tid / L, l = tid - (tid / L) * L;
+  const int l1 = l % P, l2 = l / P;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t ntiles = (int64_t)tiles_x * ny * nz;
   const T sc = a.sc, ss = a.ss, half = T(0.5);
+  T *t1 = T1 + c * M3, *t2 = T2 + c * M3, *u = U + c * M3, *rr = R + c * M3;
+  T *tro = TRo + c * 12 * M2, *fr = FR + c * 12 * M2, *nbq = NBq + c * 12 * M2;
+  T *nbg = NBg + c * 12 * P2, *nb1 = NB1 + c * 12 * P * M;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int rhs = (int)(item / ntiles);
     const int64_t t = item - (int64_t)rhs * ntiles;
@@ -66,221 +75,251 @@ __global__ void __launch_bounds__(256) k_fused(const ScalarArgs<T> a, const T *_
     const int cy = (int)(yz % ny), cz = (int)(yz / ny);
     const int cx0 = tx * tile;
     const int nc = min(tile, nx - cx0);
-    const int64_t c0 = cx0 + (int64_t)nx * (cy + (int64_t)ny * cz);
+    const bool act = c < nc;
+    const int64_t cell = cx0 + c + (int64_t)nx * (cy + (int64_t)ny * cz);
     const T *xr = x + rhs * sdof;
     T *yr = y + rhs * sdof;
-    // ---- gather: own coefficients and the neighbours' face data at the GLL nodes
-    for (int i = tid; i < nc * P3; i += nt) X[i] = xr[c0 * P3 + i];
-    for (int i = tid; i < nc * 12 * P2; i += nt) {
-      const int c = i / (12 * P2), r = i - c * (12 * P2);
-      const int lq = r / P2, nd = r - lq * P2;
-      const int lf = lq >> 1, qty = lq & 1, ax = lf >> 1, side = lf & 1;
-      int cc[3] = {cx0 + c, cy, cz};
-      const int nlim = ax == 0 ? nx : (ax == 1 ? ny : nz);
-      cc[ax] += side ? 1 : -1;
-      T v = T(0);
-      if (cc[ax] >= 0 && cc[ax] < nlim) {
-        const int64_t nb = cc[0] + (int64_t)nx * (cc[1] + (int64_t)ny * cc[2]);
-        const int n1 = nd % P, n2 = nd / P;
-        // DOF of the neighbour at layer j along ax and tangential node (n1, n2)
-        int base, stride;
-        if (ax == 0) { base = P * (n1 + P * n2); stride = 1; }
-        else if (ax == 1) { base = n1 + P2 * n2; stride = P; }
-        else { base = n1 + P * n2; stride = P2; }
-        const T *src = xr + nb * P3 + base;
-        if (qty == 0) {
-          v = src[(side ? 0 : P - 1) * stride];  // the neighbour's face layer (GLL node at the face)
-        } else {
+    const int cc0 = cx0 + c;
+    T uz[M];  // this thread's z-line of Gauss-point values (kept from the axis-2 pass)
+    if (act) {
+      // own x-line (j1, j2) = (l1, l2), interpolated along x in registers
+      T xl[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) xl[j] = xr[cell * P3 + l * P + j];
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        T acc = tb.interp[q * P] * xl[0];
+#pragma unroll
+        for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], xl[j], acc);
+        t1[l * M + q] = acc;
+      }
+      // neighbours' face data at GLL node (n1, n2) = (l1, l2) of each face
+#pragma unroll
+      for (int lf = 0; lf < 6; ++lf) {
+        const int ax = lf >> 1, side = lf & 1;
+        const int coord = ax == 0 ? cc0 : (ax == 1 ? cy : cz);
+        const int nlim = ax == 0 ? nx : (ax == 1 ? ny : nz);
+        const int nbc = coord + (side ? 1 : -1);
+        T vu = T(0), vd = T(0);
+        if (nbc >= 0 && nbc < nlim) {
+          const int64_t step = ax == 0 ? 1 : (ax == 1 ? (int64_t)nx : (int64_t)nx * ny);
+          const int64_t nb = side ? cell + step : cell - step;
+          int base, stride;
+          if (ax == 0) { base = P * (l1 + P * l2); stride = 1; }
+          else if (ax == 1) { base = l1 + P2 * l2; stride = P; }
+          else { base = l1 + P * l2; stride = P2; }
+          const T *src = xr + nb * P3 + base;
           const T *row = side ? tb.gd0 : tb.gd1;
-          v = row[0] * src[0];
+          T line[P];
 #pragma unroll
-          for (int j = 1; j < P; ++j) v = fma(row[j], src[j * stride], v);
+          for (int j = 0; j < P; ++j) line[j] = src[j * stride];
+          vu = line[side ? 0 : P - 1];
+          vd = row[0] * line[0];
+#pragma unroll
+          for (int j = 1; j < P; ++j) vd = fma(row[j], line[j], vd);
+        }
+        nbg[(2 * lf) * P2 + l] = vu;
+        nbg[(2 * lf + 1) * P2 + l] = vd;
+      }
+    }
+    __syncthreads();
+    if (act) {
+      // own axis-1 line (q0, j2) = (l1, l2)
+      T in[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) in[j] = t1[l2 * P * M + j * M + l1];
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        T acc = tb.interp[q * P] * in[0];
+#pragma unroll
+        for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], in[j], acc);
+        t2[l2 * M2 + q * M + l1] = acc;
+      }
+      // neighbour tangential sweep along t1: lines (lq, n2)
+      for (int ln = l; ln < 12 * P; ln += L) {
+        const int lq = ln / P, n2 = ln - (ln / P) * P;
+        const T *src = nbg + lq * P2 + n2 * P;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          T acc = tb.interp[q * P] * src[0];
+#pragma unroll
+          for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], src[j], acc);
+          nb1[lq * P * M + n2 * M + q] = acc;
         }
       }
-      NBg[i] = v;
     }
     __syncthreads();
-    // ---- own axis 0 / neighbour tangential sweep along t1
-    for (int i = tid; i < nc * P2 * M; i += nt) {
-      const int c = i / (P2 * M), r = i - c * (P2 * M);
-      const int q0 = r % M, j12 = r / M;
-      const T *src = X + c * P3 + j12 * P;
-      T acc = tb.interp[q0 * P] * src[0];
+    if (act) {
+      // own axis-2 line (q0, q1) = (l1, l2) -> U, kept in registers
+      T in[P];
 #pragma unroll
-      for (int j = 1; j < P; ++j) acc = fma(tb.interp[q0 * P + j], src[j], acc);
-      T1[c * M3 + r] = acc;
-    }
-    for (int i = tid; i < nc * 12 * P * M; i += nt) {
-      const int c = i / (12 * P * M), r = i - c * (12 * P * M);
-      const int lq = r / (P * M), rr = r - lq * (P * M);
-      const int q1 = rr % M, n2 = rr / M;
-      const T *src = NBg + (c * 12 + lq) * P2 + n2 * P;
-      T acc = tb.interp[q1 * P] * src[0];
+      for (int j = 0; j < P; ++j) in[j] = t2[j * M2 + l2 * M + l1];
 #pragma unroll
-      for (int j = 1; j < P; ++j) acc = fma(tb.interp[q1 * P + j], src[j], acc);
-      NB1[(c * 12 + lq) * P * M + rr] = acc;
-    }
-    __syncthreads();
-    // ---- own axis 1 / neighbour tangential sweep along t2
-    for (int i = tid; i < nc * P * M2; i += nt) {
-      const int c = i / (P * M2), r = i - c * (P * M2);
-      const int q0 = r % M, q1 = (r / M) % M, j2 = r / M2;
-      const T *src = T1 + c * M3 + j2 * (P * M) + q0;
-      T acc = tb.interp[q1 * P] * src[0];
+      for (int q = 0; q < M; ++q) {
+        T acc = tb.interp[q * P] * in[0];
 #pragma unroll
-      for (int j = 1; j < P; ++j) acc = fma(tb.interp[q1 * P + j], src[j * M], acc);
-      T2[c * M3 + r] = acc;
-    }
-    for (int i = tid; i < nc * 12 * M2; i += nt) {
-      const int c = i / (12 * M2), r = i - c * (12 * M2);
-      const int lq = r / M2, qf = r - lq * M2;
-      const int q1 = qf % M, q2 = qf / M;
-      const T *src = NB1 + (c * 12 + lq) * P * M + q1;
-      T acc = tb.interp[q2 * P] * src[0];
-#pragma unroll
-      for (int j = 1; j < P; ++j) acc = fma(tb.interp[q2 * P + j], src[j * M], acc);
-      NBq[i] = acc;
-    }
-    __syncthreads();
-    // ---- own axis 2 -> U
-    for (int i = tid; i < nc * M3; i += nt) {
-      const int c = i / M3, r = i - c * M3;
-      const int q01 = r % M2, q2 = r / M2;
-      const T *src = T2 + c * M3 + q01;
-      T acc = tb.interp[q2 * P] * src[0];
-#pragma unroll
-      for (int j = 1; j < P; ++j) acc = fma(tb.interp[q2 * P + j], src[j * M2], acc);
-      U[i] = acc;
-    }
-    __syncthreads();
-    // ---- own traces; gradient and pointwise volume flux
-    for (int i = tid; i < nc * 12 * M2; i += nt) {
-      const int c = i / (12 * M2), r = i - c * (12 * M2);
-      const int lq = r / M2, qf = r - lq * M2;
-      const int lf = lq >> 1, qty = lq & 1, ax = lf >> 1, side = lf & 1;
-      const int qs = qf % M, qt = qf / M;
-      int base, stride;
-      if (ax == 0) { base = M * (qs + M * qt); stride = 1; }
-      else if (ax == 1) { base = qs + M2 * qt; stride = M; }
-      else { base = qs + M * qt; stride = M2; }
-      const T *row = side ? (qty ? tb.d1 : tb.e1) : (qty ? tb.d0 : tb.e0);
-      const T *src = U + c * M3 + base;
-      T acc = row[0] * src[0];
-#pragma unroll
-      for (int j = 1; j < M; ++j) acc = fma(row[j], src[j * stride], acc);
-      TRo[i] = acc;
-    }
-    for (int i = tid; i < nc * M3; i += nt) {
-      const int c = i / M3, q = i - c * M3;
-      const int q0 = q % M, q1 = (q / M) % M, q2 = q / M2;
-      const T *u = U + c * M3;
-      T g0 = tb.dcol[q0 * M] * u[q1 * M + q2 * M2];
-      T g1 = tb.dcol[q1 * M] * u[q0 + q2 * M2];
-      T g2 = tb.dcol[q2 * M] * u[q0 + q1 * M];
-#pragma unroll
-      for (int k = 1; k < M; ++k) {
-        g0 = fma(tb.dcol[q0 * M + k], u[k + q1 * M + q2 * M2], g0);
-        g1 = fma(tb.dcol[q1 * M + k], u[q0 + k * M + q2 * M2], g1);
-        g2 = fma(tb.dcol[q2 * M + k], u[q0 + q1 * M + k * M2], g2);
+        for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], in[j], acc);
+        uz[q] = acc;
+        u[q * M2 + l2 * M + l1] = acc;
       }
-      const T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
-      F0[i] = (W * a.vol_g[0]) * g0;
-      F1[i] = (W * a.vol_g[1]) * g1;
-      F2[i] = (W * a.vol_g[2]) * g2;
+      // neighbour tangential sweep along t2: lines (lq, q1)
+      for (int ln = l; ln < 12 * M; ln += L) {
+        const int lq = ln / M, q1 = ln - (ln / M) * M;
+        const T *src = nb1 + lq * P * M + q1;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          T acc = tb.interp[q * P] * src[0];
+#pragma unroll
+          for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], src[j * M], acc);
+          nbq[lq * M2 + q1 + M * q] = acc;
+        }
+      }
     }
     __syncthreads();
-    // ---- volume residual at the Gauss points; face terms of each own face
-    for (int i = tid; i < nc * M3; i += nt) {
-      const int c = i / M3, q = i - c * M3;
-      const int q0 = q % M, q1 = (q / M) % M, q2 = q / M2;
-      T acc = ((tb.w[q0] * tb.w[q1] * tb.w[q2]) * a.vol_m) * U[i];
-      const T *f0 = F0 + c * M3, *f1 = F1 + c * M3, *f2 = F2 + c * M3;
+    // direction passes: line values v, gradient g, flux f, transposed derivative, traces
+    // of the two faces normal to the direction (face point = the line's (l1, l2))
+    auto pass = [&](const T *v, T coefd, T massc, T *acc_out, int lf0, bool first, bool mass) {
+      T g[M];
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        acc = fma(tb.dcol[k * M + q0], f0[k + q1 * M + q2 * M2], acc);
-        acc = fma(tb.dcol[k * M + q1], f1[q0 + k * M + q2 * M2], acc);
-        acc = fma(tb.dcol[k * M + q2], f2[q0 + q1 * M + k * M2], acc);
+      for (int q = 0; q < M; ++q) {
+        T s = tb.dcol[q * M] * v[0];
+#pragma unroll
+        for (int r = 1; r < M; ++r) s = fma(tb.dcol[q * M + r], v[r], s);
+        g[q] = s;
       }
-      R[i] = acc;
+      T f[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) f[q] = (coefd * tb.w[q]) * g[q];
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        T s = first ? T(0) : acc_out[q];
+        if (mass) s = fma(massc * tb.w[q], v[q], s);
+#pragma unroll
+        for (int r = 0; r < M; ++r) s = fma(tb.dcol[r * M + q], f[r], s);
+        acc_out[q] = s;
+      }
+      T u0 = tb.e0[0] * v[0], d0 = tb.d0[0] * v[0], u1 = tb.e1[0] * v[0], d1 = tb.d1[0] * v[0];
+#pragma unroll
+      for (int r = 1; r < M; ++r) {
+        u0 = fma(tb.e0[r], v[r], u0); d0 = fma(tb.d0[r], v[r], d0);
+        u1 = fma(tb.e1[r], v[r], u1); d1 = fma(tb.d1[r], v[r], d1);
+      }
+      tro[(2 * lf0) * M2 + l] = u0;
+      tro[(2 * lf0 + 1) * M2 + l] = d0;
+      tro[(2 * lf0 + 2) * M2 + l] = u1;
+      tro[(2 * lf0 + 3) * M2 + l] = d1;
+    };
+    if (act) {  // x-lines (q1, q2) = (l1, l2)
+      T v[M], o[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) v[r] = u[l2 * M2 + l1 * M + r];
+      pass(v, (tb.w[l1] * tb.w[l2]) * a.vol_g[0], T(0), o, 0, true, false);
+#pragma unroll
+      for (int q = 0; q < M; ++q) rr[l2 * M2 + l1 * M + q] = o[q];
     }
-    for (int i = tid; i < nc * 6 * M2; i += nt) {
-      const int c = i / (6 * M2), r = i - c * (6 * M2);
-      const int lf = r / M2, qf = r - lf * M2;
-      const int ax = lf >> 1, side = lf & 1;
-      const int qs = qf % M, qt = qf / M;
+    __syncthreads();
+    if (act) {  // y-lines (q0, q2) = (l1, l2)
+      T v[M], o[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) { v[r] = u[l2 * M2 + r * M + l1]; o[r] = rr[l2 * M2 + r * M + l1]; }
+      pass(v, (tb.w[l1] * tb.w[l2]) * a.vol_g[1], T(0), o, 2, false, false);
+#pragma unroll
+      for (int q = 0; q < M; ++q) rr[l2 * M2 + q * M + l1] = o[q];
+    }
+    __syncthreads();
+    if (act) {  // z-lines (q0, q1) = (l1, l2), with the mass term
+      T o[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) o[r] = rr[r * M2 + l2 * M + l1];
+      pass(uz, (tb.w[l1] * tb.w[l2]) * a.vol_g[2], (tb.w[l1] * tb.w[l2]) * a.vol_m, o, 4, false, true);
+#pragma unroll
+      for (int q = 0; q < M; ++q) rr[q * M2 + l2 * M + l1] = o[q];
+    }
+    __syncthreads();
+    if (act) {  // own-side face terms at face point qf = l of each face
+      const int qs = l1, qt = l2;
       const T W = tb.w[qs] * tb.w[qt];
-      const T bW = W * a.face_b[ax], pw = W * a.face_pw[ax];
-      const int cc = ax == 0 ? cx0 + c : (ax == 1 ? cy : cz);
-      const int nlim = ax == 0 ? nx : (ax == 1 ? ny : nz);
-      const bool bnd = side ? (cc + 1 >= nlim) : (cc == 0);
-      const T uo = TRo[(c * 12 + 2 * lf) * M2 + qf], dno = TRo[(c * 12 + 2 * lf + 1) * M2 + qf];
-      T Rv = T(0), Rn = T(0);
-      if (bnd) {
-        if ((a.dmask >> lf) & 1u) {
-          const T b = side ? bW : -bW;
-          Rv = fma(sc, b * dno, pw * uo);
-          Rn = ss * uo * b;
+#pragma unroll
+      for (int lf = 0; lf < 6; ++lf) {
+        const int ax = lf >> 1, side = lf & 1;
+        const T bW = W * a.face_b[ax], pw = W * a.face_pw[ax];
+        const int coord = ax == 0 ? cc0 : (ax == 1 ? cy : cz);
+        const int nlim = ax == 0 ? nx : (ax == 1 ? ny : nz);
+        const bool bnd = side ? (coord + 1 >= nlim) : (coord == 0);
+        const T uo = tro[(2 * lf) * M2 + l], dno = tro[(2 * lf + 1) * M2 + l];
+        T Rv = T(0), Rn = T(0);
+        if (bnd) {
+          if ((a.dmask >> lf) & 1u) {
+            const T b = side ? bW : -bW;
+            Rv = fma(sc, b * dno, pw * uo);
+            Rn = ss * uo * b;
+          }
+        } else {
+          const T un = nbq[(2 * lf) * M2 + l], dnn = nbq[(2 * lf + 1) * M2 + l];
+          const T J = side ? uo - un : un - uo;
+          const T flux = half * bW * (dno + dnn);
+          const T v = fma(sc, flux, pw * J);
+          Rv = side ? v : -v;
+          Rn = ss * half * J * bW;
         }
-      } else {
-        const T un = NBq[(c * 12 + 2 * lf) * M2 + qf], dnn = NBq[(c * 12 + 2 * lf + 1) * M2 + qf];
-        const T J = side ? uo - un : un - uo;  // u- - u+ with T- the lower cell along ax
-        const T flux = half * bW * (dno + dnn);
-        const T v = fma(sc, flux, pw * J);
-        Rv = side ? v : -v;
-        Rn = ss * half * J * bW;
+        fr[(2 * lf) * M2 + l] = Rv;
+        fr[(2 * lf + 1) * M2 + l] = Rn;
       }
-      FR[(c * 12 + 2 * lf) * M2 + qf] = Rv;
-      FR[(c * 12 + 2 * lf + 1) * M2 + qf] = Rn;
     }
     __syncthreads();
-    // ---- lift the face residuals onto the Gauss points
-    for (int i = tid; i < nc * M3; i += nt) {
-      const int c = i / M3, q = i - c * M3;
-      const int qv[3] = {q % M, (q / M) % M, q / M2};
-      const T *sf = FR + c * 12 * M2;
-      T acc = R[i];
+    if (act) {  // lifting and transposed interpolation along x: line (q1, q2) = (l1, l2)
+      const int q1 = l1, q2 = l2;
+      T v[M];
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        const int qa = qv[ax];
-        const int qf = (ax == 0) ? qv[1] + M * qv[2] : (ax == 1 ? qv[0] + M * qv[2] : qv[0] + M * qv[1]);
-        const T *lo = sf + (2 * ax) * 2 * M2, *hi = sf + (2 * ax + 1) * 2 * M2;
-        acc = fma(tb.e0[qa], lo[qf], acc);
-        acc = fma(tb.d0[qa], lo[M2 + qf], acc);
-        acc = fma(tb.e1[qa], hi[qf], acc);
-        acc = fma(tb.d1[qa], hi[M2 + qf], acc);
+      for (int q0 = 0; q0 < M; ++q0) {
+        T s = rr[q2 * M2 + q1 * M + q0];
+        s = fma(tb.e0[q0], fr[0 * M2 + q1 + M * q2], s);
+        s = fma(tb.d0[q0], fr[1 * M2 + q1 + M * q2], s);
+        s = fma(tb.e1[q0], fr[2 * M2 + q1 + M * q2], s);
+        s = fma(tb.d1[q0], fr[3 * M2 + q1 + M * q2], s);
+        s = fma(tb.e0[q1], fr[4 * M2 + q0 + M * q2], s);
+        s = fma(tb.d0[q1], fr[5 * M2 + q0 + M * q2], s);
+        s = fma(tb.e1[q1], fr[6 * M2 + q0 + M * q2], s);
+        s = fma(tb.d1[q1], fr[7 * M2 + q0 + M * q2], s);
+        s = fma(tb.e0[q2], fr[8 * M2 + q0 + M * q1], s);
+        s = fma(tb.d0[q2], fr[9 * M2 + q0 + M * q1], s);
+        s = fma(tb.e1[q2], fr[10 * M2 + q0 + M * q1], s);
+        s = fma(tb.d1[q2], fr[11 * M2 + q0 + M * q1], s);
+        v[q0] = s;
       }
-      T1[i] = acc;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        T acc = tb.interp[j] * v[0];
+#pragma unroll
+        for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j], v[q], acc);
+        t1[q2 * M * P + q1 * P + j] = acc;
+      }
     }
     __syncthreads();
-    // ---- transposed interpolation back to the GLL coefficients
-    for (int i = tid; i < nc * M2 * P; i += nt) {
-      const int c = i / (M2 * P), r = i - c * (M2 * P);
-      const int j0 = r % P, q12 = r / P;
-      const T *src = T1 + c * M3 + q12 * M;
-      T acc = tb.interp[j0] * src[0];
+    if (act) {  // along y: line (j0, q2) = (l1, l2)
+      T in[M];
 #pragma unroll
-      for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j0], src[q], acc);
-      T2[c * M3 + r] = acc;
+      for (int q = 0; q < M; ++q) in[q] = t1[l2 * M * P + q * P + l1];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        T acc = tb.interp[j] * in[0];
+#pragma unroll
+        for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j], in[q], acc);
+        t2[l2 * P2 + j * P + l1] = acc;
+      }
     }
     __syncthreads();
-    for (int i = tid; i < nc * M * P2; i += nt) {
-      const int c = i / (M * P2), r = i - c * (M * P2);
-      const int j0 = r % P, j1 = (r / P) % P, q2 = r / P2;
-      const T *src = T2 + c * M3 + q2 * (M * P) + j0;
-      T acc = tb.interp[j1] * src[0];
+    if (act) {  // along z: line (j0, j1) = (l1, l2) -> y
+      T in[M];
 #pragma unroll
-      for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j1], src[q * P], acc);
-      T1[c * M3 + r] = acc;
-    }
-    __syncthreads();
-    for (int i = tid; i < nc * P3; i += nt) {
-      const int c = i / P3, r = i - c * P3;
-      const int j01 = r % P2, j2 = r / P2;
-      const T *src = T1 + c * M3 + j01;
-      T acc = tb.interp[j2] * src[0];
+      for (int q = 0; q < M; ++q) in[q] = t2[q * P2 + l2 * P + l1];
 #pragma unroll
-      for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j2], src[q * P2], acc);
-      yr[c0 * P3 + i] = acc;
+      for (int j = 0; j < P; ++j) {
+        T acc = tb.interp[j] * in[0];
+#pragma unroll
+        for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j], in[q], acc);
+        yr[cell * P3 + j * P2 + l2 * P + l1] = acc;
+      }
     }
     __syncthreads();
   }
@@ -294,7 +333,9 @@ cudaError_t run(const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t sdof
   cudaError_t e;
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
     return e;
-  const int threads = 256;
+  constexpr int L = P * P;
+  if (tile < 1 || tile * L > 1024) return cudaErrorInvalidValue;
+  const int threads = tile * L;
   int per_sm = 0, dev = 0, sms = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm)) != cudaSuccess) return e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
