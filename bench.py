@@ -180,6 +180,18 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------- GPU path
 
+def aggregate(ms_local: float, ndofs: int, world: int, dist, device="cuda"):
+    """Whole-job result of a replica run: the slowest rank's milliseconds per step (max
+    over ranks) and value = total DOFs of all ranks / that time."""
+    ms = ms_local
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * ndofs / (ms * 1e-3)
+
+
 def time_applies(op, x, y, steps, warmup, dist, profile=False):
     import torch
     from paper_1812_08075_gb300 import dg
@@ -239,6 +251,52 @@ def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
                     "frac_hbm": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "kernel_ms": kt}
         del op, xx, yy
     return res
+
+
+def stokes_apply(pk, n_cells=32, k=3):
+    """Config 3: DG Stokes block operator, 32^3 affine cells, velocity Q3 / pressure Q2."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    op = dg.Operator(dg.Mesh(n_cells, n_cells, n_cells), k, problem=dg.DG_STOKES, dirichlet_mask=0b111101)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    y = torch.empty_like(x)
+    ms, kt, _ = time_applies(op, x, y, 20, 3, None, profile=True)
+    f = sum(op.stats().flops)
+    return {"workload": f"DG Stokes, {n_cells}^3 affine cells, velocity Q{k} x3 + pressure Q{k - 1}, FP64",
+            "ndofs": op.ndofs, "dof_s": op.ndofs / (ms * 1e-3), "ms": ms, "kernel_ms": kt,
+            "tflops_model": f / (ms * 1e-3) / 1e12, "frac_fp64_peak_model": f / (ms * 1e-3) / 1e12 / pk["fp64_tflops"]}
+
+
+def adjoint_apply(n_cells=64, k=3):
+    """Config 5: adjoint (A^T r and dL/dkappa at every point) on 64^3 trilinear cells, Q3,
+    log-normal kappa; geometry recomputed in the kernels."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    n = (n_cells,) * 3
+    op = dg.Operator(dg.Mesh(*n, wl.perturbed_vertices(*n, seed=1)), k)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    tkv, tkf = torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda()
+    op.set_kappa(tkv, tkf)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 3)).cuda()
+    r = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    y = torch.empty_like(x)
+    gv, gf = torch.empty_like(tkv), torch.empty_like(tkf)
+    ms_fwd, _, _ = time_applies(op, x, y, 20, 3, None, profile=False)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(), gf.data_ptr(),
+                            stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(), gf.data_ptr(),
+                            stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / 20
+    return {"workload": f"{n_cells}^3 trilinear cells, Q{k}, log-normal kappa at every point, FP64",
+            "ndofs": op.ndofs, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
+            "adjoint_dof_s": op.ndofs / (ms_adj * 1e-3), "geometry": "recomputed in the adjoint kernels"}
 
 
 def run_solve(args):
@@ -302,12 +360,7 @@ def run_ours(args, rank, world, dist):
         sampler.start()
     ms, kt, (t0, t1) = time_applies(op, x, y, args.steps, args.warmup, dist, profile=True)
     clocks = sampler.stop(t0, t1) if sampler else None
-    ms_all = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * op.ndofs / (ms_all * 1e-3)
+    ms_all, value = aggregate(ms, op.ndofs, world, dist)
     st = op.stats()
     flops = list(st.flops)
     names = ["k_cell (volume: interpolate, gradient, pointwise, transposed derivative; face traces)",
@@ -362,6 +415,9 @@ def run_ours(args, rank, world, dist):
         out["sweep"] = sweep
     if args.mixed and rank == 0:
         out["mixed_apply"] = mixed_apply(pk, n_cells=args.mixed_cells)
+    if args.sweep and rank == 0:
+        out["stokes"] = stokes_apply(pk)
+        out["adjoint"] = adjoint_apply()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -25,10 +25,25 @@ struct FTab {
   T gd0[P], gd1[P];
 };
 
+// Per-cell shared memory: T1, T2, U (values along the interpolation), then one region
+// used first for the neighbours' face data (NBg, NB1) and later for R, TRo and FR, then
+// NBq. Each array's per-cell stride is padded to an odd number of words so that the
+// stride-(k+1) line accesses of neighbouring cells fall into different banks.
+template <int P>
+struct FLayout {
+  static constexpr int P2 = P * P, P3 = P * P * P;
+  static constexpr int pad(int n) { return n | 1; }
+  static constexpr int sV = pad(P3);                              // T1, T2, U, R
+  static constexpr int sTR = pad(12 * P2);                        // TRo, FR, NBq
+  static constexpr int sNBg = pad(12 * P2), sNB1 = pad(12 * P2);  // M = P
+  static constexpr int late = sV + 2 * sTR, early = sNBg + sNB1;
+  static constexpr int region = late > early ? late : early;
+  static constexpr int per_cell = 3 * sV + region + sTR;
+};
+
 template <int P, typename T>
 constexpr size_t fused_smem(int tile) {
-  constexpr int P2 = P * P, P3 = P * P * P;
-  return align16<T>(sizeof(FTab<P, T>)) + size_t(tile) * (4 * P3 + 60 * P2) * sizeof(T);
+  return align16<T>(sizeof(FTab<P, T>)) + size_t(tile) * FLayout<P>::per_cell * sizeof(T);
 }
 
 // Thread layout: (k+1)^2 threads per cell; in every pass a thread owns one tensor line
@@ -42,13 +57,8 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
   constexpr int M = P, L = P * P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &tb = *reinterpret_cast<FTab<P, T> *>(smem_raw);
-  T *T1 = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(FTab<P, T>)));
-  T *T2 = T1 + tile * M3, *U = T2 + tile * M3, *R = U + tile * M3;
-  T *TRo = R + tile * M3;         // own traces [c][lf][qty][M2]
-  T *FR = TRo + tile * 12 * M2;   // own face residuals [c][lf][qty][M2]
-  T *NBq = FR + tile * 12 * M2;   // neighbour traces at the face Gauss points [c][lq][M2]
-  T *NBg = NBq + tile * 12 * M2;  // neighbour face data at the GLL nodes [c][lq][P2]
-  T *NB1 = NBg + tile * 12 * P2;  // after the first tangential sweep [c][lq][n2][q1]
+  using LY = FLayout<P>;
+  T *base = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(FTab<P, T>)));
   const int tid = threadIdx.x;
   {
     const DevTables<T> *g = a.tab;
@@ -64,9 +74,12 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t ntiles = (int64_t)tiles_x * ny * nz;
   const T sc = a.sc, ss = a.ss, half = T(0.5);
-  T *t1 = T1 + c * M3, *t2 = T2 + c * M3, *u = U + c * M3, *rr = R + c * M3;
-  T *tro = TRo + c * 12 * M2, *fr = FR + c * 12 * M2, *nbq = NBq + c * 12 * M2;
-  T *nbg = NBg + c * 12 * P2, *nb1 = NB1 + c * 12 * P * M;
+  T *cellmem = base + c * LY::per_cell;
+  T *t1 = cellmem, *t2 = t1 + LY::sV, *u = t2 + LY::sV;
+  T *region = u + LY::sV;
+  T *rr = region, *tro = rr + LY::sV, *fr = tro + LY::sTR;  // after the neighbour sweeps
+  T *nbg = region, *nb1 = region + LY::sNBg;                  // before (same memory)
+  T *nbq = region + LY::region;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int rhs = (int)(item / ntiles);
     const int64_t t = item - (int64_t)rhs * ntiles;
