@@ -37,6 +37,10 @@ N_CELLS = 64
 SM_COUNT = 152
 FP64_FLOPS_PER_SM_CLK = 4.0   # 2 DFMA per SM per clock: 1.25 TFLOP/s nominal at 2.07 GHz
 FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FFMA per SM per clock
+# DRAM bytes (read + write) of one k_cell launch from the ncu capture of the 40^3 Q3 case
+# (profiles/scalar_apply_q3_fp64.md: 262.4 MB + 103.9 MB for 64000 cells); the kernel's
+# traffic is proportional to the number of cells, so it scales to a full launch by cells.
+KCELL_Q3_DRAM_BYTES_PER_CELL = (262.393344e6 + 103.932928e6) / 40 ** 3
 
 
 def peaks():
@@ -367,8 +371,12 @@ def run_ours(args, rank, world, dist):
              "k_face (interior and boundary face terms)", "k_back (face lifting and transposed interpolation)"]
     dom = int(np.argmax(kt))
     achieved = flops[dom] / (kt[dom] * 1e-3) / 1e12
+    traffic = (KCELL_Q3_DRAM_BYTES_PER_CELL * op.mesh.ncell) if (k == 3 and dom == 0) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["fp64_tflops"], "traffic": None,
+                "frac": achieved / pk["fp64_tflops"], "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_cell at 40^3 Q3, "
+                                  "scaled by cells to this launch" if traffic else None,
+                "algorithmic_bytes_per_launch": st.bytes[dom],
                 "kernel": names[dom], "kernel_ms": kt[dom],
                 "peak_source": f"FP64 CUDA-core peak derived: {SM_COUNT} SMs x 2 DFMA/clk x 2 flop x "
                                f"{pk['clk_mhz']:.0f} MHz (1.25 TFLOP/s nominal)",
