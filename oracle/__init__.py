@@ -62,6 +62,7 @@ def _load():
         lib.oracle_apply.argtypes = [P, ctypes.c_int, dp, dp]
         lib.oracle_apply_cells.argtypes = [P, ctypes.c_int, dp, ctypes.c_int64, dp, dp, ctypes.c_int]
         lib.oracle_dkappa.argtypes = [P, dp, dp, dp, dp]
+        lib.oracle_rhs.argtypes = [P, dp, dp, dp]
         lib.oracle_assemble_coo.argtypes = [P, ctypes.c_int64, dp, dp, dp]
         lib.oracle_assemble_coo.restype = ctypes.c_int64
         _lib = lib
@@ -174,6 +175,16 @@ class Problem:
         if _load().oracle_dkappa(ctypes.byref(s), _ptr(x), _ptr(r), _ptr(dv), _ptr(df)):
             raise RuntimeError("oracle_dkappa failed")
         return dv, df
+
+    def rhs(self, f_vol=None, g_face=None) -> np.ndarray:
+        """F = (f, v) + theta (g, n.kappa grad v)_D + gamma (g, v)_D (data terms, r = A u - F)."""
+        s, keep = self._struct()
+        fv = None if f_vol is None else np.ascontiguousarray(f_vol, dtype=np.float64)
+        gf = None if g_face is None else np.ascontiguousarray(g_face, dtype=np.float64)
+        F = np.zeros(self.ndofs())
+        if _load().oracle_rhs(ctypes.byref(s), _ptr(fv), _ptr(gf), _ptr(F)):
+            raise RuntimeError("oracle_rhs failed")
+        return F
 
     def assemble(self):
         """Sparse matrix A (scipy CSR) from the local cell and face matrices."""

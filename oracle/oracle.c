@@ -789,3 +789,59 @@ int64_t oracle_assemble_coo(const oracle_problem *pb, int64_t cap, int64_t *rows
   free(e);
   return cnt;
 }
+
+int oracle_rhs(const oracle_problem *pb, const double *f_vol, const double *g_face, double *F) {
+  octx o;
+  if (ctx_init(&o, pb) || pb->problem != 0) return 1;
+  const int P3 = o.P3, m = o.m, m2 = m * m, m3 = m * m * m;
+  static __thread side_data dm;
+  double *phi = malloc(sizeof(double) * P3 * 4);
+  if (!phi) return 2;
+  double (*g)[3] = (double (*)[3])(phi + P3);
+  memset(F, 0, sizeof(double) * o.ncell * P3);
+  if (f_vol) {
+    for (int64_t c = 0; c < o.ncell; ++c) {
+      double V[8][3], J[3][3], Ji[3][3], xi[3];
+      cell_vertices(&o, c, V);
+      for (int q2 = 0; q2 < m; ++q2)
+        for (int q1 = 0; q1 < m; ++q1)
+          for (int q0 = 0; q0 < m; ++q0) {
+            xi[0] = o.s[q0]; xi[1] = o.s[q1]; xi[2] = o.s[q2];
+            map_jacobian(V, xi, J);
+            double dJ = det3(J);
+            inv3(J, dJ, Ji);
+            basis3d(o.p, o.zv, xi, Ji, phi, g);
+            double w = o.w[q0] * o.w[q1] * o.w[q2] * dJ * f_vol[c * m3 + q0 + m * (q1 + m * q2)];
+            for (int i = 0; i < P3; ++i) F[c * P3 + i] += w * phi[i];
+          }
+    }
+  }
+  free(phi);
+  if (g_face) {
+    for (int a = 0; a < 3; ++a) {
+      int t1, t2;
+      tangential_axes(a, &t1, &t2);
+      for (int i2 = 0; i2 < o.n[t2]; ++i2)
+        for (int i1 = 0; i1 < o.n[t1]; ++i1)
+          for (int side = 0; side < 2; ++side) {
+            int cc[3];
+            cc[t1] = i1; cc[t2] = i2; cc[a] = side ? o.n[a] - 1 : 0;
+            if (!((pb->dirichlet_mask >> (2 * a + side)) & 1)) continue;
+            int64_t c = cell_index(&o, cc);
+            int lf = 2 * a + side;
+            double gam = penalty(&o, a, c, side, -1);
+            for (int qt = 0; qt < m; ++qt)
+              for (int qs = 0; qs < m; ++qs) {
+                double n[3], ds;
+                side_eval(&o, c, a, side, qs, qt, NULL, n, &ds, &dm);
+                double W = o.w[qs] * o.w[qt] * ds;
+                double gv = g_face[(c * 6 + lf) * m2 + qs + m * qt];
+                double kap = kappa_face_at(&o, c, lf, qs, qt);
+                for (int i = 0; i < P3; ++i)
+                  F[c * P3 + i] += W * gv * (pb->theta * kap * dm.dn[i] + gam * dm.phi[i]);
+              }
+          }
+    }
+  }
+  return 0;
+}

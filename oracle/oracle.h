@@ -74,6 +74,13 @@ int oracle_apply_cells(const oracle_problem *pb, int transpose, const double *x,
 int oracle_dkappa(const oracle_problem *pb, const double *x, const double *r,
                   double *dk_vol, double *dk_face);
 
+/* Data terms of Eq. (diffreac_weak) moved to the right-hand side (scalar problem):
+ * F_i = (f, phi_i) + theta (g, n.kappa grad phi_i)_{Gamma_D} + gamma_F (g, phi_i)_{Gamma_D},
+ * so that the residual is r = A u - F. f_vol: f at the volume Gauss points [ncell][m^3]
+ * (NULL = 0); g_face: g at each cell's face Gauss points [ncell][6][m^2], read only on
+ * Dirichlet boundary faces (NULL = 0). */
+int oracle_rhs(const oracle_problem *pb, const double *f_vol, const double *g_face, double *F);
+
 /* COO assembly of A from per-cell and per-face local matrices. Returns the number of
  * entries written, or -(needed) if cap is too small, or a value < -(1<<60) on error. */
 int64_t oracle_assemble_coo(const oracle_problem *pb, int64_t cap, int64_t *rows,

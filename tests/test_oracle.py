@@ -403,3 +403,60 @@ def test_dkappa_sum_identity():
     p.kappa_vol, p.kappa_face = np.zeros_like(kv), np.zeros_like(kf)
     base = r @ p.apply(x)
     assert abs(kv @ dv + kf @ df - (full - base)) < 1e-12 * abs(full)
+
+
+# ------------------------------------------------------------ data terms (right-hand side)
+
+def _qp_values(v, n, k, func):
+    """func at the volume Gauss points [ncell][m^3] and at each cell's face Gauss points
+    [ncell][6][m^2] (numpy Gauss nodes, test-side trilinear map)."""
+    m = k + 1
+    t, _ = npleg.leggauss(m)
+    s = (t + 1) / 2
+    ncell = n[0] * n[1] * n[2]
+    fv = np.zeros((ncell, m ** 3))
+    gf = np.zeros((ncell, 6, m * m))
+    for c in range(ncell):
+        V8 = _cell_corners(v, n, c)
+        for q2 in range(m):
+            for q1 in range(m):
+                for q0 in range(m):
+                    fv[c, q0 + m * (q1 + m * q2)] = func(_trilinear_point(V8, (s[q0], s[q1], s[q2])))
+        for lf in range(6):
+            a, side = lf // 2, lf % 2
+            t1, t2 = (1, 2) if a == 0 else ((0, 2) if a == 1 else (0, 1))
+            for qt in range(m):
+                for qs in range(m):
+                    xi = [0.0, 0.0, 0.0]
+                    xi[a], xi[t1], xi[t2] = float(side), s[qs], s[qt]
+                    gf[c, lf, qs + m * qt] = func(_trilinear_point(V8, xi))
+    return fv.ravel(), gf.ravel()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_rhs_paper_manufactured_solution_all_cells_affine(k):
+    # Sec. 5.2's g = |x|^2 with kappa = 1, c = 1, f = -6 + |x|^2 and the Dirichlet data
+    # terms on every boundary face: A g_I = F exactly on every cell of an affine mesh
+    n = (3, 4, 3)
+    v = wl.unit_cube_vertices(*n)
+    p = oracle.Problem(*n, k, c=1.0)
+    u = _interpolate(v, n, k, lambda x: float(x @ x))[:, 0, :].ravel()
+    fv, gf = _qp_values(v, n, k, lambda x: float(x @ x) - 6.0)
+    _, gg = _qp_values(v, n, k, lambda x: float(x @ x))
+    res = p.apply(u) - p.rhs(fv, gg)
+    assert np.abs(res).max() < 1e-12 * np.abs(p.apply(u)).max()
+
+
+@pytest.mark.parametrize("k,theta", [(1, -1.0), (2, 1.0), (2, 0.0)])
+def test_rhs_linear_solution_all_cells_perturbed(k, theta):
+    # u linear, kappa = 1, c = 0, f = 0, g = u: the theta and penalty data terms cancel
+    # their counterparts in A u_I point by point, the rest is integrated exactly
+    n = (3, 3, 4)
+    v = wl.perturbed_vertices(*n, seed=1)
+    p = oracle.Problem(*n, k, vertices=v, c=0.0, theta=theta)
+    lin = lambda x: 0.3 + 1.1 * x[0] - 0.7 * x[1] + 0.4 * x[2]
+    u = _interpolate(v, n, k, lin)[:, 0, :].ravel()
+    _, gg = _qp_values(v, n, k, lin)
+    Au = p.apply(u)
+    res = Au - p.rhs(None, gg)
+    assert np.abs(res).max() < 1e-12 * np.abs(Au).max()
