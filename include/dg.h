@@ -189,6 +189,18 @@ dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void
 dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host, int nrhs,
                         void *stream);
 
+/* Data terms of Eq. (diffreac_weak) moved to the right-hand side (scalar problem):
+ *   F(v) = (f, v) + theta (g, n.kappa grad v)_{Gamma_D} + gamma_F (g, v)_{Gamma_D},
+ * so that the residual of Sec. 2.1 is r(u) = A u - F and the discrete problem A u = F.
+ * f_vol: f at the volume Gauss points, device [ncell][m^3] (points q0 + m(q1 + m q2)),
+ * NULL = 0; g_face: Dirichlet data at each cell's face Gauss points, device
+ * [ncell][6][m^2] (layout of kappa_face), read only on Dirichlet boundary faces, NULL = 0.
+ * kappa as set by dg_operator_set_kappa. F: device [ndofs], overwritten. Uses the
+ * operator's scratch (ordered with applies on one stream). Trilinear geometry is
+ * recomputed from the vertices. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (Stokes),
+ * DG_ERR_CUDA. */
+dg_status dg_rhs(const dg_operator *op, const void *f_vol, const void *g_face, void *F, void *stream);
+
 /* Adjoint of the scalar operator for the loss L = 0.5 ||A(kappa) x - b||^2:
  *   y = A^T r (the transposed apply, r = A x - b supplied by the caller), and, when
  *   x and the output arrays are non-NULL, dkappa_vol[c][q] = r^T dA/dkappa_vol[c][q] x

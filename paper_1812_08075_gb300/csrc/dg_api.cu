@@ -437,6 +437,25 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   return DG_OK;
 }
 
+dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face, void *F, void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !F || F == f_vol || F == g_face || !aligned16(F)) return fail(DG_ERR_INVALID_ARG);
+  if ((f_vol && !aligned16(f_vol)) || (g_face && !aligned16(g_face))) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
+  const bool kap = op->kappa_face != nullptr;
+  cudaError_t e;
+  if (op->precision == DG_FP64)
+    e = launch_rhs<double>(op->p, geo, kap, scalar_args<double>(op, false), op->theta, (const double *)f_vol,
+                           (const double *)g_face, (double *)F, (double *)op->d_rvol, (double *)op->d_fres, op->cpb,
+                           op->fpb, (cudaStream_t)stream);
+  else
+    e = launch_rhs<float>(op->p, geo, kap, scalar_args<float>(op, false), (float)op->theta, (const float *)f_vol,
+                          (const float *)g_face, (float *)F, (float *)op->d_rvol, (float *)op->d_fres, op->cpb,
+                          op->fpb, (cudaStream_t)stream);
+  return e == cudaSuccess ? DG_OK : fail(DG_ERR_CUDA);
+}
+
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block) {
   if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_FUSED || cells_per_block < 0 || faces_per_block < 0)
     return fail(DG_ERR_INVALID_ARG);

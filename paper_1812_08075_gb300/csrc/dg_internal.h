@@ -103,6 +103,12 @@ cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const T *x,
                                 T *fres, int nrhs, int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
 
+// Data terms of the residual (dg_rhs.cu): F from f at the volume points and g at the
+// boundary face points; geo = GEO_AFFINE or GEO_RECOMPUTE.
+template <typename T>
+cudaError_t launch_rhs(int p, int geo, bool kappa, const ScalarArgs<T> &a, T theta, const T *f, const T *g, T *F,
+                       T *rvol, T *fres, int cpb, int fpb, cudaStream_t s);
+
 // Geometry precompute (dg_geometry.cu).
 template <typename T>
 cudaError_t launch_geometry(int m, const ScalarArgs<T> &a, const double *verts, double c,

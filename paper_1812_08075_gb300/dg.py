@@ -29,7 +29,7 @@ EXPORTED = [
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
-    "dg_operator_autotune",
+    "dg_operator_autotune", "dg_rhs",
 ]
 
 
@@ -101,6 +101,7 @@ def lib():
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
         L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
+        L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
@@ -222,6 +223,10 @@ def dg_operator_autotune(op: int, nrhs: int, stream: Optional[int]) -> dict:
     return {f: getattr(r, f) for f, _ in dg_tune_result._fields_}
 
 
+def dg_rhs(op: int, f_ptr: Optional[int], g_ptr: Optional[int], F_ptr: int, stream: Optional[int]):
+    _check(lib().dg_rhs(op, f_ptr, g_ptr, F_ptr, stream), "dg_rhs")
+
+
 def dg_operator_profile(op: int, enable: bool):
     _check(lib().dg_operator_profile(op, int(enable)), "dg_operator_profile")
 
@@ -330,6 +335,14 @@ class Operator:
             y = torch.empty_like(x)
         dg_apply(self.handle, _dev_ptr(x, self.dtype, "x"), _dev_ptr(y, self.dtype, "y"), nrhs, _stream_ptr(stream))
         return y
+
+    def rhs(self, f_vol=None, g_face=None, stream=None):
+        """F = (f, v) + theta (g, n.kappa grad v)_D + gamma (g, v)_D from point values (CUDA tensors)."""
+        import torch
+        F = torch.empty(self.ndofs, dtype=self.dtype, device="cuda")
+        dg_rhs(self.handle, None if f_vol is None else _dev_ptr(f_vol, self.dtype, "f_vol"),
+               None if g_face is None else _dev_ptr(g_face, self.dtype, "g_face"), F.data_ptr(), _stream_ptr(stream))
+        return F
 
     def apply_host(self, x, y, stream=None):
         """y = A x through host buffers (numpy arrays or CPU tensors, ideally pinned)."""
