@@ -241,7 +241,8 @@ typedef struct {
  * together, vectors in the operator's precision, dot products accumulated in FP64,
  * per right-hand-side scalars kept on the device. x (device [nrhs][ndofs]) holds the
  * initial guess and receives the solution; b and x must not alias. info has nrhs
- * entries. Workspace (4 vectors x max_rhs) is allocated on the first call and kept by
+ * entries. When the recursively updated residual meets rtol, the true residual b - A x is
+ * recomputed and the solve continues from it (at most 3 times) where it does not. Workspace (4 vectors x max_rhs) is allocated on the first call and kept by
  * the operator. Synchronises the stream before returning. Errors: DG_ERR_INVALID_ARG,
  * DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NOT_CONVERGED (info filled). */
 dg_status dg_cg_solve(const dg_operator *op, const void *b, void *x, int nrhs,

@@ -108,6 +108,15 @@ __global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
   S->breakdown[r] = 0;
 }
 
+// Restart from a recomputed residual (rz = r.r already reduced): iteration counts kept.
+__global__ void k_restart_scalars(Scalars *S, int nrhs) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  S->rr[r] = S->rz[r];
+  S->active[r] = S->rr[r] > S->tol2[r] ? 1 : 0;
+  S->pAp[r] = 0.0;
+}
+
 __global__ void k_alpha(Scalars *S, int nrhs) {
   const int r = threadIdx.x;
   if (r >= nrhs) return;
@@ -240,8 +249,10 @@ dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Wor
 
 // CG on A x = b for nrhs right-hand sides; x holds the initial guess (x_zero: it is 0
 // and b is the initial residual). Fills info[] and returns the status.
+// verify: on convergence of the recursive residual, recompute r = b - A x and restart
+// (at most 3 times) the right-hand sides whose true residual is still above the target.
 template <typename T>
-dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_options &o, bool x_zero,
+dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_options &o, bool x_zero, bool verify,
                  dg_solve_info *info, cudaStream_t s) {
   const size_t es = sizeof(T);
   dg_status st = ensure_workspace(op, es);
@@ -297,20 +308,39 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   Scalars h;
   int done = 0;
   dg_status result = DG_ERR_NOT_CONVERGED;
-  while (done < o.max_iters) {
-    if (o.use_graph) {
-      SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
-    } else {
-      st = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
-      if (st != DG_OK) return st;
+  for (int restart = 0;; ++restart) {
+    result = DG_ERR_NOT_CONVERGED;
+    while (done < o.max_iters) {
+      if (o.use_graph) {
+        SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
+      } else {
+        st = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
+        if (st != DG_OK) return st;
+      }
+      done += chunk;
+      SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+      SCK(cudaStreamSynchronize(cs));
+      int any = 0;
+      for (int i = 0; i < nrhs; ++i) any |= h.active[i];
+      if (!any) {
+        result = DG_OK;
+        break;
+      }
     }
-    done += chunk;
+    if (!verify || result != DG_OK) break;
+    st = dg_apply_internal(op, x, Ap, nrhs, cs, false);
+    if (st != DG_OK) return st;
+    k_residual<T><<<g, kThreads, 0, cs>>>(b, Ap, r, n);
+    k_init_dir<T><<<g, kThreads, 0, cs>>>(r, p, W->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, cs>>>(W->partial, S->rz, g.x);
+    k_restart_scalars<<<1, 32, 0, cs>>>(S, nrhs);
+    SCK(cudaGetLastError());
     SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
     SCK(cudaStreamSynchronize(cs));
     int any = 0;
     for (int i = 0; i < nrhs; ++i) any |= h.active[i];
-    if (!any) {
-      result = DG_OK;
+    if (!any || restart >= 3 || done >= o.max_iters) {
+      if (any) result = DG_ERR_NOT_CONVERGED;
       break;
     }
   }
@@ -354,8 +384,8 @@ dg_status dg_cg_solve(const dg_operator *op_c, const void *b, void *x, int nrhs,
   if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
   cudaStream_t s = (cudaStream_t)stream;
   dg_status st;
-  if (op->precision == DG_FP64) st = cg_run<double>(op, (const double *)b, (double *)x, nrhs, *opt, false, info, s);
-  else st = cg_run<float>(op, (const float *)b, (float *)x, nrhs, *opt, false, info, s);
+  if (op->precision == DG_FP64) st = cg_run<double>(op, (const double *)b, (double *)x, nrhs, *opt, false, true, info, s);
+  else st = cg_run<float>(op, (const float *)b, (float *)x, nrhs, *opt, false, true, info, s);
   return st == DG_OK ? DG_OK : dg_record_error(st);
 }
 
@@ -420,7 +450,7 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
     }
     k_to_float<<<grid_for((int64_t)nv), kThreads, 0, s>>>(r64, r32, (int64_t)nv);
     SCK(cudaMemsetAsync(d32, 0, nv * sizeof(float), s));
-    st = cg_run<float>(op32, r32, d32, nrhs, *inner, true, sub, s);
+    st = cg_run<float>(op32, r32, d32, nrhs, *inner, true, false, sub, s);
     if (st != DG_OK && st != DG_ERR_NOT_CONVERGED) return dg_record_error(st);
     for (int i = 0; i < nrhs; ++i) inner_iters[i] += sub[i].iters;
     k_add_correction<<<grid_for((int64_t)nv), kThreads, 0, s>>>(x, d32, (int64_t)nv);
