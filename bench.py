@@ -315,7 +315,16 @@ def run_solve(args):
     b = torch.from_numpy(wl.refinement_rhs(n, n, n, (k + 1) ** 3, range(nrhs))).cuda()
     stream = torch.cuda.current_stream().cuda_stream
     out = {"mode": "solve", "workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides",
-           "ndofs": op64.ndofs, "rtol": args.solve_rtol}
+           "ndofs": op64.ndofs, "rtol": args.solve_rtol,
+           "preconditioner": "point Jacobi (diagonal set up outside the timed solves)" if args.precond else "none"}
+    if args.precond:  # set up both diagonals before timing (they are cached by the operators)
+        warm = dg.dg_cg_options(1e-1, 50, 50, 0, args.precond)
+        xz = torch.zeros_like(b)
+        dg.dg_cg_solve(op64.handle, b.data_ptr(), xz.data_ptr(), nrhs, warm, stream)
+        bz = b.float()
+        xz32 = torch.zeros_like(bz)
+        dg.dg_cg_solve(op32.handle, bz.data_ptr(), xz32.data_ptr(), nrhs, warm, stream)
+        del xz, bz, xz32
 
     def check(x):
         r = b - op64.apply(x)
@@ -325,7 +334,7 @@ def run_solve(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     ok, info = dg.dg_refine_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, args.solve_rtol, 30,
-                                  dg.dg_cg_options(args.inner_rtol, 100000, 50, 1, 0), stream)
+                                  dg.dg_cg_options(args.inner_rtol, 100000, 50, 1, args.precond), stream)
     torch.cuda.synchronize()
     t_mixed = time.perf_counter() - t
     out["mixed"] = {"seconds": t_mixed, "converged": ok, "outer": max(i["outer"] for i in info),
@@ -335,7 +344,7 @@ def run_solve(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     ok, info = dg.dg_cg_solve(op64.handle, b.data_ptr(), x.data_ptr(), nrhs,
-                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, 0), stream)
+                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, args.precond), stream)
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t
     out["fp64_cg"] = {"seconds": t64, "converged": ok, "iters_max": max(i["iters"] for i in info),
@@ -459,6 +468,7 @@ def main():
     ap.add_argument("--solve-rtol", type=float, default=1e-10)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--fp64-max-iters", type=int, default=20000)
+    ap.add_argument("--precond", type=int, default=0, help="0: none, 1: point Jacobi (both solvers)")
     args = ap.parse_args()
     global N_CELLS
     N_CELLS = args.cells

@@ -48,6 +48,7 @@ enum { DG_SCALAR = 0, DG_STOKES = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
 enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2 };
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1 };
 
 /* Interior-penalty factor gamma_F (Sec. 5.2).
  *   DG_PEN_CONFIG: gamma_F = alpha * k * (k+1) / h_a with h_a = 1/n_a the nominal cell
@@ -216,14 +217,25 @@ dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, 
  *   rtol       stop a right-hand side when ||b - A x||_2 <= rtol ||b||_2
  *   max_iters  iteration limit (rounded up to a multiple of chunk)
  *   chunk      iterations enqueued between host convergence checks (0 = 25)
- *   use_graph  1: capture one chunk into a CUDA graph on the first call and replay it */
+ *   use_graph  1: capture one chunk into a CUDA graph on the first call and replay it
+ *   precond    DG_PRECOND_NONE, or DG_PRECOND_JACOBI (point Jacobi with diag(A) from
+ *              dg_operator_diagonal, computed on first use and kept by the operator
+ *              until its kappa changes) */
 typedef struct {
   double rtol;
   int32_t max_iters;
   int32_t chunk;
   int32_t use_graph;
-  int32_t reserved;
+  int32_t precond;
 } dg_cg_options;
+
+/* diag(A) of the scalar operator (device [ndofs], operator precision): A is applied to
+ * unit vectors of one cell colour (the 8 parity classes of the cell coordinates, which
+ * share no face) and one local DOF at a time, 8 (k+1)^3 applies in all. Allocates and
+ * frees two vectors; synchronises the stream. The paper has no preconditioner; this is
+ * the point-Jacobi preconditioner of the solves below. Errors: DG_ERR_INVALID_ARG,
+ * DG_ERR_UNSUPPORTED (Stokes), DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_operator_diagonal(const dg_operator *op, void *diag, void *stream);
 
 /* Per right-hand-side result of a solve. iters: CG iterations (summed over the inner
  * solves of a refinement); outer: refinement steps; relres: final ||b - A x|| / ||b||
@@ -236,7 +248,7 @@ typedef struct {
   double relres;
 } dg_solve_info;
 
-/* Batched unpreconditioned conjugate gradients on A x = b (scalar operator, SPD for
+/* Batched (optionally Jacobi-preconditioned) conjugate gradients on A x = b (scalar operator, SPD for
  * theta = -1 with penalty large enough): nrhs (1..max_rhs) independent solves advanced
  * together, vectors in the operator's precision, dot products accumulated in FP64,
  * per right-hand-side scalars kept on the device. x (device [nrhs][ndofs]) holds the

@@ -274,6 +274,10 @@ dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const vo
   if ((kappa_vol && !aligned16(kappa_vol)) || (kappa_face && !aligned16(kappa_face))) return fail(DG_ERR_INVALID_ARG);
   if ((kappa_vol == nullptr) != (kappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  if (op->kappa_vol != kappa_vol || op->kappa_face != kappa_face) {
+    if (op->sv_dinv) cudaFree(op->sv_dinv);  // the Jacobi diagonal depends on kappa
+    op->sv_dinv = nullptr;
+  }
   op->kappa_vol = kappa_vol;
   op->kappa_face = kappa_face;
   if (op->variant == DG_VARIANT_FUSED && !fused_ok(op)) op->variant = DG_VARIANT_THREE_KERNEL;

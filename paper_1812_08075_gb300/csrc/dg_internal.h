@@ -172,6 +172,7 @@ struct dg_operator {
   void *sv_aux = nullptr;   // FP64 vectors of the refinement loop
   size_t sv_aux_bytes = 0;
   void *sv_scal = nullptr;  // per right-hand-side scalars
+  void *sv_dinv = nullptr;  // inverse diagonal of A (Jacobi preconditioner), operator precision
   void *sv_graph = nullptr; // cached CUDA graph of a chunk of CG iterations (cudaGraphExec_t)
   void *sv_graph_key = nullptr;
 };

@@ -29,6 +29,7 @@ constexpr int kMaxBlocks = 152 * 16;  // grid of the vector kernels (fixed per s
 struct Workspace {
   Scalars S;
   double partial[16 * kMaxBlocks];
+  double partial2[16 * kMaxBlocks];
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -48,6 +49,26 @@ __device__ __forceinline__ void block_partial(double v, double *partial) {
     double w = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
     w = warp_sum(w);
     if (threadIdx.x == 0) partial[blockIdx.y * kMaxBlocks + blockIdx.x] = w;
+  }
+  __syncthreads();
+}
+
+// Two block sums at once (same fixed order as block_partial).
+__device__ __forceinline__ void block_partial2(double v, double w, double *pa, double *pb) {
+  __shared__ double part[2][kThreads / 32];
+  v = warp_sum(v);
+  w = warp_sum(w);
+  if ((threadIdx.x & 31) == 0) { part[0][threadIdx.x >> 5] = v; part[1][threadIdx.x >> 5] = w; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool in = threadIdx.x < (blockDim.x >> 5);
+    double a = in ? part[0][threadIdx.x] : 0.0, b = in ? part[1][threadIdx.x] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+      pa[blockIdx.y * kMaxBlocks + blockIdx.x] = a;
+      pb[blockIdx.y * kMaxBlocks + blockIdx.x] = b;
+    }
   }
   __syncthreads();
 }
@@ -84,23 +105,25 @@ __global__ void k_dot(const T *__restrict__ u, const T *__restrict__ v, double *
   block_partial(s, partial);
 }
 
-// Start of CG: z = r (no preconditioner), p = z, partials of r.r.
+// Start of CG: z = D^-1 r (dinv NULL: z = r), p = z, partials of r.z and r.r.
 template <typename T>
-__global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, double *partial, int64_t n) {
+__global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ dinv, double *prz,
+                           double *prr, int64_t n) {
   const int64_t off = (int64_t)blockIdx.y * n;
-  double s = 0.0;
+  double s = 0.0, t = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T v = r[off + i];
-    p[off + i] = v;
-    s = fma((double)v, (double)v, s);
+    const T z = dinv ? dinv[i] * v : v;
+    p[off + i] = z;
+    s = fma((double)v, (double)z, s);
+    t = fma((double)v, (double)v, t);
   }
-  block_partial(s, partial);
+  block_partial2(s, t, prz, prr);
 }
 
 __global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
   const int r = threadIdx.x;
   if (r >= nrhs) return;
-  S->rr[r] = S->rz[r];
   S->tol2[r] = rtol * rtol * S->bb[r];
   S->active[r] = S->rr[r] > S->tol2[r] ? 1 : 0;
   S->pAp[r] = 0.0;
@@ -112,7 +135,6 @@ __global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
 __global__ void k_restart_scalars(Scalars *S, int nrhs) {
   const int r = threadIdx.x;
   if (r >= nrhs) return;
-  S->rr[r] = S->rz[r];
   S->active[r] = S->rr[r] > S->tol2[r] ? 1 : 0;
   S->pAp[r] = 0.0;
 }
@@ -132,24 +154,26 @@ __global__ void k_alpha(Scalars *S, int nrhs) {
   S->alpha[r] = a;
 }
 
-// x += alpha p, r -= alpha Ap, and r.r into rz_new
+// x += alpha p, r -= alpha Ap, and the partials of r.z (z = D^-1 r) and r.r
 template <typename T>
 __global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ Ap,
-                         const Scalars *S, double *partial, int64_t n) {
+                         const T *__restrict__ dinv, const Scalars *S, double *prz, double *prr, int64_t n) {
   const int rhs = blockIdx.y;
   const int64_t off = (int64_t)rhs * n;
   const double ad = S->alpha[rhs];
-  double s = 0.0;
+  double s = 0.0, t = 0.0;
   if (ad != 0.0) {
     const T a = (T)ad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
       x[off + i] = fma(a, p[off + i], x[off + i]);
       const T v = fma(-a, Ap[off + i], r[off + i]);
       r[off + i] = v;
-      s = fma((double)v, (double)v, s);
+      const T z = dinv ? dinv[i] * v : v;
+      s = fma((double)v, (double)z, s);
+      t = fma((double)v, (double)v, t);
     }
   }
-  block_partial(s, partial);
+  block_partial2(s, t, prz, prr);
 }
 
 __global__ void k_beta(Scalars *S, int nrhs) {
@@ -159,7 +183,6 @@ __global__ void k_beta(Scalars *S, int nrhs) {
     S->iters[r] += 1;
     S->beta[r] = S->rz_new[r] / S->rz[r];
     S->rz[r] = S->rz_new[r];
-    S->rr[r] = S->rz_new[r];
     if (S->rr[r] <= S->tol2[r]) S->active[r] = 0;
   } else {
     S->beta[r] = 0.0;
@@ -167,13 +190,40 @@ __global__ void k_beta(Scalars *S, int nrhs) {
 }
 
 template <typename T>
-__global__ void k_direction(T *__restrict__ p, const T *__restrict__ r, const Scalars *S, int64_t n) {
+__global__ void k_direction(T *__restrict__ p, const T *__restrict__ r, const T *__restrict__ dinv, const Scalars *S,
+                            int64_t n) {
   const int rhs = blockIdx.y;
   if (!S->active[rhs]) return;
   const int64_t off = (int64_t)rhs * n;
   const T b = (T)S->beta[rhs];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[off + i] = fma(b, p[off + i], r[off + i]);
+    p[off + i] = fma(b, p[off + i], dinv ? dinv[i] * r[off + i] : r[off + i]);
+}
+
+// Unit vectors of one colour (cells whose coordinate parities give `color`) at local DOF j.
+template <typename T>
+__global__ void k_unit_color(T *__restrict__ e, int64_t ncell, int P3, int nx, int ny, int color, int j) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncell * P3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = i / P3;
+    const int jj = (int)(i - cell * P3);
+    const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((int64_t)nx * ny));
+    const int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+    e[i] = (col == color && jj == j) ? T(1) : T(0);
+  }
+}
+
+// diag[cell][j] = y[cell][j] for the cells of `color` (optionally inverted)
+template <typename T>
+__global__ void k_take_color(const T *__restrict__ y, T *__restrict__ diag, int64_t ncell, int P3, int nx, int ny,
+                             int color, int j, int invert) {
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += (int64_t)gridDim.x * blockDim.x) {
+    const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((int64_t)nx * ny));
+    const int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+    if (col == color) {
+      const T d = y[cell * P3 + j];
+      diag[cell * P3 + j] = invert ? T(1) / d : d;
+    }
+  }
 }
 
 __global__ void k_zero_scalars(Scalars *S) {
@@ -225,10 +275,53 @@ dg_status ensure_workspace(dg_operator *op, size_t es) {
   return DG_OK;
 }
 
+// diag(A) (or its inverse) by applying A to unit vectors of one cell colour and one
+// local DOF at a time: cells of one colour share no face, so (A e)_i = A_ii on them.
+template <typename T>
+dg_status diagonal_by_colours(dg_operator *op, T *out, bool invert, cudaStream_t s) {
+  const int64_t n = op->ndofs;
+  const int P3 = op->p * op->p * op->p;
+  T *e = nullptr, *y = nullptr;
+  if (cudaMalloc(&e, n * sizeof(T)) != cudaSuccess || cudaMalloc(&y, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    if (e) cudaFree(e);
+    return dg_record_error(DG_ERR_OOM);
+  }
+  dg_status st = DG_OK;
+  for (int color = 0; color < 8 && st == DG_OK; ++color)
+    for (int j = 0; j < P3 && st == DG_OK; ++j) {
+      k_unit_color<T><<<grid_for(n), kThreads, 0, s>>>(e, op->ncell, P3, op->nx, op->ny, color, j);
+      st = dg_apply_internal(op, e, y, 1, s, false);
+      if (st != DG_OK) break;
+      k_take_color<T><<<grid_for(op->ncell), kThreads, 0, s>>>(y, out, op->ncell, P3, op->nx, op->ny, color, j,
+                                                                invert ? 1 : 0);
+    }
+  if (st == DG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = dg_record_error(DG_ERR_CUDA);
+  cudaFree(e);
+  cudaFree(y);
+  return st;
+}
+
+template <typename T>
+dg_status ensure_inverse_diagonal(dg_operator *op, cudaStream_t s) {
+  if (op->sv_dinv) return DG_OK;
+  if (cudaMalloc(&op->sv_dinv, op->ndofs * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    op->sv_dinv = nullptr;
+    return dg_record_error(DG_ERR_OOM);
+  }
+  dg_status st = diagonal_by_colours<T>(op, (T *)op->sv_dinv, true, s);
+  if (st != DG_OK) {
+    cudaFree(op->sv_dinv);
+    op->sv_dinv = nullptr;
+  }
+  return st;
+}
+
 // Enqueue `iters` CG iterations on x, r, p, Ap (device, [nrhs][n]) with scalars S.
 template <typename T>
-dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Workspace *W, int nrhs, int iters,
-                             cudaStream_t s) {
+dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, Workspace *W, int nrhs,
+                             int iters, cudaStream_t s) {
   const int64_t n = op->ndofs;
   const dim3 g(grid_for(n), nrhs);
   Scalars *S = &W->S;
@@ -238,10 +331,11 @@ dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, Wor
     k_dot<T><<<g, kThreads, 0, s>>>(p, Ap, W->partial, n);
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
     k_alpha<<<1, 32, 0, s>>>(S, nrhs);
-    k_update<T><<<g, kThreads, 0, s>>>(x, r, p, Ap, S, W->partial, n);
+    k_update<T><<<g, kThreads, 0, s>>>(x, r, p, Ap, dinv, S, W->partial, W->partial2, n);
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz_new, g.x);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
     k_beta<<<1, 32, 0, s>>>(S, nrhs);
-    k_direction<T><<<g, kThreads, 0, s>>>(p, r, S, n);
+    k_direction<T><<<g, kThreads, 0, s>>>(p, r, dinv, S, n);
   }
   SCK(cudaGetLastError());
   return DG_OK;
@@ -259,6 +353,12 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   if (st != DG_OK) return st;
   const int64_t n = op->ndofs;
   T *r = (T *)op->sv_vec, *p = r + op->max_rhs * n, *Ap = p + op->max_rhs * n;
+  const T *dinv = nullptr;
+  if (o.precond == DG_PRECOND_JACOBI) {
+    st = ensure_inverse_diagonal<T>(op, s);
+    if (st != DG_OK) return st;
+    dinv = (const T *)op->sv_dinv;
+  }
   Workspace *W = (Workspace *)op->sv_scal;
   Scalars *S = &W->S;
   const dim3 g(grid_for(n), nrhs);
@@ -272,14 +372,16 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   }
   k_dot<T><<<g, kThreads, 0, s>>>(b, b, W->partial, n);
   k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->bb, g.x);
-  k_init_dir<T><<<g, kThreads, 0, s>>>(r, p, W->partial, n);
+  k_init_dir<T><<<g, kThreads, 0, s>>>(r, p, dinv, W->partial, W->partial2, n);
   k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz, g.x);
+  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
   k_init_scalars<<<1, 32, 0, s>>>(S, nrhs, o.rtol);
   SCK(cudaGetLastError());
   const int chunk = o.chunk > 0 ? o.chunk : 25;
   // the graph depends on the buffers, nrhs and chunk: rebuild when any of them changes
   void *key = (void *)((uintptr_t)x ^ ((uintptr_t)b << 1) ^ ((uintptr_t)op->kappa_vol << 2) ^
-                       ((uintptr_t)op->kappa_face << 3) ^ ((uintptr_t)nrhs << 48) ^ ((uintptr_t)chunk << 56));
+                       ((uintptr_t)op->kappa_face << 3) ^ ((uintptr_t)dinv << 5) ^ ((uintptr_t)nrhs << 48) ^
+                       ((uintptr_t)chunk << 56));
   cudaStream_t cs = s;
   bool own_stream = false;
   if (o.use_graph && s == 0) {  // the legacy stream cannot be captured
@@ -293,7 +395,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     const_cast<dg_operator *>(op)->prof = false;
     cudaGraph_t graph;
     SCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    dg_status est = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
+    dg_status est = enqueue_iterations<T>(op, x, r, p, Ap, dinv, W, nrhs, chunk, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     op->prof = prof;
     if (est != DG_OK) return est;
@@ -314,7 +416,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
       if (o.use_graph) {
         SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
       } else {
-        st = enqueue_iterations<T>(op, x, r, p, Ap, W, nrhs, chunk, cs);
+        st = enqueue_iterations<T>(op, x, r, p, Ap, dinv, W, nrhs, chunk, cs);
         if (st != DG_OK) return st;
       }
       done += chunk;
@@ -331,8 +433,9 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     st = dg_apply_internal(op, x, Ap, nrhs, cs, false);
     if (st != DG_OK) return st;
     k_residual<T><<<g, kThreads, 0, cs>>>(b, Ap, r, n);
-    k_init_dir<T><<<g, kThreads, 0, cs>>>(r, p, W->partial, n);
+    k_init_dir<T><<<g, kThreads, 0, cs>>>(r, p, dinv, W->partial, W->partial2, n);
     k_reduce<<<nrhs, kThreads, 0, cs>>>(W->partial, S->rz, g.x);
+    k_reduce<<<nrhs, kThreads, 0, cs>>>(W->partial2, S->rr, g.x);
     k_restart_scalars<<<1, 32, 0, cs>>>(S, nrhs);
     SCK(cudaGetLastError());
     SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
@@ -370,16 +473,27 @@ void dg_solver_release(dg_operator *op) {
   if (op->sv_vec) cudaFree(op->sv_vec);
   if (op->sv_aux) cudaFree(op->sv_aux);
   if (op->sv_scal) cudaFree(op->sv_scal);
-  op->sv_vec = op->sv_aux = op->sv_scal = nullptr;
+  if (op->sv_dinv) cudaFree(op->sv_dinv);
+  op->sv_vec = op->sv_aux = op->sv_scal = op->sv_dinv = nullptr;
 }
 
 extern "C" {
+
+dg_status dg_operator_diagonal(const dg_operator *op_c, void *diag, void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !diag || ((uintptr_t)diag & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op->precision == DG_FP64) return diagonal_by_colours<double>(op, (double *)diag, false, s);
+  return diagonal_by_colours<float>(op, (float *)diag, false, s);
+}
 
 dg_status dg_cg_solve(const dg_operator *op_c, const void *b, void *x, int nrhs, const dg_cg_options *opt,
                       dg_solve_info *info, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !b || !x || !opt || !info || b == x) return dg_record_error(DG_ERR_INVALID_ARG);
   if (nrhs < 1 || nrhs > op->max_rhs || opt->max_iters < 1 || !(opt->rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (opt->precond != DG_PRECOND_NONE && opt->precond != DG_PRECOND_JACOBI) return dg_record_error(DG_ERR_INVALID_ARG);
   if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
   cudaStream_t s = (cudaStream_t)stream;

@@ -23,13 +23,14 @@ DG_SCALAR, DG_STOKES = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
 DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED = 0, 1, 2
+DG_PRECOND_NONE, DG_PRECOND_JACOBI = 0, 1
 
 EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
-    "dg_operator_autotune", "dg_rhs",
+    "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal",
 ]
 
 
@@ -51,7 +52,7 @@ class dg_coefficients(ctypes.Structure):
 
 class dg_cg_options(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("precond", ctypes.c_int32)]
 
 
 class dg_solve_info(ctypes.Structure):
@@ -102,6 +103,7 @@ def lib():
         L.dg_operator_profile.argtypes = [vp, i32]
         L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
+        L.dg_operator_diagonal.argtypes = [vp, vp, vp]
         L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
@@ -225,6 +227,10 @@ def dg_operator_autotune(op: int, nrhs: int, stream: Optional[int]) -> dict:
 
 def dg_rhs(op: int, f_ptr: Optional[int], g_ptr: Optional[int], F_ptr: int, stream: Optional[int]):
     _check(lib().dg_rhs(op, f_ptr, g_ptr, F_ptr, stream), "dg_rhs")
+
+
+def dg_operator_diagonal(op: int, diag_ptr: int, stream: Optional[int]):
+    _check(lib().dg_operator_diagonal(op, diag_ptr, stream), "dg_operator_diagonal")
 
 
 def dg_operator_profile(op: int, enable: bool):

@@ -109,3 +109,56 @@ def test_refinement_reaches_1e10_with_fp32_inner_solves(geom):
     for r in range(nrhs):
         res = np.linalg.norm(b[r] - orc.apply(xs[r])) / np.linalg.norm(b[r])
         assert res <= 1.05e-10, (r, res)
+
+
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_diagonal_matches_assembled_matrix(geom):
+    n, k = (5, 3, 4), 2
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    op = dg.Operator(dg.Mesh(*n, verts), k)
+    orc = oracle.Problem(*n, k, vertices=verts)
+    if geom == "trilinear":
+        kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+        op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+        orc.kappa_vol, orc.kappa_face = kv, kf
+    d = torch.empty(op.ndofs, dtype=torch.float64, device="cuda")
+    dg.dg_operator_diagonal(op.handle, d.data_ptr(), None)
+    ref = orc.assemble().diagonal()
+    assert np.abs(d.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_jacobi_pcg_matches_scipy_with_fewer_iterations():
+    n, k, nrhs = (8, 6, 7), 2, 2
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=nrhs)
+    b = rhs(n, k, nrhs)
+    bd = torch.from_numpy(b).cuda()
+    its = {}
+    for pre in (dg.DG_PRECOND_NONE, dg.DG_PRECOND_JACOBI):
+        x = torch.zeros_like(bd)
+        o = dg.dg_cg_options(1e-10, 5000, 10, 1, pre)
+        ok, info = dg.dg_cg_solve(op.handle, bd.data_ptr(), x.data_ptr(), nrhs, o, None)
+        assert ok
+        its[pre] = max(i["iters"] for i in info)
+        A = oracle.Problem(*n, k, vertices=verts).assemble()
+        for r in range(nrhs):
+            got = x[r].cpu().numpy()
+            assert np.linalg.norm(b[r] - A @ got) <= 1.01e-10 * np.linalg.norm(b[r])
+    assert its[dg.DG_PRECOND_JACOBI] < its[dg.DG_PRECOND_NONE]
+
+
+def test_refinement_with_jacobi_inner_solves():
+    n, k, nrhs = (8, 8, 8), 2, 4
+    mesh = dg.Mesh(*n)
+    op64 = dg.Operator(mesh, k, max_rhs=nrhs)
+    op32 = dg.Operator(mesh, k, precision=dg.DG_FP32, max_rhs=nrhs)
+    b = rhs(n, k, nrhs)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    ok, info = dg.dg_refine_solve(op64.handle, op32.handle, bd.data_ptr(), x.data_ptr(), nrhs, 1e-10, 20,
+                                  dg.dg_cg_options(1e-4, 5000, 20, 1, dg.DG_PRECOND_JACOBI), None)
+    assert ok, info
+    orc = oracle.Problem(*n, k)
+    xs = x.cpu().numpy()
+    for r in range(nrhs):
+        assert np.linalg.norm(b[r] - orc.apply(xs[r])) <= 1.05e-10 * np.linalg.norm(b[r])
