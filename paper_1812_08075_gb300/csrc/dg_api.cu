@@ -356,10 +356,10 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   const bool kap = op->kappa_vol != nullptr;
   if (op->variant == DG_VARIANT_FUSED && fused_ok(op)) {
     if (op->precision == DG_FP64)
-      e = launch_fused_apply<double>(op->p, scalar_args<double>(op, transpose), (const double *)x, (double *)y, nrhs,
+      e = launch_fused_apply<double>(op->p, scalar_args<double>(op, transpose), op->ht, (const double *)x, (double *)y, nrhs,
                                      sdof, op->tile, s, ev, &op->fused_grid);
     else
-      e = launch_fused_apply<float>(op->p, scalar_args<float>(op, transpose), (const float *)x, (float *)y, nrhs,
+      e = launch_fused_apply<float>(op->p, scalar_args<float>(op, transpose), op->ht, (const float *)x, (float *)y, nrhs,
                                     sdof, op->tile, s, ev, &op->fused_grid);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;

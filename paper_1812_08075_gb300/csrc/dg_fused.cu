@@ -43,7 +43,7 @@ struct FLayout {
 
 template <int P, typename T>
 constexpr size_t fused_smem(int tile) {
-  return align16<T>(sizeof(FTab<P, T>)) + size_t(tile) * FLayout<P>::per_cell * sizeof(T);
+  return size_t(tile) * FLayout<P>::per_cell * sizeof(T);
 }
 
 // Thread layout: (k+1)^2 threads per cell; in every pass a thread owns one tensor line
@@ -51,26 +51,29 @@ constexpr size_t fused_smem(int tile) {
 // so the contraction along the line runs in registers and the index arithmetic is done
 // once per work item. Affine cells have a diagonal G, so each direction's gradient,
 // pointwise flux and transposed derivative run on lines of that direction alone.
+// The reference tables are a by-value kernel parameter: in the line passes every thread
+// of a warp reads the same entry, so they are served from the constant bank as FFMA
+// operands instead of shared-memory loads. Entries indexed by the thread's own line
+// coordinates are copied to registers once.
 template <int P, typename T>
-__global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *__restrict__ x, T *__restrict__ y,
-                                                int64_t sdof, int tile, int tiles_x, int64_t nitems) {
+__global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTab<P, T> tb, const T *__restrict__ x,
+                                                T *__restrict__ y, int64_t sdof, int tile, int tiles_x,
+                                                int64_t nitems) {
   constexpr int M = P, L = P * P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto &tb = *reinterpret_cast<FTab<P, T> *>(smem_raw);
   using LY = FLayout<P>;
-  T *base = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(FTab<P, T>)));
+  T *base = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
-  {
-    const DevTables<T> *g = a.tab;
-    for (int i = tid; i < P * P; i += blockDim.x) { tb.interp[i] = g->interp[i]; tb.dcol[i] = g->dcol[i]; }
-    for (int i = tid; i < P; i += blockDim.x) {
-      tb.e0[i] = g->e0[i]; tb.e1[i] = g->e1[i]; tb.d0[i] = g->d0[i]; tb.d1[i] = g->d1[i];
-      tb.w[i] = g->w[i]; tb.gd0[i] = g->gd0[i]; tb.gd1[i] = g->gd1[i];
-    }
-  }
-  __syncthreads();
   const int c = tid / L, l = tid - (tid / L) * L;
   const int l1 = l % P, l2 = l / P;
+  // thread-dependent table entries
+  T w1 = tb.w[0], w2 = tb.w[0], e0_1 = tb.e0[0], d0_1 = tb.d0[0], e1_1 = tb.e1[0], d1_1 = tb.d1[0];
+  T e0_2 = tb.e0[0], d0_2 = tb.d0[0], e1_2 = tb.e1[0], d1_2 = tb.d1[0];
+#pragma unroll
+  for (int i = 1; i < P; ++i) {
+    if (l1 == i) { w1 = tb.w[i]; e0_1 = tb.e0[i]; d0_1 = tb.d0[i]; e1_1 = tb.e1[i]; d1_1 = tb.d1[i]; }
+    if (l2 == i) { w2 = tb.w[i]; e0_2 = tb.e0[i]; d0_2 = tb.d0[i]; e1_2 = tb.e1[i]; d1_2 = tb.d1[i]; }
+  }
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t ntiles = (int64_t)tiles_x * ny * nz;
   const T sc = a.sc, ss = a.ss, half = T(0.5);
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
       T v[M], o[M];
 #pragma unroll
       for (int r = 0; r < M; ++r) v[r] = u[l2 * M2 + l1 * M + r];
-      pass(v, (tb.w[l1] * tb.w[l2]) * a.vol_g[0], T(0), o, 0, true, false);
+      pass(v, (w1 * w2) * a.vol_g[0], T(0), o, 0, true, false);
 #pragma unroll
       for (int q = 0; q < M; ++q) rr[l2 * M2 + l1 * M + q] = o[q];
     }
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
       T v[M], o[M];
 #pragma unroll
       for (int r = 0; r < M; ++r) { v[r] = u[l2 * M2 + r * M + l1]; o[r] = rr[l2 * M2 + r * M + l1]; }
-      pass(v, (tb.w[l1] * tb.w[l2]) * a.vol_g[1], T(0), o, 2, false, false);
+      pass(v, (w1 * w2) * a.vol_g[1], T(0), o, 2, false, false);
 #pragma unroll
       for (int q = 0; q < M; ++q) rr[l2 * M2 + q * M + l1] = o[q];
     }
@@ -244,14 +247,13 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
       T o[M];
 #pragma unroll
       for (int r = 0; r < M; ++r) o[r] = rr[r * M2 + l2 * M + l1];
-      pass(uz, (tb.w[l1] * tb.w[l2]) * a.vol_g[2], (tb.w[l1] * tb.w[l2]) * a.vol_m, o, 4, false, true);
+      pass(uz, (w1 * w2) * a.vol_g[2], (w1 * w2) * a.vol_m, o, 4, false, true);
 #pragma unroll
       for (int q = 0; q < M; ++q) rr[q * M2 + l2 * M + l1] = o[q];
     }
     __syncthreads();
     if (act) {  // own-side face terms at face point qf = l of each face
-      const int qs = l1, qt = l2;
-      const T W = tb.w[qs] * tb.w[qt];
+      const T W = w1 * w2;
 #pragma unroll
       for (int lf = 0; lf < 6; ++lf) {
         const int ax = lf >> 1, side = lf & 1;
@@ -290,14 +292,14 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
         s = fma(tb.d0[q0], fr[1 * M2 + q1 + M * q2], s);
         s = fma(tb.e1[q0], fr[2 * M2 + q1 + M * q2], s);
         s = fma(tb.d1[q0], fr[3 * M2 + q1 + M * q2], s);
-        s = fma(tb.e0[q1], fr[4 * M2 + q0 + M * q2], s);
-        s = fma(tb.d0[q1], fr[5 * M2 + q0 + M * q2], s);
-        s = fma(tb.e1[q1], fr[6 * M2 + q0 + M * q2], s);
-        s = fma(tb.d1[q1], fr[7 * M2 + q0 + M * q2], s);
-        s = fma(tb.e0[q2], fr[8 * M2 + q0 + M * q1], s);
-        s = fma(tb.d0[q2], fr[9 * M2 + q0 + M * q1], s);
-        s = fma(tb.e1[q2], fr[10 * M2 + q0 + M * q1], s);
-        s = fma(tb.d1[q2], fr[11 * M2 + q0 + M * q1], s);
+        s = fma(e0_1, fr[4 * M2 + q0 + M * q2], s);
+        s = fma(d0_1, fr[5 * M2 + q0 + M * q2], s);
+        s = fma(e1_1, fr[6 * M2 + q0 + M * q2], s);
+        s = fma(d1_1, fr[7 * M2 + q0 + M * q2], s);
+        s = fma(e0_2, fr[8 * M2 + q0 + M * q1], s);
+        s = fma(d0_2, fr[9 * M2 + q0 + M * q1], s);
+        s = fma(e1_2, fr[10 * M2 + q0 + M * q1], s);
+        s = fma(d1_2, fr[11 * M2 + q0 + M * q1], s);
         v[q0] = s;
       }
 #pragma unroll
@@ -339,8 +341,14 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const T *
 }
 
 template <int P, typename T>
-cudaError_t run(const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t sdof, int tile, cudaStream_t s,
-                const cudaEvent_t *ev, int *grid_out) {
+cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof, int tile,
+                cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+  FTab<P, T> tb;
+  for (int i = 0; i < P * P; ++i) { tb.interp[i] = (T)ht.interp[i]; tb.dcol[i] = (T)ht.dcol[i]; }
+  for (int i = 0; i < P; ++i) {
+    tb.e0[i] = (T)ht.e0[i]; tb.e1[i] = (T)ht.e1[i]; tb.d0[i] = (T)ht.d0[i]; tb.d1[i] = (T)ht.d1[i];
+    tb.w[i] = (T)ht.gauss_w[i]; tb.gd0[i] = (T)ht.gd0[i]; tb.gd1[i] = (T)ht.gd1[i];
+  }
   const size_t sm = fused_smem<P, T>(tile);
   auto k = k_fused<P, T>;
   cudaError_t e;
@@ -359,7 +367,7 @@ cudaError_t run(const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t sdof
   if (grid > nitems) grid = nitems;
   if (grid_out) *grid_out = (int)grid;
   if (ev) cudaEventRecord(ev[0], s);
-  k<<<(unsigned)grid, threads, sm, s>>>(a, x, y, sdof, tile, tiles_x, nitems);
+  k<<<(unsigned)grid, threads, sm, s>>>(a, tb, x, y, sdof, tile, tiles_x, nitems);
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
@@ -371,19 +379,20 @@ cudaError_t run(const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t sdof
 }  // namespace dgf
 
 template <typename T>
-cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t sdof, int tile,
-                               cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
+                               int64_t sdof, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+  if (ht.m != p || ht.p != p) return cudaErrorInvalidValue;
   switch (p) {
-    case 2: return dgf::run<2, T>(a, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 3: return dgf::run<3, T>(a, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 4: return dgf::run<4, T>(a, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 5: return dgf::run<5, T>(a, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 6: return dgf::run<6, T>(a, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 2: return dgf::run<2, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 3: return dgf::run<3, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 4: return dgf::run<4, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 5: return dgf::run<5, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 6: return dgf::run<6, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template cudaError_t launch_fused_apply<float>(int, const ScalarArgs<float> &, const float *, float *, int, int64_t,
-                                               int, cudaStream_t, const cudaEvent_t *, int *);
-template cudaError_t launch_fused_apply<double>(int, const ScalarArgs<double> &, const double *, double *, int,
-                                                int64_t, int, cudaStream_t, const cudaEvent_t *, int *);
+template cudaError_t launch_fused_apply<float>(int, const ScalarArgs<float> &, const HostTables &, const float *,
+                                               float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *);
+template cudaError_t launch_fused_apply<double>(int, const ScalarArgs<double> &, const HostTables &, const double *,
+                                                double *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *);

@@ -93,8 +93,8 @@ cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<d
 // blocks that loop over (right-hand side, row of cells) work items; each cell gathers its
 // neighbours' face data from their coefficients, so no scratch memory is used.
 template <typename T>
-cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const T *x, T *y, int nrhs, int64_t stride_dofs,
-                               int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out);
+cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
+                               int64_t stride_dofs, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out);
 
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
