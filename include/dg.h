@@ -123,8 +123,9 @@ dg_status dg_mesh_destroy(dg_mesh *mesh);
 
 /* Operator y = A x of Eq. (diffreac_weak) or Eq. (stokes_weak) without the data terms
  * (the Jacobian action for a linear problem, Sec. 2.1), degree k (1..5 scalar, 2..5
- * Stokes), quad_points_1d Gauss-Legendre points per direction (0 = k+1; only k+1 is
- * built). Uploads reference tables, precomputes geometry if stored, allocates scratch
+ * Stokes), quad_points_1d Gauss-Legendre points per direction (0 = k+1; k+2 over-
+ * integrates the scalar operator on the three-kernel path; the fused variant, Stokes,
+ * the adjoint and dg_rhs need k+1). Uploads reference tables, precomputes geometry if stored, allocates scratch
  * for max_rhs right-hand sides. Synchronous. Errors: DG_ERR_INVALID_ARG,
  * DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d,

@@ -147,7 +147,7 @@ static void default_blocking(dg_operator *o) {
 }
 
 static bool fused_ok(const dg_operator *o) {
-  return o->problem == DG_SCALAR && o->geo == GEO_AFFINE && o->kappa_vol == nullptr;
+  return o->problem == DG_SCALAR && o->geo == GEO_AFFINE && o->kappa_vol == nullptr && o->m == o->p;
 }
 
 static int resolve_variant(const dg_operator *o, int v) {
@@ -165,7 +165,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   if (degree > 5) return fail(DG_ERR_UNSUPPORTED);
   const int m = quad_points_1d == 0 ? degree + 1 : quad_points_1d;
   if (m < degree + 1) return fail(DG_ERR_INVALID_ARG);
-  if (m != degree + 1) return fail(DG_ERR_UNSUPPORTED);
+  if (m > degree + 2 || (m != degree + 1 && co->problem == DG_STOKES)) return fail(DG_ERR_UNSUPPORTED);
   if (co->problem != DG_SCALAR && co->problem != DG_STOKES) return fail(DG_ERR_INVALID_ARG);
   if (co->problem == DG_STOKES && (degree < 2 || !mesh->affine)) return fail(DG_ERR_UNSUPPORTED);
   if (co->precision != DG_FP64 && co->precision != DG_FP32) return fail(DG_ERR_INVALID_ARG);
@@ -422,7 +422,7 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   if (!aligned16(r) || !aligned16(y) || (x && !aligned16(x))) return fail(DG_ERR_INVALID_ARG);
   if ((dkappa_vol == nullptr) != (dkappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (dkappa_vol && (!x || !aligned16(dkappa_vol) || !aligned16(dkappa_face))) return fail(DG_ERR_INVALID_ARG);
-  if (op->problem != DG_SCALAR || op->precision != DG_FP64) return fail(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || op->precision != DG_FP64 || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
   const int M2 = op->m * op->m;
   if (dkappa_vol && !op->d_tr2) {
     if (cudaMalloc(&op->d_tr2, (size_t)op->ncell * 12 * M2 * sizeof(double)) != cudaSuccess) {
@@ -445,7 +445,7 @@ dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face,
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !F || F == f_vol || F == g_face || !aligned16(F)) return fail(DG_ERR_INVALID_ARG);
   if ((f_vol && !aligned16(f_vol)) || (g_face && !aligned16(g_face))) return fail(DG_ERR_INVALID_ARG);
-  if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
   const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
   const bool kap = op->kappa_face != nullptr;
   cudaError_t e;

@@ -6,7 +6,7 @@
 #include "../../include/dg.h"
 
 #define DG_MAXP 6  // basis points per direction (degree <= 5)
-#define DG_MAXM 6  // Gauss points per direction
+#define DG_MAXM 7  // Gauss points per direction (k+1, or k+2 for over-integration)
 
 // Reference-element tables in the operator's precision, uploaded once per operator.
 // Internally the kernels work on values at the Gauss points (a collocated Lagrange

@@ -15,11 +15,10 @@ inline int threads_for(int work) {
   return t < 64 ? 64 : (t > 256 ? 256 : t);
 }
 
-template <int P, typename T, int GEO, bool KAPPA>
+template <int P, int M, typename T, int GEO, bool KAPPA>
 static cudaError_t apply_pmk(const ScalarArgs<T> &a, const T *x, T *y, T *rvol, T *traces, T *fres,
                              int nrhs, int64_t sdof, int64_t srv, int64_t str, int cpb, int fpb,
                              cudaStream_t s, const cudaEvent_t *ev) {
-  constexpr int M = P;
   constexpr int M2 = M * M, M3 = M * M * M;
   cudaError_t e;
   {
@@ -53,17 +52,17 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const T *x, T *y, T *rvol, 
   return cudaSuccess;
 }
 
-template <int P, typename T>
+template <int P, int M, typename T>
 static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const T *x, T *y, T *rvol,
                            T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
                            int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev) {
   if (geo == GEO_AFFINE) {
-    if (kappa) return apply_pmk<P, T, GEO_AFFINE, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
-    return apply_pmk<P, T, GEO_AFFINE, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
+    if (kappa) return apply_pmk<P, M, T, GEO_AFFINE, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
+    return apply_pmk<P, M, T, GEO_AFFINE, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
   }
   if (geo == GEO_STORED) {
-    if (kappa) return apply_pmk<P, T, GEO_STORED, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
-    return apply_pmk<P, T, GEO_STORED, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
+    if (kappa) return apply_pmk<P, M, T, GEO_STORED, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
+    return apply_pmk<P, M, T, GEO_STORED, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev);
   }
   return cudaErrorInvalidValue;
 }
@@ -75,13 +74,12 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
                                 T *rvol, T *traces, T *fres, int nrhs, int64_t stride_dofs,
                                 int64_t stride_rvol, int64_t stride_tr, int cpb, int fpb, cudaStream_t s,
                                 const cudaEvent_t *ev) {
-  if (m != p) return cudaErrorInvalidValue;
-  switch (p) {
-    case 2: return dgk::apply_p<2, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, stride_tr, cpb, fpb, s, ev);
-    case 3: return dgk::apply_p<3, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, stride_tr, cpb, fpb, s, ev);
-    case 4: return dgk::apply_p<4, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, stride_tr, cpb, fpb, s, ev);
-    case 5: return dgk::apply_p<5, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, stride_tr, cpb, fpb, s, ev);
-    case 6: return dgk::apply_p<6, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, stride_tr, cpb, fpb, s, ev);
-    default: return cudaErrorInvalidValue;
-  }
+#define DGK_CASE(PP, MM)                                                                                      \
+  if (p == PP && m == MM)                                                                                     \
+    return dgk::apply_p<PP, MM, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, \
+                                   stride_tr, cpb, fpb, s, ev);
+  DGK_CASE(2, 2) DGK_CASE(3, 3) DGK_CASE(4, 4) DGK_CASE(5, 5) DGK_CASE(6, 6)
+  DGK_CASE(2, 3) DGK_CASE(3, 4) DGK_CASE(4, 5) DGK_CASE(5, 6) DGK_CASE(6, 7)
+#undef DGK_CASE
+  return cudaErrorInvalidValue;
 }

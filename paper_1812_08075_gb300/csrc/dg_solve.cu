@@ -168,12 +168,15 @@ __global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restri
       x[off + i] = fma(a, p[off + i], x[off + i]);
       const T v = fma(-a, Ap[off + i], r[off + i]);
       r[off + i] = v;
-      const T z = dinv ? dinv[i] * v : v;
-      s = fma((double)v, (double)z, s);
-      t = fma((double)v, (double)v, t);
+      if (dinv) {
+        s = fma((double)v, (double)(dinv[i] * v), s);
+        t = fma((double)v, (double)v, t);
+      } else {  // r.z = r.r: one FP64 accumulation per element (FP64 is scarce on this part)
+        s = fma((double)v, (double)v, s);
+      }
     }
   }
-  block_partial2(s, t, prz, prr);
+  block_partial2(s, dinv ? t : s, prz, prr);
 }
 
 __global__ void k_beta(Scalars *S, int nrhs) {

@@ -215,3 +215,21 @@ def test_autotune_keeps_parity(precision, geom):
     tol = TOL64 if precision == dg.DG_FP64 else TOL32
     for r in range(2):
         assert relerr(y[r], orc.apply(xs[r])) <= tol
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_overintegration_k_plus_2_points(k, geom):
+    n = (4, 3, 5)
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    m = k + 2
+    op = dg.Operator(dg.Mesh(*n, verts), k, quad_points=m)
+    orc = oracle.Problem(*n, k, m=m, vertices=verts)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, m, seed=2)
+    op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    orc.kappa_vol, orc.kappa_face = kv, kf
+    x = wl.uniform_vector(op.ndofs, 0)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert relerr(y, orc.apply(x)) <= TOL64
+    with pytest.raises(dg.DGError):
+        op.set_variant(dg.DG_VARIANT_FUSED)
