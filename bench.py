@@ -462,7 +462,9 @@ def main():
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=64, help="cells per axis (64 is the benchmark workload)")
-    ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve", "extras"])
+    ap.add_argument("--stokes-cells", type=int, default=32)
+    ap.add_argument("--adjoint-cells", type=int, default=64)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", default=True)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
     ap.add_argument("--mixed-cells", type=int, default=128, help="cells per axis of the mixed-precision apply")
@@ -489,6 +491,13 @@ def main():
     if args.mode == "solve":
         if rank == 0:
             run_solve(args)
+    elif args.mode == "extras":
+        if rank == 0:
+            import torch
+            from paper_1812_08075_gb300 import build as libbuild
+            libbuild.build()
+            print(json.dumps({"mode": "extras", "stokes": stokes_apply(peaks(), n_cells=args.stokes_cells),
+                              "adjoint": adjoint_apply(n_cells=args.adjoint_cells)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
