@@ -469,7 +469,7 @@ dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_bl
   const int M = op->m, P = op->p;
   if (cells_per_block > 0) {
     if (v == DG_VARIANT_FUSED && cells_per_block * P * P > 1024) return fail(DG_ERR_UNSUPPORTED);
-    const size_t per = v == DG_VARIANT_FUSED ? (size_t)(4 * P * P * P + 40 * P * P) * es
+    const size_t per = v == DG_VARIANT_FUSED ? (size_t)(6 * P * P * P + 40 * P * P) * es
                                              : (size_t)(op->problem == DG_STOKES ? 12 : 4) * M * M * M * es;
     if (cells_per_block * per + 4096 > 200 * 1024) return fail(DG_ERR_UNSUPPORTED);
   }
@@ -567,7 +567,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
       const int P = op->p;
       for (int i = 0; i < 6 && st == DG_OK; ++i) {
         const int t = cand_t[i];
-        if (!fits((size_t)t * (4 * P * P * P + 40 * P * P) * es) || t * P * P > 1024) continue;
+        if (!fits((size_t)t * (6 * P * P * P + 40 * P * P) * es) || t * P * P > 1024) continue;
         op->tile = t;
         if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
         ++out->candidates;

@@ -36,7 +36,7 @@ struct FLayout {
   static constexpr int sV = pad(P3);                              // T1, T2, U, R
   static constexpr int sTR = pad(12 * P2);                        // TRo, FR, NBq
   static constexpr int sNBg = pad(12 * P2), sNB1 = pad(12 * P2);  // M = P
-  static constexpr int late = sV + 2 * sTR, early = sNBg + sNB1;
+  static constexpr int late = 3 * sV + 2 * sTR, early = sNBg + sNB1;  // R per direction
   static constexpr int region = late > early ? late : early;
   static constexpr int per_cell = 3 * sV + region + sTR;
 };
@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
   T *cellmem = base + c * LY::per_cell;
   T *t1 = cellmem, *t2 = t1 + LY::sV, *u = t2 + LY::sV;
   T *region = u + LY::sV;
-  T *rr = region, *tro = rr + LY::sV, *fr = tro + LY::sTR;  // after the neighbour sweeps
+  T *rr = region, *ry = rr + LY::sV, *rz = ry + LY::sV;     // after the neighbour sweeps
+  T *tro = rz + LY::sV, *fr = tro + LY::sTR;
   T *nbg = region, *nb1 = region + LY::sNBg;                  // before (same memory)
   T *nbq = region + LY::region;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
       tro[(2 * lf0 + 2) * M2 + l] = u1;
       tro[(2 * lf0 + 3) * M2 + l] = d1;
     };
+    // the three passes are independent: each writes its own residual array
     if (act) {  // x-lines (q1, q2) = (l1, l2)
       T v[M], o[M];
 #pragma unroll
@@ -232,24 +234,16 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
       pass(v, (w1 * w2) * a.vol_g[0], T(0), o, 0, true, false);
 #pragma unroll
       for (int q = 0; q < M; ++q) rr[l2 * M2 + l1 * M + q] = o[q];
-    }
-    __syncthreads();
-    if (act) {  // y-lines (q0, q2) = (l1, l2)
-      T v[M], o[M];
+      // y-lines (q0, q2) = (l1, l2)
 #pragma unroll
-      for (int r = 0; r < M; ++r) { v[r] = u[l2 * M2 + r * M + l1]; o[r] = rr[l2 * M2 + r * M + l1]; }
-      pass(v, (w1 * w2) * a.vol_g[1], T(0), o, 2, false, false);
+      for (int r = 0; r < M; ++r) v[r] = u[l2 * M2 + r * M + l1];
+      pass(v, (w1 * w2) * a.vol_g[1], T(0), o, 2, true, false);
 #pragma unroll
-      for (int q = 0; q < M; ++q) rr[l2 * M2 + q * M + l1] = o[q];
-    }
-    __syncthreads();
-    if (act) {  // z-lines (q0, q1) = (l1, l2), with the mass term
-      T o[M];
+      for (int q = 0; q < M; ++q) ry[l2 * M2 + q * M + l1] = o[q];
+      // z-lines (q0, q1) = (l1, l2), with the mass term
+      pass(uz, (w1 * w2) * a.vol_g[2], (w1 * w2) * a.vol_m, o, 4, true, true);
 #pragma unroll
-      for (int r = 0; r < M; ++r) o[r] = rr[r * M2 + l2 * M + l1];
-      pass(uz, (w1 * w2) * a.vol_g[2], (w1 * w2) * a.vol_m, o, 4, false, true);
-#pragma unroll
-      for (int q = 0; q < M; ++q) rr[q * M2 + l2 * M + l1] = o[q];
+      for (int q = 0; q < M; ++q) rz[q * M2 + l2 * M + l1] = o[q];
     }
     __syncthreads();
     if (act) {  // own-side face terms at face point qf = l of each face
@@ -287,7 +281,8 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
       T v[M];
 #pragma unroll
       for (int q0 = 0; q0 < M; ++q0) {
-        T s = rr[q2 * M2 + q1 * M + q0];
+        const int qq = q2 * M2 + q1 * M + q0;
+        T s = rr[qq] + ry[qq] + rz[qq];
         s = fma(tb.e0[q0], fr[0 * M2 + q1 + M * q2], s);
         s = fma(tb.d0[q0], fr[1 * M2 + q1 + M * q2], s);
         s = fma(tb.e1[q0], fr[2 * M2 + q1 + M * q2], s);
