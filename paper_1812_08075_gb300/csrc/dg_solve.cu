@@ -250,6 +250,17 @@ unsigned grid_for(int64_t n) {
   return (unsigned)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
 }
 
+// Blocks per right-hand side of the reducing vector kernels: one wave of 8 blocks per SM
+// over all right-hand sides, so every thread streams many elements before the block's
+// FP64 reduction tree (FP64 add throughput is scarce on this part; a reduction per few
+// elements would cost more than the vector traffic itself).
+unsigned grid_vec(int64_t n, int nrhs) {
+  const int64_t wave = 8 * 152;
+  int64_t g = (n + kThreads - 1) / kThreads;
+  const int64_t cap = wave / nrhs > 1 ? wave / nrhs : 1;
+  return (unsigned)(g > cap ? cap : (g < 1 ? 1 : g));
+}
+
 #define SCK(call)                                          \
   do {                                                     \
     if ((call) != cudaSuccess) return dg_record_error(DG_ERR_CUDA); \
@@ -326,7 +337,7 @@ template <typename T>
 dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, Workspace *W, int nrhs,
                              int iters, cudaStream_t s) {
   const int64_t n = op->ndofs;
-  const dim3 g(grid_for(n), nrhs);
+  const dim3 g(grid_vec(n, nrhs), nrhs);
   Scalars *S = &W->S;
   for (int it = 0; it < iters; ++it) {
     dg_status st = dg_apply_internal(op, p, Ap, nrhs, s, false);
@@ -364,7 +375,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   }
   Workspace *W = (Workspace *)op->sv_scal;
   Scalars *S = &W->S;
-  const dim3 g(grid_for(n), nrhs);
+  const dim3 g(grid_vec(n, nrhs), nrhs);
   k_zero_scalars<<<1, 128, 0, s>>>(S);
   if (x_zero) {
     SCK(cudaMemcpyAsync(r, b, (size_t)nrhs * n * es, cudaMemcpyDeviceToDevice, s));
@@ -534,7 +545,7 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
   Workspace *W = (Workspace *)op64->sv_scal;
   Scalars *S = &W->S;
   cudaStream_t s = (cudaStream_t)stream;
-  const dim3 g(grid_for(n), nrhs);
+  const dim3 g(grid_vec(n, nrhs), nrhs);
   Scalars h;
   std::vector<int> inner_iters(nrhs, 0);
   dg_solve_info sub[16];
