@@ -172,7 +172,10 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   if (co->max_rhs < 1 || co->max_rhs > 16) return fail(DG_ERR_INVALID_ARG);
   if (pen->mode != DG_PEN_CONFIG && pen->mode != DG_PEN_PAPER) return fail(DG_ERR_INVALID_ARG);
   if (co->dirichlet_mask < 0 || co->dirichlet_mask > 63) return fail(DG_ERR_INVALID_ARG);
-  if (co->geometry == DG_GEOM_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+  if (co->geometry < DG_GEOM_AUTO || co->geometry > DG_GEOM_RECOMPUTE) return fail(DG_ERR_INVALID_ARG);
+  if (co->geometry == DG_GEOM_RECOMPUTE && !mesh->affine &&
+      (co->precision != DG_FP64 || co->problem != DG_SCALAR || m != degree + 1))
+    return fail(DG_ERR_UNSUPPORTED);
 
   dg_operator *o = new (std::nothrow) dg_operator;
   if (!o) return fail(DG_ERR_OOM);
@@ -184,7 +187,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   o->dmask = (unsigned)co->dirichlet_mask;
   o->c = co->c; o->mu = co->mu; o->theta = co->theta;
   o->pen = *pen;
-  o->geo = mesh->affine ? GEO_AFFINE : GEO_STORED;
+  o->geo = mesh->affine ? GEO_AFFINE : (co->geometry == DG_GEOM_RECOMPUTE ? GEO_RECOMPUTE : GEO_STORED);
   o->ncell = (int64_t)o->nx * o->ny * o->nz;
   const int n[3] = {o->nx, o->ny, o->nz};
   o->face_off[0] = 0;
@@ -237,6 +240,10 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
       free_op(o);
       return fail(DG_ERR_CUDA);
     }
+    if (o->geo == GEO_RECOMPUTE) {
+      if (cudaDeviceSynchronize() != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
+      goto geometry_done;
+    }
     ALLOC(o->d_gvol, (size_t)o->ncell * 7 * M3 * es);
     ALLOC(o->d_gface, (size_t)o->nface * 7 * M2 * es);
     cudaError_t e;
@@ -248,6 +255,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
                                  o->ht.gauss_w, (float *)o->d_gvol, (float *)o->d_gface, 0);
     if (e != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) { free_op(o); return fail(DG_ERR_CUDA); }
   }
+geometry_done:
   const size_t R = (size_t)o->max_rhs;
   const size_t nrv = stokes ? 4 : 1, ntr = stokes ? 42 : 12;
   ALLOC(o->d_rvol, R * o->ncell * nrv * M3 * es);
@@ -305,7 +313,7 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   auto thr = [](int w) { int t = ((w + 31) / 32) * 32; return t < 64 ? 64 : (t > 256 ? 256 : t); };
   out->threads_cell = thr(op->cpb * M3);
   out->threads_face = thr(op->fpb * M2);
-  out->geometry = op->geo;
+  out->geometry = op->geo == GEO_AFFINE ? 0 : (op->geo == GEO_STORED ? DG_GEOM_STORED : DG_GEOM_RECOMPUTE);
   out->variant = op->variant;
   out->persistent_grid = op->fused_grid;
   if (op->variant == DG_VARIANT_FUSED) {
@@ -354,6 +362,16 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   }
   const int64_t sdof = op->ndofs, srv = op->ncell * M3, str = op->ncell * 12 * M2;
   const bool kap = op->kappa_vol != nullptr;
+  if (op->geo == GEO_RECOMPUTE) {  // geometry from the vertices, in the adjoint kernels with forward coefficients
+    for (int r = 0; r < nrhs; ++r) {
+      e = launch_scalar_adjoint(op->p, GEO_RECOMPUTE, kap, scalar_args<double>(op, transpose), op->theta,
+                                (const double *)x + r * sdof, nullptr, (double *)y + r * sdof, nullptr, nullptr,
+                                (double *)op->d_rvol, (double *)op->d_tr, nullptr, (double *)op->d_fres, op->cpb,
+                                op->fpb, s, r == 0 ? ev : nullptr);
+      if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+    }
+    return DG_OK;
+  }
   if (op->variant == DG_VARIANT_FUSED && fused_ok(op)) {
     if (op->precision == DG_FP64)
       e = launch_fused_apply<double>(op->p, scalar_args<double>(op, transpose), op->ht, (const double *)x, (double *)y, nrhs,
@@ -575,6 +593,17 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
       }
     }
     if (st != DG_OK) break;
+    int bgeo = op->geo;
+    if (op->geo == GEO_STORED && op->precision == DG_FP64 && op->problem == DG_SCALAR && op->m == op->p) {
+      op->geo = GEO_RECOMPUTE;  // stored vs recomputed per-point geometry
+      op->cpb = bc;
+      op->fpb = bf;
+      if ((st = time_kernels(op, x, y, nrhs, s, 1, 3, ms)) != DG_OK) { op->geo = GEO_STORED; break; }
+      ++out->candidates;
+      if (ms[0] + ms[1] + ms[2] < best) { best = ms[0] + ms[1] + ms[2]; bgeo = GEO_RECOMPUTE; bv = DG_VARIANT_THREE_KERNEL; }
+      op->geo = GEO_STORED;
+    }
+    op->geo = bgeo;
     op->variant = bv;
     op->cpb = bc;
     op->fpb = bf;

@@ -233,3 +233,22 @@ def test_overintegration_k_plus_2_points(k, geom):
     assert relerr(y, orc.apply(x)) <= TOL64
     with pytest.raises(dg.DGError):
         op.set_variant(dg.DG_VARIANT_FUSED)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_recomputed_geometry_forward(k):
+    # DG_GEOM_RECOMPUTE: no stored per-point geometry; the apply recomputes it from the vertices
+    n = (4, 3, 5)
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, theta=1.0, max_rhs=2, geometry=dg.DG_GEOM_RECOMPUTE)
+    assert op.stats().geometry == dg.DG_GEOM_RECOMPUTE
+    orc = oracle.Problem(*n, k, vertices=verts, theta=1.0)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    orc.kappa_vol, orc.kappa_face = kv, kf
+    xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(2)])
+    y = op.apply(torch.from_numpy(xs).cuda()).cpu().numpy()
+    for r in range(2):
+        assert relerr(y[r], orc.apply(xs[r])) <= TOL64
+    with pytest.raises(dg.DGError):
+        dg.Operator(dg.Mesh(*n, verts), k, precision=dg.DG_FP32, geometry=dg.DG_GEOM_RECOMPUTE)
