@@ -117,8 +117,10 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
         const int coord = ax == 0 ? cc0 : (ax == 1 ? cy : cz);
         const int nlim = ax == 0 ? nx : (ax == 1 ? ny : nz);
         const int nbc = coord + (side ? 1 : -1);
+        // x-neighbours inside this row tile hand over their own traces later (no gather)
+        const bool in_tile = ax == 0 && (side ? c + 1 < nc : c > 0);
         T vu = T(0), vd = T(0);
-        if (nbc >= 0 && nbc < nlim) {
+        if (!in_tile && nbc >= 0 && nbc < nlim) {
           const int64_t step = ax == 0 ? 1 : (ax == 1 ? (int64_t)nx : (int64_t)nx * ny);
           const int64_t nb = side ? cell + step : cell - step;
           int base, stride;
@@ -152,9 +154,11 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
         for (int j = 1; j < P; ++j) acc = fma(tb.interp[q * P + j], in[j], acc);
         t2[l2 * M2 + q * M + l1] = acc;
       }
-      // neighbour tangential sweep along t1: lines (lq, n2)
+      // neighbour tangential sweep along t1: lines (lq, n2); x faces with an in-tile
+      // neighbour (lq 0,1: lower; 2,3: upper) are skipped
       for (int ln = l; ln < 12 * P; ln += L) {
         const int lq = ln / P, n2 = ln - (ln / P) * P;
+        if ((lq < 2 && c > 0) || (lq >= 2 && lq < 4 && c + 1 < nc)) continue;
         const T *src = nbg + lq * P2 + n2 * P;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
@@ -182,6 +186,7 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
       // neighbour tangential sweep along t2: lines (lq, q1)
       for (int ln = l; ln < 12 * M; ln += L) {
         const int lq = ln / M, q1 = ln - (ln / M) * M;
+        if ((lq < 2 && c > 0) || (lq >= 2 && lq < 4 && c + 1 < nc)) continue;
         const T *src = nb1 + lq * P * M + q1;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
@@ -264,7 +269,16 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
             Rn = ss * uo * b;
           }
         } else {
-          const T un = nbq[(2 * lf) * M2 + l], dnn = nbq[(2 * lf + 1) * M2 + l];
+          T un, dnn;
+          if (ax == 0 && (side ? c + 1 < nc : c > 0)) {
+            // the neighbour's own trace of the shared face (its face lf ^ 1)
+            const T *ntro = base + (c + (side ? 1 : -1)) * LY::per_cell + 3 * LY::sV + 3 * LY::sV;
+            un = ntro[(2 * (lf ^ 1)) * M2 + l];
+            dnn = ntro[(2 * (lf ^ 1) + 1) * M2 + l];
+          } else {
+            un = nbq[(2 * lf) * M2 + l];
+            dnn = nbq[(2 * lf + 1) * M2 + l];
+          }
           const T J = side ? uo - un : un - uo;
           const T flux = half * bW * (dno + dnn);
           const T v = fma(sc, flux, pw * J);
