@@ -35,6 +35,7 @@ from paper_1812_08075_gb300 import workloads as wl  # noqa: E402
 METRIC = "dg_apply DOF/s (FP64 and mixed) at Q2-Q5; % of FP64-peak / HBM roofline"
 N_CELLS = 64
 SM_COUNT = 152
+VARIANT_NAMES = {1: "three-kernel", 2: "fused persistent", 3: "cellwise persistent"}
 FP64_FLOPS_PER_SM_CLK = 4.0   # 2 DFMA per SM per clock: 1.25 TFLOP/s nominal at 2.07 GHz
 FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FFMA per SM per clock
 # DRAM bytes (read + write) of one k_cell launch from the ncu capture of the 40^3 Q3 case
@@ -248,7 +249,7 @@ def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
         peak = pk["fp32_tflops"] if prec == dg.DG_FP32 else pk["fp64_tflops"]
         byt = st.dofs_bytes * nrhs
         res[tag] = {"dof_s": nrhs * op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "variant":
-                    "fused persistent" if st.variant == dg.DG_VARIANT_FUSED else "three-kernel",
+                    VARIANT_NAMES[st.variant],
                     "persistent_grid": st.persistent_grid, "tflops": f / (ms * 1e-3) / 1e12,
                     "frac_alu_peak": f / (ms * 1e-3) / 1e12 / peak,
                     "hbm_gbs_algorithmic": byt / (ms * 1e-3) / 1e9,
@@ -402,7 +403,7 @@ def run_ours(args, rank, world, dist):
            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
            "roofline": roofline, "apply": whole,
-           "gpu_launches": (1 if st.variant == dg.DG_VARIANT_FUSED else 3) * args.steps, "clocks": clocks,
+           "gpu_launches": (3 if st.variant == dg.DG_VARIANT_THREE_KERNEL else 1) * args.steps, "clocks": clocks,
            "tuning": tuning}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).pin_memory()

@@ -47,7 +47,7 @@ enum { DG_PEN_CONFIG = 0, DG_PEN_PAPER = 1 };
 enum { DG_SCALAR = 0, DG_STOKES = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
-enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2 };
+enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2, DG_VARIANT_CELLWISE = 3 };
 enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1 };
 
 /* Interior-penalty factor gamma_F (Sec. 5.2).
@@ -102,7 +102,7 @@ typedef struct {
   int32_t threads_cell;
   int32_t threads_face;
   int32_t geometry;       /* DG_GEOM_* in effect (0 = affine fast path) */
-  int32_t variant;        /* DG_VARIANT_THREE_KERNEL or DG_VARIANT_FUSED */
+  int32_t variant;        /* DG_VARIANT_THREE_KERNEL, _FUSED or _CELLWISE */
   int32_t persistent_grid;/* blocks of the last fused (persistent) launch, 0 if none yet */
   int32_t reserved;
 } dg_stats;
@@ -146,10 +146,18 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
  *     (right-hand side, row of cells) items) in which each cell evaluates its faces from
  *     its own side with the neighbour's trace gathered from its coefficients; affine
  *     scalar operators without kappa only; no scratch.
- *   DG_VARIANT_AUTO: fused for FP32 affine scalar operators, three-kernel otherwise.
- * cells_per_block (cells per block, or cells per row tile of the fused kernel) and
- * faces_per_block: 0 keeps the default. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED
- * (fused variant on an operator it does not cover, blocking over the shared-memory limit). */
+ *   DG_VARIANT_CELLWISE: one persistent launch with one thread per cell: a block owns a
+ *     brick of 8 x 4 x (cells_per_block / 32) cells (cells_per_block = 64, 128 or 256),
+ *     each cell's sum factorisation runs in registers and the cells of a brick exchange
+ *     face traces through shared memory; neighbours across the brick boundary are
+ *     evaluated from their coefficients. Same operators as the fused variant, degree
+ *     k <= 2; no scratch.
+ *   DG_VARIANT_AUTO: cellwise for FP32 affine scalar operators of degree k <= 2, fused
+ *     for other FP32 affine scalar operators, three-kernel otherwise.
+ * cells_per_block (cells per block, cells per row tile of the fused kernel, or cells per
+ * brick of the cellwise kernel) and faces_per_block: 0 keeps the default. Errors:
+ * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (a variant on an operator it does not cover,
+ * blocking over the shared-memory limit or not a brick size). */
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block);
 
 /* Result of dg_operator_autotune. ms_* are CUDA-event times of one apply of nrhs

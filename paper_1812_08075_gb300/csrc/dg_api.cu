@@ -150,8 +150,20 @@ static bool fused_ok(const dg_operator *o) {
   return o->problem == DG_SCALAR && o->geo == GEO_AFFINE && o->kappa_vol == nullptr && o->m == o->p;
 }
 
+static bool cellwise_ok(const dg_operator *o) { return fused_ok(o) && o->p <= 3; }
+
+static const size_t kMaxSmemBlock = 227 * 1024;  // opt-in shared memory per block
+
+static bool variant_ok(const dg_operator *o, int v) {
+  return v == DG_VARIANT_THREE_KERNEL || (v == DG_VARIANT_FUSED && fused_ok(o)) ||
+         (v == DG_VARIANT_CELLWISE && cellwise_ok(o));
+}
+
 static int resolve_variant(const dg_operator *o, int v) {
-  if (v == DG_VARIANT_AUTO) return (o->precision == DG_FP32 && fused_ok(o)) ? DG_VARIANT_FUSED : DG_VARIANT_THREE_KERNEL;
+  if (v == DG_VARIANT_AUTO) {
+    if (o->precision == DG_FP32 && cellwise_ok(o)) return DG_VARIANT_CELLWISE;
+    return (o->precision == DG_FP32 && fused_ok(o)) ? DG_VARIANT_FUSED : DG_VARIANT_THREE_KERNEL;
+  }
   return v;
 }
 
@@ -288,7 +300,7 @@ dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const vo
   }
   op->kappa_vol = kappa_vol;
   op->kappa_face = kappa_face;
-  if (op->variant == DG_VARIANT_FUSED && !fused_ok(op)) op->variant = DG_VARIANT_THREE_KERNEL;
+  if (!variant_ok(op, op->variant)) op->variant = DG_VARIANT_THREE_KERNEL;
   return DG_OK;
 }
 
@@ -303,6 +315,8 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
     stokes_work_model(op->p, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
   else if (op->variant == DG_VARIANT_FUSED)
     fused_work_model(op->p, op->ncell, op->nbface, out->flops, out->bytes, es);
+  else if (op->variant == DG_VARIANT_CELLWISE)
+    cellwise_work_model(op->p, op->nx, op->ny, op->nz, op->brick, op->nbface, out->flops, out->bytes, es);
   else
     scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, out->flops,
                       out->bytes, es);
@@ -316,9 +330,10 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   out->geometry = op->geo == GEO_AFFINE ? 0 : (op->geo == GEO_STORED ? DG_GEOM_STORED : DG_GEOM_RECOMPUTE);
   out->variant = op->variant;
   out->persistent_grid = op->fused_grid;
-  if (op->variant == DG_VARIANT_FUSED) {
-    out->cells_per_block = op->tile;
-    out->threads_cell = 256;
+  if (op->variant == DG_VARIANT_FUSED || op->variant == DG_VARIANT_CELLWISE) {
+    const bool fz = op->variant == DG_VARIANT_FUSED;
+    out->cells_per_block = fz ? op->tile : op->brick;
+    out->threads_cell = fz ? op->tile * op->p * op->p : op->brick;
     out->faces_per_block = 0;
     out->threads_face = 0;
   }
@@ -370,6 +385,16 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
                                 op->fpb, s, r == 0 ? ev : nullptr);
       if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     }
+    return DG_OK;
+  }
+  if (op->variant == DG_VARIANT_CELLWISE && cellwise_ok(op)) {
+    if (op->precision == DG_FP64)
+      e = launch_cellwise_apply<double>(op->p, scalar_args<double>(op, transpose), op->ht, (const double *)x,
+                                        (double *)y, nrhs, sdof, op->brick, s, ev, &op->fused_grid);
+    else
+      e = launch_cellwise_apply<float>(op->p, scalar_args<float>(op, transpose), op->ht, (const float *)x, (float *)y,
+                                       nrhs, sdof, op->brick, s, ev, &op->fused_grid);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;
   }
   if (op->variant == DG_VARIANT_FUSED && fused_ok(op)) {
@@ -479,12 +504,21 @@ dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face,
 }
 
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block) {
-  if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_FUSED || cells_per_block < 0 || faces_per_block < 0)
+  if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_CELLWISE || cells_per_block < 0 || faces_per_block < 0)
     return fail(DG_ERR_INVALID_ARG);
   const int v = resolve_variant(op, variant);
-  if (v == DG_VARIANT_FUSED && !fused_ok(op)) return fail(DG_ERR_UNSUPPORTED);
+  if (!variant_ok(op, v)) return fail(DG_ERR_UNSUPPORTED);
   const size_t es = op->precision == DG_FP64 ? 8 : 4;
   const int M = op->m, P = op->p;
+  if (v == DG_VARIANT_CELLWISE) {
+    if (cells_per_block > 0) {
+      const size_t sm = cellwise_smem_bytes(P, cells_per_block, (int)es);
+      if (sm == 0 || sm > kMaxSmemBlock) return fail(DG_ERR_UNSUPPORTED);
+    }
+    op->variant = v;
+    if (cells_per_block > 0) op->brick = cells_per_block;
+    return DG_OK;
+  }
   if (cells_per_block > 0) {
     if (v == DG_VARIANT_FUSED && cells_per_block * P * P > 1024) return fail(DG_ERR_UNSUPPORTED);
     const size_t per = v == DG_VARIANT_FUSED ? (size_t)(6 * P * P * P + 40 * P * P) * es
@@ -538,7 +572,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
   cudaStream_t s = (cudaStream_t)stream;
   dg_status st = DG_OK;
   const int M = op->m, M2 = M * M, M3 = M * M * M;
-  const int save_v = op->variant, save_c = op->cpb, save_f = op->fpb, save_t = op->tile;
+  const int save_v = op->variant, save_c = op->cpb, save_f = op->fpb, save_t = op->tile, save_b = op->brick;
   double ms[3];
   auto fits = [&](size_t smem) { return smem + 4096 <= 160 * 1024; };
   const bool stokes = op->problem == DG_STOKES;
@@ -593,6 +627,20 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
       }
     }
     if (st != DG_OK) break;
+    int bbrick = save_b;
+    if (cellwise_ok(op)) {
+      op->variant = DG_VARIANT_CELLWISE;
+      const int cand_b[] = {64, 128, 256};
+      for (int i = 0; i < 3 && st == DG_OK; ++i) {
+        const size_t sm = cellwise_smem_bytes(op->p, cand_b[i], (int)es);
+        if (sm == 0 || sm > kMaxSmemBlock) continue;
+        op->brick = cand_b[i];
+        if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
+        ++out->candidates;
+        if (ms[0] + ms[1] + ms[2] < best) { best = ms[0] + ms[1] + ms[2]; bv = DG_VARIANT_CELLWISE; bbrick = cand_b[i]; }
+      }
+    }
+    if (st != DG_OK) break;
     int bgeo = op->geo;
     if (op->geo == GEO_STORED && op->precision == DG_FP64 && op->problem == DG_SCALAR && op->m == op->p) {
       op->geo = GEO_RECOMPUTE;  // stored vs recomputed per-point geometry
@@ -608,13 +656,14 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     op->cpb = bc;
     op->fpb = bf;
     op->tile = btile;
+    op->brick = bbrick;
     out->variant = bv;
-    out->cells_per_block = bv == DG_VARIANT_FUSED ? btile : bc;
-    out->faces_per_block = bv == DG_VARIANT_FUSED ? 0 : bf;
+    out->cells_per_block = bv == DG_VARIANT_FUSED ? btile : (bv == DG_VARIANT_CELLWISE ? bbrick : bc);
+    out->faces_per_block = bv == DG_VARIANT_THREE_KERNEL ? bf : 0;
     out->ms_best = best;
   } while (0);
   if (st != DG_OK) {
-    op->variant = save_v; op->cpb = save_c; op->fpb = save_f; op->tile = save_t;
+    op->variant = save_v; op->cpb = save_c; op->fpb = save_f; op->tile = save_t; op->brick = save_b;
   }
   cudaStreamSynchronize(s);
   cudaFree(x);
@@ -733,5 +782,29 @@ void fused_work_model(int P, int64_t ncell, int64_t nbface, double flops[3], dou
   flops[0] = f + cell * (double)ncell;
   flops[1] = flops[2] = 0.0;
   bytes[0] = es * (double)ncell * 2.0 * P3;
+  bytes[1] = bytes[2] = 0.0;
+}
+
+// Cellwise variant: per cell, interpolation, mass, per axis (gradient, pointwise flux,
+// transposed derivative, four face rows per line, the two faces' terms and lifting),
+// transposed interpolation; per brick-boundary face with a neighbour, the neighbour's
+// normal derivative and two tangential sweeps of two quantities. Bytes: x read, y written.
+void cellwise_work_model(int P, int nx, int ny, int nz, int brick, int64_t nbface, double flops[3], double bytes[3],
+                         int es) {
+  const double M = P, P2 = P * P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  const double cP = 2.0 * P - 1.0, cM = 2.0 * M - 1.0;
+  const double ncell = (double)nx * ny * nz;
+  const int bx = 8, by = 4, bz = brick / 32 > 0 ? brick / 32 : 1;
+  // faces between bricks (each evaluated from the neighbour's coefficients once per side)
+  const double halo = 2.0 * ((double)((nx - 1) / bx) * ny * nz + (double)((ny - 1) / by) * nx * nz +
+                             (double)((nz - 1) / bz) * nx * ny);
+  const double per_halo = P2 * cP + 2.0 * (M * P + M2) * cP;
+  double cell = 2.0 * (P2 * M + P * M2 + M3) * cP + M3;
+  cell += 3.0 * (M3 * cM + M3 + 2.0 * M * M3 + 4.0 * M2 * cM);
+  const double own_sides = 6.0 * ncell - (double)nbface;  // interior own sides
+  const double face = own_sides * M2 * (7.0 + 4.0 * M) + (double)nbface * M2 * (5.0 + 4.0 * M);
+  flops[0] = cell * ncell + face + halo * per_halo;
+  flops[1] = flops[2] = 0.0;
+  bytes[0] = es * ncell * 2.0 * P3;
   bytes[1] = bytes[2] = 0.0;
 }

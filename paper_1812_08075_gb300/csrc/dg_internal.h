@@ -96,6 +96,14 @@ template <typename T>
 cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
                                int64_t stride_dofs, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out);
 
+// One-thread-per-cell persistent apply for affine meshes, degree k <= 2 (dg_cellwise.cu):
+// bricks of 8 x 4 x (cells / 32) cells per block, cells = 64, 128 or 256.
+template <typename T>
+cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
+                                  int64_t stride_dofs, int cells, cudaStream_t s, const cudaEvent_t *ev,
+                                  int *grid_out);
+size_t cellwise_smem_bytes(int p, int cells, int es);  // 0 if (p, cells) is not supported
+
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
@@ -121,6 +129,8 @@ cudaError_t launch_penalty(int m, int k, int pen_mode, double alpha, int nx, int
 
 // Work model of the fused single-pass variant, per right-hand side (all in flops[0]).
 void fused_work_model(int p, int64_t ncell, int64_t nbface, double flops[3], double bytes[3], int elem_size);
+void cellwise_work_model(int p, int nx, int ny, int nz, int brick, int64_t nbface, double flops[3], double bytes[3],
+                         int elem_size);
 
 // Work model of the Stokes apply (op counts of the kernels), per right-hand side.
 void stokes_work_model(int p, int64_t ncell, int64_t nface, int64_t nbface, double flops[3], double bytes[3],
@@ -160,6 +170,7 @@ struct dg_operator {
   int cpb = 1, fpb = 1;
   int variant = DG_VARIANT_THREE_KERNEL;  // resolved (never AUTO)
   int tile = 8;                          // cells per row tile of the fused kernel
+  int brick = 128;                       // cells per brick of the cellwise kernel
   int fused_grid = 0;
   double gamma_axis[3];
   // per-kernel event timing (dg_operator_profile)

@@ -178,13 +178,69 @@ def test_fused_fp32(k):
 
 
 def test_fused_is_the_fp32_affine_default_and_rejected_elsewhere():
-    assert dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32).stats().variant == dg.DG_VARIANT_FUSED
+    assert dg.Operator(dg.Mesh(3, 3, 3), 3, precision=dg.DG_FP32).stats().variant == dg.DG_VARIANT_FUSED
+    assert dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32).stats().variant == dg.DG_VARIANT_CELLWISE
     assert dg.Operator(dg.Mesh(3, 3, 3), 2).stats().variant == dg.DG_VARIANT_THREE_KERNEL
     op = dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, precision=dg.DG_FP32)
     assert op.stats().variant == dg.DG_VARIANT_THREE_KERNEL
     with pytest.raises(dg.DGError) as e:
         op.set_variant(dg.DG_VARIANT_FUSED)
     assert e.value.status == dg.DG_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- cellwise persistent variant
+
+def run_cellwise(n, k, precision, nrhs=1, brick=0, theta=-1.0, mask=0b111111, c=1.0):
+    op = dg.Operator(dg.Mesh(*n), k, precision=precision, max_rhs=nrhs, theta=theta, dirichlet_mask=mask, c=c)
+    op.set_variant(dg.DG_VARIANT_CELLWISE, brick)
+    st = op.stats()
+    assert st.variant == dg.DG_VARIANT_CELLWISE and st.cells_per_block == (brick or 128)
+    orc = oracle.Problem(*n, k, theta=theta, dirichlet_mask=mask, c=c)
+    xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(nrhs)])
+    y = op.apply(torch.from_numpy(xs).to("cuda", op.dtype)).double().cpu().numpy()
+    assert op.stats().persistent_grid > 0
+    return max(relerr(y[r], orc.apply(xs[r])) for r in range(nrhs))
+
+
+@pytest.mark.parametrize("k,brick", [(1, 64), (1, 128), (1, 256), (2, 64), (2, 128), (2, 256)])
+def test_cellwise_fp64_matches_oracle(k, brick):
+    # bricks of 8 x 4 x (brick/32) cells: 19 x 6 x 11 cells leave ragged bricks on all axes
+    # and brick-boundary faces in every direction
+    assert run_cellwise((19, 6, 11), k, dg.DG_FP64, brick=brick) <= TOL64
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (3, 2, 2), (8, 4, 2), (17, 9, 3), (2, 13, 20)])
+def test_cellwise_meshes_smaller_and_larger_than_a_brick(n):
+    assert run_cellwise(n, 2, dg.DG_FP64, brick=64) <= TOL64
+
+
+@pytest.mark.parametrize("mask,theta,c", [(0b100111, 1.0, 0.5), (0, -1.0, 0.0), (0b010101, 0.0, 2.0)])
+def test_cellwise_theta_masks_and_rhs(mask, theta, c):
+    assert run_cellwise((10, 5, 9), 2, dg.DG_FP64, nrhs=3, brick=64, theta=theta, mask=mask, c=c) <= TOL64
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_cellwise_fp32(k):
+    err = run_cellwise((19, 6, 11), k, dg.DG_FP32, nrhs=4, brick=128)
+    print(f"cellwise FP32 Q{k}: rel err {err:.2e}")
+    assert err <= TOL32
+
+
+def test_cellwise_rejected_where_it_does_not_apply():
+    for op in (dg.Operator(dg.Mesh(3, 3, 3), 3, precision=dg.DG_FP32),
+               dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, precision=dg.DG_FP32)):
+        with pytest.raises(dg.DGError) as e:
+            op.set_variant(dg.DG_VARIANT_CELLWISE)
+        assert e.value.status == dg.DG_ERR_UNSUPPORTED
+    op = dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32)
+    for bad in (32, 96, 512):
+        with pytest.raises(dg.DGError):
+            op.set_variant(dg.DG_VARIANT_CELLWISE, bad)
+
+
+@pytest.mark.parametrize("brick", [64, 256])
+def test_cellwise_fp32_bricks_and_rhs(brick):
+    assert run_cellwise((21, 7, 17), 2, dg.DG_FP32, nrhs=3, brick=brick, theta=1.0, mask=0b011110) <= TOL32
 
 
 def test_config4_fp32_16rhs_full_size_sampled():
