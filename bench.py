@@ -317,7 +317,8 @@ def run_solve(args):
     stream = torch.cuda.current_stream().cuda_stream
     out = {"mode": "solve", "workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides",
            "ndofs": op64.ndofs, "rtol": args.solve_rtol,
-           "preconditioner": "point Jacobi (diagonal set up outside the timed solves)" if args.precond else "none"}
+           "preconditioner": {0: "none", 1: "point Jacobi (diagonal set up outside the timed solves)",
+                              2: "cell-block Jacobi by fast diagonalisation"}[args.precond]}
     if args.precond:  # set up both diagonals before timing (they are cached by the operators)
         warm = dg.dg_cg_options(1e-1, 50, 50, 0, args.precond)
         xz = torch.zeros_like(b)
@@ -475,7 +476,8 @@ def main():
     ap.add_argument("--solve-rtol", type=float, default=1e-10)
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--fp64-max-iters", type=int, default=20000)
-    ap.add_argument("--precond", type=int, default=0, help="0: none, 1: point Jacobi (both solvers)")
+    ap.add_argument("--precond", type=int, default=0, choices=(0, 1, 2),
+                    help="0: none, 1: point Jacobi, 2: cell-block Jacobi (both solvers)")
     args = ap.parse_args()
     global N_CELLS
     N_CELLS = args.cells

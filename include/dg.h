@@ -48,7 +48,7 @@ enum { DG_SCALAR = 0, DG_STOKES = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
 enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2, DG_VARIANT_CELLWISE = 3 };
-enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1 };
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1, DG_PRECOND_BLOCK_JACOBI = 2 };
 
 /* Interior-penalty factor gamma_F (Sec. 5.2).
  *   DG_PEN_CONFIG: gamma_F = alpha * k * (k+1) / h_a with h_a = 1/n_a the nominal cell
@@ -227,9 +227,10 @@ dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, 
  *   max_iters  iteration limit (rounded up to a multiple of chunk)
  *   chunk      iterations enqueued between host convergence checks (0 = 25)
  *   use_graph  1: capture one chunk into a CUDA graph on the first call and replay it
- *   precond    DG_PRECOND_NONE, or DG_PRECOND_JACOBI (point Jacobi with diag(A) from
+ *   precond    DG_PRECOND_NONE; DG_PRECOND_JACOBI (point Jacobi with diag(A) from
  *              dg_operator_diagonal, computed on first use and kept by the operator
- *              until its kappa changes) */
+ *              until its kappa changes); or DG_PRECOND_BLOCK_JACOBI (the cell blocks of
+ *              A inverted by dg_operator_block_jacobi; operators it covers only) */
 typedef struct {
   double rtol;
   int32_t max_iters;
@@ -246,6 +247,18 @@ typedef struct {
  * DG_ERR_UNSUPPORTED (Stokes), DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_operator_diagonal(const dg_operator *op, void *diag, void *stream);
 
+/* Cell-block Jacobi preconditioner: z_c = A_cc^-1 r_c for every cell c, where A_cc is the
+ * diagonal block of cell c (the volume terms of Eq. diffreac_weak and the cell's own side
+ * of its six faces). On affine cells with kappa = 1 that block is a Kronecker sum of 1D
+ * matrices (Sec. 2.2's tensor structure), so it is inverted exactly by fast
+ * diagonalisation: generalized eigenvectors of the 1D stiffness-plus-face matrix and the
+ * 1D mass matrix per axis and cell position (computed on the host in FP64 on first use),
+ * then three transposed sweeps, a pointwise division and three sweeps per cell (the
+ * paper has no preconditioner). r, z: device [nrhs][ndofs], operator precision, distinct.
+ * Errors: DG_ERR_INVALID_ARG; DG_ERR_UNSUPPORTED unless the operator is scalar, affine,
+ * without kappa, theta = -1 and k+1 points per direction; DG_ERR_CUDA. */
+dg_status dg_operator_block_jacobi(const dg_operator *op, const void *r, void *z, int nrhs, void *stream);
+
 /* Per right-hand-side result of a solve. iters: CG iterations (summed over the inner
  * solves of a refinement); outer: refinement steps; relres: final ||b - A x|| / ||b||
  * (for refinement recomputed in FP64); breakdown: CG met p.Ap <= 0. */
@@ -257,7 +270,7 @@ typedef struct {
   double relres;
 } dg_solve_info;
 
-/* Batched (optionally Jacobi-preconditioned) conjugate gradients on A x = b (scalar operator, SPD for
+/* Batched (optionally point- or block-Jacobi-preconditioned) conjugate gradients on A x = b (scalar operator, SPD for
  * theta = -1 with penalty large enough): nrhs (1..max_rhs) independent solves advanced
  * together, vectors in the operator's precision, dot products accumulated in FP64,
  * per right-hand-side scalars kept on the device. x (device [nrhs][ndofs]) holds the

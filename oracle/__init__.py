@@ -186,6 +186,18 @@ class Problem:
             raise RuntimeError("oracle_rhs failed")
         return F
 
+    def block_jacobi(self, r: np.ndarray) -> np.ndarray:
+        """z with A_cc z_c = r_c for every cell c, A_cc the cell's diagonal block of the
+        assembled matrix (cell-block Jacobi; dense solves, small meshes only)."""
+        A = self.assemble()
+        loc = self.ndofs() // self.ncell
+        r = np.asarray(r, dtype=np.float64)
+        z = np.empty_like(r)
+        for c in range(self.ncell):
+            sl = slice(c * loc, (c + 1) * loc)
+            z[sl] = np.linalg.solve(A[sl, sl].toarray(), r[sl])
+        return z
+
     def assemble(self):
         """Sparse matrix A (scipy CSR) from the local cell and face matrices."""
         import scipy.sparse as sp

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/dg.h"
 
 #define DG_MAXP 6  // basis points per direction (degree <= 5)
@@ -104,6 +106,16 @@ cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTable
                                   int *grid_out);
 size_t cellwise_smem_bytes(int p, int cells, int es);  // 0 if (p, cells) is not supported
 
+// Cell-block Jacobi preconditioner by fast diagonalisation (dg_precond.cu): host tables
+// (per axis and cell position, S and L; -1 if the operator is not affine scalar SIPG with
+// kappa = 1, theta = -1 and k+1 points) and z = A_cc^-1 r with optional r.z partials.
+struct dg_operator;
+int block_jacobi_tables(const dg_operator *op, std::vector<double> &tab);
+void block_jacobi_inverse_sums(int p, const std::vector<double> &tab, std::vector<double> &dinv);
+template <typename T>
+cudaError_t launch_block_jacobi(const dg_operator *op, const double *tab, const T *dinv, const T *r, T *z, int nrhs,
+                                double *partial, int stride, int *blocks, cudaStream_t s);
+
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
@@ -140,7 +152,6 @@ void stokes_work_model(int p, int64_t ncell, int64_t nface, int64_t nbface, doub
 void scalar_work_model(int p, int m, int geo, bool kappa, int64_t ncell, int64_t nface,
                        int64_t nbface, double flops[3], double bytes[3], int elem_size);
 
-#include <vector>
 
 struct dg_mesh {
   int nx, ny, nz;
@@ -184,6 +195,8 @@ struct dg_operator {
   size_t sv_aux_bytes = 0;
   void *sv_scal = nullptr;  // per right-hand-side scalars
   void *sv_dinv = nullptr;  // inverse diagonal of A (Jacobi preconditioner), operator precision
+  std::vector<double> bj_tab;  // block-Jacobi tables (empty until first use)
+  void *d_bjinv = nullptr;     // their inverse eigenvalue sums on the device, operator precision
   void *sv_graph = nullptr; // cached CUDA graph of a chunk of CG iterations (cudaGraphExec_t)
   void *sv_graph_key = nullptr;
 };

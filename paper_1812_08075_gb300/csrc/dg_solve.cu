@@ -382,6 +382,36 @@ dg_status diagonal_by_colours(dg_operator *op, T *out, bool invert, cudaStream_t
   return st;
 }
 
+dg_status ensure_block_jacobi(dg_operator *op) {
+  if (!op->bj_tab.empty() && op->d_bjinv) return DG_OK;
+  if (block_jacobi_tables(op, op->bj_tab) != 0) {
+    op->bj_tab.clear();
+    return dg_record_error(DG_ERR_UNSUPPORTED);
+  }
+  std::vector<double> inv;
+  block_jacobi_inverse_sums(op->p, op->bj_tab, inv);
+  const size_t es = op->precision == DG_FP64 ? 8 : 4;
+  std::vector<float> inv32;
+  const void *src = inv.data();
+  if (es == 4) {
+    inv32.assign(inv.begin(), inv.end());
+    src = inv32.data();
+  }
+  if (cudaMalloc(&op->d_bjinv, inv.size() * es) != cudaSuccess) {
+    cudaGetLastError();
+    op->d_bjinv = nullptr;
+    op->bj_tab.clear();
+    return dg_record_error(DG_ERR_OOM);
+  }
+  if (cudaMemcpy(op->d_bjinv, src, inv.size() * es, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(op->d_bjinv);
+    op->d_bjinv = nullptr;
+    op->bj_tab.clear();
+    return dg_record_error(DG_ERR_CUDA);
+  }
+  return DG_OK;
+}
+
 template <typename T>
 dg_status ensure_inverse_diagonal(dg_operator *op, cudaStream_t s) {
   if (op->sv_dinv) return DG_OK;
@@ -406,9 +436,11 @@ bool use_v4(int64_t n, const void *x, const void *b) {
 }
 
 // Enqueue `iters` CG iterations on x, r, p, Ap (device, [nrhs][n]) with scalars S.
+// z (non-NULL): block-Jacobi preconditioning, z = B r computed after the update with the
+// r.z partials, and the direction p = z + beta p.
 template <typename T, bool V4>
-dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, Workspace *W, int nrhs,
-                             int iters, cudaStream_t s) {
+dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, T *z, Workspace *W,
+                             int nrhs, int iters, cudaStream_t s) {
   const int64_t n = op->ndofs;
   const dim3 g(grid_vec(V4 ? n / 4 : n, nrhs), nrhs);
   Scalars *S = &W->S;
@@ -419,6 +451,15 @@ dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, con
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
     k_alpha<<<1, 32, 0, s>>>(S, nrhs);
     k_update<T, V4><<<g, kThreads, 0, s>>>(x, r, p, Ap, dinv, S, W->partial, W->partial2, n);
+    if (z) {
+      k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
+      int nb = 0;
+      SCK(launch_block_jacobi<T>(op, op->bj_tab.data(), (const T *)op->d_bjinv, r, z, nrhs, W->partial, kMaxBlocks, &nb, s));
+      k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz_new, nb);
+      k_beta<<<1, 32, 0, s>>>(S, nrhs);
+      k_direction<T, V4><<<g, kThreads, 0, s>>>(p, z, nullptr, S, n);
+      continue;
+    }
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz_new, g.x);
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
     k_beta<<<1, 32, 0, s>>>(S, nrhs);
@@ -454,12 +495,34 @@ void launch_init_dir(bool v4, dim3 g, cudaStream_t s, const T *r, T *p, const T 
 }
 
 template <typename T>
-dg_status enqueue(bool v4, const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, Workspace *W, int nrhs,
-                  int iters, cudaStream_t s) {
+dg_status enqueue(bool v4, const dg_operator *op, T *x, T *r, T *p, T *Ap, const T *dinv, T *z, Workspace *W,
+                  int nrhs, int iters, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (v4) return enqueue_iterations<T, true>(op, x, r, p, Ap, dinv, W, nrhs, iters, s);
+    if (v4) return enqueue_iterations<T, true>(op, x, r, p, Ap, dinv, z, W, nrhs, iters, s);
   }
-  return enqueue_iterations<T, false>(op, x, r, p, Ap, dinv, W, nrhs, iters, s);
+  return enqueue_iterations<T, false>(op, x, r, p, Ap, dinv, z, W, nrhs, iters, s);
+}
+
+// Start (or restart) of CG from the residual r: p = z = M^-1 r and the reductions of
+// r.z (into S->rz) and r.r (into S->rr).
+template <typename T>
+dg_status start_directions(const dg_operator *op, bool v4, dim3 g, T *r, T *p, const T *dinv, T *z, Workspace *W,
+                           int nrhs, cudaStream_t s) {
+  const int64_t n = op->ndofs;
+  Scalars *S = &W->S;
+  if (z) {
+    int nb = 0;
+    SCK(launch_block_jacobi<T>(op, op->bj_tab.data(), (const T *)op->d_bjinv, r, z, nrhs, W->partial, kMaxBlocks, &nb, s));
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz, nb);
+    launch_dot<T>(v4, g, s, r, r, W->partial2, n);
+    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
+    SCK(cudaMemcpyAsync(p, z, (size_t)nrhs * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return DG_OK;
+  }
+  launch_init_dir<T>(v4, g, s, r, p, dinv, W->partial, W->partial2, n);
+  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz, g.x);
+  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
+  return DG_OK;
 }
 
 // CG on A x = b for nrhs right-hand sides; x holds the initial guess (x_zero: it is 0
@@ -475,10 +538,15 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   const int64_t n = op->ndofs;
   T *r = (T *)op->sv_vec, *p = r + op->max_rhs * n, *Ap = p + op->max_rhs * n;
   const T *dinv = nullptr;
+  T *z = nullptr;
   if (o.precond == DG_PRECOND_JACOBI) {
     st = ensure_inverse_diagonal<T>(op, s);
     if (st != DG_OK) return st;
     dinv = (const T *)op->sv_dinv;
+  } else if (o.precond == DG_PRECOND_BLOCK_JACOBI) {
+    st = ensure_block_jacobi(op);
+    if (st != DG_OK) return st;
+    z = Ap + op->max_rhs * n;
   }
   Workspace *W = (Workspace *)op->sv_scal;
   Scalars *S = &W->S;
@@ -494,15 +562,14 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   }
   launch_dot<T>(v4, g, s, b, b, W->partial, n);
   k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->bb, g.x);
-  launch_init_dir<T>(v4, g, s, r, p, dinv, W->partial, W->partial2, n);
-  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz, g.x);
-  k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);
+  st = start_directions<T>(op, v4, g, r, p, dinv, z, W, nrhs, s);
+  if (st != DG_OK) return st;
   k_init_scalars<<<1, 32, 0, s>>>(S, nrhs, o.rtol);
   SCK(cudaGetLastError());
   const int chunk = o.chunk > 0 ? o.chunk : 25;
   // the graph depends on the buffers, nrhs and chunk: rebuild when any of them changes
   void *key = (void *)((uintptr_t)x ^ ((uintptr_t)b << 1) ^ ((uintptr_t)op->kappa_vol << 2) ^
-                       ((uintptr_t)op->kappa_face << 3) ^ ((uintptr_t)dinv << 5) ^ ((uintptr_t)nrhs << 48) ^
+                       ((uintptr_t)op->kappa_face << 3) ^ ((uintptr_t)dinv << 5) ^ ((uintptr_t)z << 7) ^ ((uintptr_t)nrhs << 48) ^
                        ((uintptr_t)chunk << 56));
   cudaStream_t cs = s;
   bool own_stream = false;
@@ -517,7 +584,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     const_cast<dg_operator *>(op)->prof = false;
     cudaGraph_t graph;
     SCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    dg_status est = enqueue<T>(v4, op, x, r, p, Ap, dinv, W, nrhs, chunk, cs);
+    dg_status est = enqueue<T>(v4, op, x, r, p, Ap, dinv, z, W, nrhs, chunk, cs);
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     op->prof = prof;
     if (est != DG_OK) return est;
@@ -538,7 +605,7 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
       if (o.use_graph) {
         SCK(cudaGraphLaunch((cudaGraphExec_t)op->sv_graph, cs));
       } else {
-        st = enqueue<T>(v4, op, x, r, p, Ap, dinv, W, nrhs, chunk, cs);
+        st = enqueue<T>(v4, op, x, r, p, Ap, dinv, z, W, nrhs, chunk, cs);
         if (st != DG_OK) return st;
       }
       done += chunk;
@@ -555,9 +622,8 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
     st = dg_apply_internal(op, x, Ap, nrhs, cs, false);
     if (st != DG_OK) return st;
     launch_residual<T>(v4, g, cs, b, Ap, r, n);
-    launch_init_dir<T>(v4, g, cs, r, p, dinv, W->partial, W->partial2, n);
-    k_reduce<<<nrhs, kThreads, 0, cs>>>(W->partial, S->rz, g.x);
-    k_reduce<<<nrhs, kThreads, 0, cs>>>(W->partial2, S->rr, g.x);
+    st = start_directions<T>(op, v4, g, r, p, dinv, z, W, nrhs, cs);
+    if (st != DG_OK) return st;
     k_restart_scalars<<<1, 32, 0, cs>>>(S, nrhs);
     SCK(cudaGetLastError());
     SCK(cudaMemcpyAsync(&h, S, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
@@ -596,7 +662,8 @@ void dg_solver_release(dg_operator *op) {
   if (op->sv_aux) cudaFree(op->sv_aux);
   if (op->sv_scal) cudaFree(op->sv_scal);
   if (op->sv_dinv) cudaFree(op->sv_dinv);
-  op->sv_vec = op->sv_aux = op->sv_scal = op->sv_dinv = nullptr;
+  if (op->d_bjinv) cudaFree(op->d_bjinv);
+  op->sv_vec = op->sv_aux = op->sv_scal = op->sv_dinv = op->d_bjinv = nullptr;
 }
 
 extern "C" {
@@ -610,12 +677,27 @@ dg_status dg_operator_diagonal(const dg_operator *op_c, void *diag, void *stream
   return diagonal_by_colours<float>(op, (float *)diag, false, s);
 }
 
+dg_status dg_operator_block_jacobi(const dg_operator *op_c, const void *r, void *z, int nrhs, void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !r || !z || r == z || nrhs < 1 || nrhs > op->max_rhs) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (((uintptr_t)r & 15u) || ((uintptr_t)z & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
+  dg_status st = ensure_block_jacobi(op);
+  if (st != DG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = op->precision == DG_FP64
+                      ? launch_block_jacobi<double>(op, op->bj_tab.data(), (const double *)op->d_bjinv,
+                                                    (const double *)r, (double *)z, nrhs, nullptr, 0, nullptr, s)
+                      : launch_block_jacobi<float>(op, op->bj_tab.data(), (const float *)op->d_bjinv,
+                                                   (const float *)r, (float *)z, nrhs, nullptr, 0, nullptr, s);
+  return e == cudaSuccess ? DG_OK : dg_record_error(DG_ERR_CUDA);
+}
+
 dg_status dg_cg_solve(const dg_operator *op_c, const void *b, void *x, int nrhs, const dg_cg_options *opt,
                       dg_solve_info *info, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !b || !x || !opt || !info || b == x) return dg_record_error(DG_ERR_INVALID_ARG);
   if (nrhs < 1 || nrhs > op->max_rhs || opt->max_iters < 1 || !(opt->rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
-  if (opt->precond != DG_PRECOND_NONE && opt->precond != DG_PRECOND_JACOBI) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (opt->precond < DG_PRECOND_NONE || opt->precond > DG_PRECOND_BLOCK_JACOBI) return dg_record_error(DG_ERR_INVALID_ARG);
   if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
   cudaStream_t s = (cudaStream_t)stream;

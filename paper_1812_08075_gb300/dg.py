@@ -23,14 +23,14 @@ DG_SCALAR, DG_STOKES = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
 DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED, DG_VARIANT_CELLWISE = 0, 1, 2, 3
-DG_PRECOND_NONE, DG_PRECOND_JACOBI = 0, 1
+DG_PRECOND_NONE, DG_PRECOND_JACOBI, DG_PRECOND_BLOCK_JACOBI = 0, 1, 2
 
 EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
     "dg_operator_destroy", "dg_operator_ndofs", "dg_operator_stats", "dg_operator_set_kappa", "dg_apply",
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
-    "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal",
+    "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
 ]
 
 
@@ -104,6 +104,7 @@ def lib():
         L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_diagonal.argtypes = [vp, vp, vp]
+        L.dg_operator_block_jacobi.argtypes = [vp, vp, vp, i32, vp]
         L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
@@ -233,6 +234,10 @@ def dg_operator_diagonal(op: int, diag_ptr: int, stream: Optional[int]):
     _check(lib().dg_operator_diagonal(op, diag_ptr, stream), "dg_operator_diagonal")
 
 
+def dg_operator_block_jacobi(op: int, r_ptr: int, z_ptr: int, nrhs: int, stream: Optional[int]):
+    _check(lib().dg_operator_block_jacobi(op, r_ptr, z_ptr, nrhs, stream), "dg_operator_block_jacobi")
+
+
 def dg_operator_profile(op: int, enable: bool):
     _check(lib().dg_operator_profile(op, int(enable)), "dg_operator_profile")
 
@@ -349,6 +354,18 @@ class Operator:
         dg_rhs(self.handle, None if f_vol is None else _dev_ptr(f_vol, self.dtype, "f_vol"),
                None if g_face is None else _dev_ptr(g_face, self.dtype, "g_face"), F.data_ptr(), _stream_ptr(stream))
         return F
+
+    def block_jacobi(self, r, z=None, stream=None):
+        """z = A_cc^-1 r per cell (cell-block Jacobi) for r of shape [ndofs] or [nrhs, ndofs]."""
+        import torch
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        if r.numel() != nrhs * self.ndofs:
+            raise ValueError("r has the wrong size")
+        if z is None:
+            z = torch.empty_like(r)
+        dg_operator_block_jacobi(self.handle, _dev_ptr(r, self.dtype, "r"), _dev_ptr(z, self.dtype, "z"), nrhs,
+                                 _stream_ptr(stream))
+        return z
 
     def apply_host(self, x, y, stream=None):
         """y = A x through host buffers (numpy arrays or CPU tensors, ideally pinned)."""

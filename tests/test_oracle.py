@@ -460,3 +460,47 @@ def test_rhs_linear_solution_all_cells_perturbed(k, theta):
     Au = p.apply(u)
     res = Au - p.rhs(None, gg)
     assert np.abs(res).max() < 1e-12 * np.abs(Au).max()
+
+
+@pytest.mark.parametrize("n,k,mask,c", [((3, 2, 4), 2, 0b111111, 1.0), ((1, 3, 2), 3, 0b010110, 0.5),
+                                        ((2, 2, 2), 1, 0, 1.0), ((4, 1, 1), 4, 0b101010, 2.0)])
+def test_block_jacobi_cell_blocks_are_kronecker_sums(n, k, mask, c):
+    # Each cell's diagonal block of the assembled affine matrix must equal the Kronecker
+    # sum of the 1D diagonal blocks of the independent Kronecker construction (the
+    # separability that fast diagonalisation relies on), and block_jacobi must invert it.
+    orc = oracle.Problem(*n, k, dirichlet_mask=mask, c=c)
+    A = orc.assemble()
+    b = kr.Basis1D(kr.gll_points(k))
+    p = k + 1
+    M = [kr.mass_1d(b, b, n[a], 1.0 / n[a]).toarray() for a in range(3)]
+    S = [kr.sipg_1d(b, n[a], 1.0 / n[a], kr.gamma_axis(k, n[a], 2.0, 0), -1.0, bool(mask >> (2 * a) & 1),
+                    bool(mask >> (2 * a + 1) & 1)).toarray() for a in range(3)]
+    r = wl.uniform_vector(orc.ndofs(), 5)
+    z = orc.block_jacobi(r)
+
+    def blk(X, e):
+        return X[e * p:(e + 1) * p, e * p:(e + 1) * p]
+
+    for cell in range(orc.ncell):
+        cx, cy, cz = cell % n[0], (cell // n[0]) % n[1], cell // (n[0] * n[1])
+        Mx, My, Mz = blk(M[0], cx), blk(M[1], cy), blk(M[2], cz)
+        Kc = (np.kron(Mz, np.kron(My, blk(S[0], cx))) + np.kron(Mz, np.kron(blk(S[1], cy), Mx))
+              + np.kron(blk(S[2], cz), np.kron(My, Mx)) + c * np.kron(Mz, np.kron(My, Mx)))
+        sl = slice(cell * p ** 3, (cell + 1) * p ** 3)
+        assert np.abs(A[sl, sl].toarray() - Kc).max() <= 1e-12 * np.abs(Kc).max()
+        assert np.abs(Kc @ z[sl] - r[sl]).max() <= 1e-10 * np.abs(r).max()
+
+
+def test_block_jacobi_inverts_single_cell_columns():
+    # for x supported on one cell c, (A x)_c = A_cc x_c, so block_jacobi(A x) returns x on c
+    orc = oracle.Problem(3, 3, 2, 2, dirichlet_mask=0b011011)
+    A = orc.assemble()
+    loc = 27
+    for cell in (0, 7, 17):
+        x = np.zeros(orc.ndofs())
+        x[cell * loc:(cell + 1) * loc] = wl.uniform_vector(loc, cell)
+        z = orc.block_jacobi(A @ x)
+        assert np.abs(z[cell * loc:(cell + 1) * loc] - x[cell * loc:(cell + 1) * loc]).max() <= 1e-11
+    # B = blockdiag(A)^-1 is symmetric for theta = -1
+    u, v = wl.uniform_vector(orc.ndofs(), 1), wl.uniform_vector(orc.ndofs(), 2)
+    assert abs(u @ orc.block_jacobi(v) - v @ orc.block_jacobi(u)) <= 1e-12 * abs(u @ orc.block_jacobi(v))
