@@ -207,6 +207,105 @@ __global__ void __launch_bounds__(256) k_block_jacobi(const BJTab<P, T> tb, cons
   }
 }
 
+// The same for FP32 and k <= 2 with one thread per cell and the cell in registers: a block of 128
+// threads takes 128 consecutive cells (r and z staged through shared memory for coalesced
+// rows), and each axis sweep is instantiated for the four cell positions with the table
+// entries as constant-bank operands. The 32 consecutive cells of a warp share their y and z
+// positions unless a row is shorter than a warp, so only the x sweeps diverge, and only in
+// warps holding a first or last cell of a row.
+template <int P, typename T, int AX, bool TR>
+__device__ __forceinline__ void bj_sweep_pos(const BJTab<P, T> &tb, int pos, const T *in, T *out) {
+  constexpr int P2 = P * P;
+  auto run = [&](const T *S) {
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        // line (a, b) over the two other axes in increasing order
+        auto idx = [&](int i) { return AX == 0 ? i + P * a + P2 * b : (AX == 1 ? a + P * i + P2 * b : a + P * b + P2 * i); };
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          T s = T(0);
+#pragma unroll
+          for (int j = 0; j < P; ++j) s = fma(TR ? S[j * P + i] : S[i * P + j], in[idx(j)], s);
+          out[idx(i)] = s;
+        }
+      }
+  };
+  switch (pos) {
+    case 0: run(tb.S[AX][0]); break;
+    case 1: run(tb.S[AX][1]); break;
+    case 2: run(tb.S[AX][2]); break;
+    default: run(tb.S[AX][3]); break;
+  }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(128) k_block_jacobi_cell(const BJTab<P, T> tb, const T *__restrict__ dinv,
+                                                           const T *__restrict__ r, T *__restrict__ z, int nx, int ny,
+                                                           int nz, int64_t ncell, int64_t sdof, double *partial,
+                                                           int stride) {
+  constexpr int P3 = P * P * P, sX = P3 | 1, NB = 128;
+  __shared__ T st[NB * sX];
+  auto position = [](int c, int n) { return n == 1 ? 3 : (c == 0 ? 1 : (c == n - 1 ? 2 : 0)); };
+  const int tid = threadIdx.x;
+  const int64_t nchunks = (ncell + NB - 1) / NB;
+  double dot = 0.0;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t c0 = ch * NB;
+    const int nc = (int)min((int64_t)NB, ncell - c0);
+    const T *rr = r + blockIdx.y * sdof + c0 * P3;
+    T *zz = z + blockIdx.y * sdof + c0 * P3;
+    __syncthreads();  // the previous chunk's z rows were read out
+    for (int i = tid; i < nc * P3; i += NB) {
+      const int c = i / P3;
+      st[c * sX + (i - c * P3)] = rr[i];
+    }
+    __syncthreads();
+    if (tid < nc) {
+      const int64_t cell = c0 + tid, cyz = cell / nx;
+      const int px = position((int)(cell - cyz * nx), nx), py = position((int)(cyz % ny), ny),
+                pz = position((int)(cyz / ny), nz);
+      T u[P3], v[P3];
+#pragma unroll
+      for (int i = 0; i < P3; ++i) u[i] = st[tid * sX + i];
+      bj_sweep_pos<P, T, 0, true>(tb, px, u, v);
+      bj_sweep_pos<P, T, 1, true>(tb, py, v, u);
+      bj_sweep_pos<P, T, 2, true>(tb, pz, u, v);
+      const T *di = dinv + (16 * px + 4 * py + pz) * P3;
+#pragma unroll
+      for (int i = 0; i < P3; ++i) v[i] *= __ldg(di + i);
+      bj_sweep_pos<P, T, 2, false>(tb, pz, v, u);
+      bj_sweep_pos<P, T, 1, false>(tb, py, u, v);
+      bj_sweep_pos<P, T, 0, false>(tb, px, v, u);
+      T g = T(0);  // r.z of the cell (FP32 groups for FP32 vectors), then FP64
+#pragma unroll
+      for (int i = 0; i < P3; ++i) {
+        g = fma(st[tid * sX + i], u[i], g);
+        st[tid * sX + i] = u[i];
+      }
+      dot += (double)g;
+    }
+    __syncthreads();
+    for (int i = tid; i < nc * P3; i += NB) {
+      const int c = i / P3;
+      zz[i] = st[c * sX + (i - c * P3)];
+    }
+  }
+  if (partial) {
+    __shared__ double part[NB / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+    if ((tid & 31) == 0) part[tid >> 5] = dot;
+    __syncthreads();
+    if (tid == 0) {
+      double w = 0.0;
+      for (int i = 0; i < NB / 32; ++i) w += part[i];
+      partial[blockIdx.y * stride + blockIdx.x] = w;
+    }
+  }
+}
+
 template <int P, typename T>
 cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int64_t ncell, const T *r, T *z, int nrhs,
                    int64_t sdof, double *partial, int stride, int *blocks, cudaStream_t s) {
@@ -216,6 +315,16 @@ cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int
       const double *src = tab + (d * 4 + pos) * (P * P + P);
       for (int i = 0; i < P * P; ++i) tb.S[d][pos][i] = (T)src[i];
     }
+  if constexpr (P <= 3 && sizeof(T) == 4) {  // one thread per cell (FP64 stays on the lines: fewer registers, no divergence)
+    const int64_t nchunks = (ncell + 127) / 128;
+    int64_t nb = (16 * 152) / nrhs > 0 ? (16 * 152) / nrhs : 1;
+    if (partial && nb > stride) nb = stride;
+    if (nb > nchunks) nb = nchunks;
+    if (blocks) *blocks = (int)nb;
+    k_block_jacobi_cell<P, T><<<dim3((unsigned)nb, nrhs), 128, 0, s>>>(tb, dinv, r, z, nx, ny, nz, ncell, sdof,
+                                                                        partial, stride);
+    return cudaGetLastError();
+  }
   const int cpb = 256 / (P * P) > 0 ? 256 / (P * P) : 1;
   const int threads = ((cpb * P * P + 31) / 32) * 32;
   const size_t sm = 2 * (size_t)cpb * P * P * P * sizeof(T);
