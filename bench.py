@@ -36,6 +36,8 @@ METRIC = "dg_apply DOF/s (FP64 and mixed) at Q2-Q5; % of FP64-peak / HBM rooflin
 N_CELLS = 64
 SM_COUNT = 152
 VARIANT_NAMES = {1: "three-kernel", 2: "fused persistent", 3: "cellwise persistent"}
+PRECOND_NAMES = {0: "none", 1: "point Jacobi (diagonal set up outside the timed solves)",
+                 2: "cell-block Jacobi by fast diagonalisation (set up outside the timed solves)"}
 FP64_FLOPS_PER_SM_CLK = 4.0   # 2 DFMA per SM per clock: 1.25 TFLOP/s nominal at 2.07 GHz
 FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FFMA per SM per clock
 # DRAM bytes (read + write) of one k_cell launch from the ncu capture of the 40^3 Q3 case
@@ -317,16 +319,16 @@ def run_solve(args):
     stream = torch.cuda.current_stream().cuda_stream
     out = {"mode": "solve", "workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides",
            "ndofs": op64.ndofs, "rtol": args.solve_rtol,
-           "preconditioner": {0: "none", 1: "point Jacobi (diagonal set up outside the timed solves)",
-                              2: "cell-block Jacobi by fast diagonalisation"}[args.precond]}
-    if args.precond:  # set up both diagonals before timing (they are cached by the operators)
-        warm = dg.dg_cg_options(1e-1, 50, 50, 0, args.precond)
-        xz = torch.zeros_like(b)
-        dg.dg_cg_solve(op64.handle, b.data_ptr(), xz.data_ptr(), nrhs, warm, stream)
-        bz = b.float()
-        xz32 = torch.zeros_like(bz)
-        dg.dg_cg_solve(op32.handle, bz.data_ptr(), xz32.data_ptr(), nrhs, warm, stream)
-        del xz, bz, xz32
+           "preconditioner": PRECOND_NAMES[args.precond]}
+    p64 = args.precond if args.precond_fp64 is None else args.precond_fp64
+    if p64 != args.precond:
+        out["preconditioner_fp64_cg"] = PRECOND_NAMES[p64]
+    # set up the preconditioners before timing (the operators keep them)
+    for op, pc, bb in ((op64, p64, b), (op32, args.precond, b.float())):
+        if pc:
+            xz = torch.zeros_like(bb)
+            dg.dg_cg_solve(op.handle, bb.data_ptr(), xz.data_ptr(), nrhs, dg.dg_cg_options(1e-1, 50, 50, 0, pc), stream)
+            del xz
 
     def check(x):
         r = b - op64.apply(x)
@@ -346,7 +348,7 @@ def run_solve(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     ok, info = dg.dg_cg_solve(op64.handle, b.data_ptr(), x.data_ptr(), nrhs,
-                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, args.precond), stream)
+                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, p64), stream)
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t
     out["fp64_cg"] = {"seconds": t64, "converged": ok, "iters_max": max(i["iters"] for i in info),
@@ -478,6 +480,8 @@ def main():
     ap.add_argument("--fp64-max-iters", type=int, default=20000)
     ap.add_argument("--precond", type=int, default=0, choices=(0, 1, 2),
                     help="0: none, 1: point Jacobi, 2: cell-block Jacobi (both solvers)")
+    ap.add_argument("--precond-fp64", type=int, default=None, choices=(0, 1, 2),
+                    help="preconditioner of the FP64 CG if it differs from --precond")
     args = ap.parse_args()
     global N_CELLS
     N_CELLS = args.cells
