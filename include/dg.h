@@ -180,6 +180,39 @@ typedef struct {
  * synchronises the stream. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_result *out);
 
+/* Launch cost model (Sec. 4's heuristic cost function cost = flops x ilp x loads, with
+ * ilp = 1 + c0 log2(s), loads = 1 + c1 log2(p), c0 = 0.5, c1 = 0.25, carried to the GPU):
+ * the predicted milliseconds of one apply of nrhs right-hand sides of the scalar operator
+ * in the given configuration (variant DG_VARIANT_THREE_KERNEL with cells_per_block and
+ * faces_per_block, or DG_VARIANT_FUSED / DG_VARIANT_CELLWISE with cells_per_block the
+ * row tile / brick). Per kernel: the roofline time max(flops / peak of the precision,
+ * bytes / HBM bandwidth) from the operator's exact work model, times 1 + c0 log2(16 / w)
+ * for w < 16 resident warps per SM (the occupancy calculator's figure for the kernel at
+ * that blocking), times the loads term with p = k+1, times the tail of the last partly
+ * empty wave, plus 50 ns per block (per work item of a persistent kernel) and SM for what
+ * each block loads before its first useful operation. It ranks the blockings of one
+ * variant; it does not capture the latency-bound efficiency of the persistent FP32
+ * variants, so choices between variants are measured. Launches nothing. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (Stokes,
+ * recomputed geometry, a variant or blocking the operator does not cover), DG_ERR_CUDA. */
+dg_status dg_operator_predict(const dg_operator *op, int nrhs, int variant, int cells_per_block,
+                              int faces_per_block, double *ms);
+
+/* Mean CUDA-event milliseconds of one apply of nrhs right-hand sides in the given
+ * configuration (arguments as dg_operator_predict), on scratch vectors the call allocates
+ * and frees; the operator's own configuration is unchanged. Synchronises the stream.
+ * Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_operator_time(const dg_operator *op, int nrhs, int variant, int cells_per_block,
+                           int faces_per_block, void *stream, double *ms);
+
+/* Tuner with the cost model as prior: ranks the candidate blockings of each variant the
+ * scalar operator supports by dg_operator_predict, times the first `measure` of each
+ * variant and keeps the fastest timed configuration.
+ * out->candidates = configurations timed, ms_best = the kept one's time, ms_default = the
+ * model's prediction for its own first choice. Errors as dg_operator_autotune, and
+ * DG_ERR_UNSUPPORTED for Stokes and recomputed geometry. */
+dg_status dg_operator_autotune_prior(dg_operator *op, int nrhs, int measure, void *stream,
+                                     dg_tune_result *out);
+
 /* Per-quadrature-point diffusion coefficient kappa (scalar problem): device arrays of
  * the operator's precision, kappa_vol [ncell][m^3] (points q0 + m(q1 + m q2)) and
  * kappa_face [ncell][6][m^2] (each cell's own side of faces -x,+x,-y,+y,-z,+z, points

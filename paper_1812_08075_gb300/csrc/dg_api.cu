@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -664,6 +665,228 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
   } while (0);
   if (st != DG_OK) {
     op->variant = save_v; op->cpb = save_c; op->fpb = save_f; op->tile = save_t; op->brick = save_b;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(x);
+  cudaFree(y);
+  return st;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Launch cost model: Sec. 4's heuristic cost function (cost = flops x ilp x loads with
+// ilp = 1 + c0 log2(s) over the splitting s, loads = 1 + c1 log2(p) over the coefficients
+// p, c0 = 0.5, c1 = 0.25) carried to the GPU. flops becomes the roofline time of a kernel
+// from the exact work models, max(flops / peak of its precision, bytes / HBM bandwidth);
+// the ILP term penalises latency that too few resident warps cannot hide,
+// 1 + c0 log2(16 / warps per SM) below 16 warps (the occupancy calculator's count for the
+// kernel at that blocking); the loads term keeps the paper's form with p = k+1, plus a
+// fixed 50 ns per block (per work item for persistent kernels) and SM for what every block
+// loads before its first useful operation (the reference tables, index setup, the first
+// barrier; fitted on three workloads: one-cell blocks cost 0.2-0.4 ms more than 32-cell
+// ones at 40^3 x 4 right-hand sides); and a tail term charges the last, partly empty wave
+// of blocks (for persistent kernels, the last round of items). A configuration's cost is
+// the sum over its kernels. The model ranks the blockings of one variant; it does not
+// capture the latency-bound efficiency of the persistent FP32 variants, so the choice
+// between variants is left to measurement.
+
+namespace {
+
+struct Candidate {
+  int variant, cpb, fpb;  // cpb: cells per block, row tile (fused) or brick (cellwise)
+};
+
+constexpr double kPeakFP64 = 152 * 2 * 2 * 2.07e9;    // 2 DFMA per SM per clock at 2070 MHz
+constexpr double kPeakFP32 = 152 * 128 * 2 * 2.07e9;  // 128 FFMA per SM per clock
+constexpr double kHBM = 6.6785e12;                     // copy bandwidth measured on this part
+
+double kernel_cost_ms(double flops, double bytes, const LaunchInfo &q, bool fp64, int p) {
+  if (q.blocks_per_sm <= 0 || q.blocks <= 0) return 1e30;
+  const double t = fmax(flops / (fp64 ? kPeakFP64 : kPeakFP32), bytes / kHBM);
+  const double warps = (double)q.blocks_per_sm * ((q.threads + 31) / 32);
+  const double ilp = 1.0 + 0.5 * log2(fmax(1.0, 16.0 / warps));
+  const double loads = 1.0 + 0.25 * log2((double)p);
+  double tail;
+  if (q.items > q.blocks) {  // persistent: rounds of items over the grid
+    const double r = (double)q.items / (double)q.blocks;
+    tail = ceil(r) / r;
+  } else {
+    const double w = (double)q.blocks / ((double)q.blocks_per_sm * 152.0);
+    tail = ceil(w) / w;
+  }
+  const double per_block = 50e-9 * (double)(q.items > q.blocks ? q.items : q.blocks) / 152.0;
+  return (t * ilp * loads * tail + per_block) * 1e3;
+}
+
+void enumerate_candidates(const dg_operator *op, std::vector<Candidate> &c) {
+  c.clear();
+  const int cand_c[] = {1, 2, 4, 8, 16, 32}, cand_f[] = {2, 4, 8, 16, 32, 64};
+  const size_t es = op->precision == DG_FP64 ? 8 : 4;
+  const int M = op->m, M2 = M * M, M3 = M2 * M, P = op->p;
+  const bool stokes = op->problem == DG_STOKES;
+  for (int cc : cand_c) {
+    const size_t per = (size_t)(stokes ? 12 : 4) * M3 * es + (stokes ? 42 : 12) * M2 * es;
+    if (cc * per + 4096 > 160 * 1024 || cc * M3 > 8192) continue;
+    for (int ff : cand_f) {
+      if ((size_t)ff * 13 * M2 * es + 4096 > 160 * 1024 || ff * M2 > 8192) continue;
+      c.push_back({DG_VARIANT_THREE_KERNEL, cc, ff});
+    }
+  }
+  if (fused_ok(op))
+    for (int t : {2, 4, 8, 16, 32, 64})
+      if ((size_t)t * (6 * P * P * P + 40 * P * P) * es + 4096 <= 160 * 1024 && t * P * P <= 1024)
+        c.push_back({DG_VARIANT_FUSED, t, 0});
+  if (cellwise_ok(op))
+    for (int b : {64, 128, 256}) {
+      const size_t sm = cellwise_smem_bytes(P, b, (int)es);
+      if (sm && sm <= kMaxSmemBlock) c.push_back({DG_VARIANT_CELLWISE, b, 0});
+    }
+}
+
+template <typename T>
+dg_status predict_t(const dg_operator *op, int nrhs, const Candidate &c, double *ms) {
+  LaunchInfo q[3];
+  double flops[3] = {0, 0, 0}, bytes[3] = {0, 0, 0};
+  const int es = sizeof(T);
+  cudaError_t e;
+  int nk = 1;
+  const ScalarArgs<T> a = scalar_args<T>(op, false);
+  if (c.variant == DG_VARIANT_FUSED) {
+    fused_work_model(op->p, op->ncell, op->nbface, flops, bytes, es);
+    e = launch_fused_apply<T>(op->p, a, op->ht, nullptr, nullptr, nrhs, op->ndofs, c.cpb, 0, nullptr, nullptr, q);
+  } else if (c.variant == DG_VARIANT_CELLWISE) {
+    cellwise_work_model(op->p, op->nx, op->ny, op->nz, c.cpb, op->nbface, flops, bytes, es);
+    e = launch_cellwise_apply<T>(op->p, a, op->ht, nullptr, nullptr, nrhs, op->ndofs, c.cpb, 0, nullptr, nullptr, q);
+  } else {
+    scalar_work_model(op->p, op->m, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface, flops, bytes,
+                      es);
+    const int M2 = op->m * op->m, M3 = M2 * op->m;
+    e = launch_scalar_apply<T>(op->p, op->m, op->geo, op->kappa_vol != nullptr, a, nullptr, nullptr, nullptr, nullptr,
+                               nullptr, nrhs, op->ndofs, op->ncell * M3, op->ncell * 12 * M2, c.cpb, c.fpb, 0, nullptr,
+                               q);
+    nk = 3;
+  }
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  double t = 0.0;
+  for (int k = 0; k < nk; ++k) t += kernel_cost_ms(flops[k] * nrhs, bytes[k] * nrhs, q[k], es == 8, op->p);
+  *ms = t;
+  return DG_OK;
+}
+
+dg_status predict(const dg_operator *op, int nrhs, const Candidate &c, double *ms) {
+  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+  if (!variant_ok(op, c.variant)) return fail(DG_ERR_UNSUPPORTED);
+  return op->precision == DG_FP64 ? predict_t<double>(op, nrhs, c, ms) : predict_t<float>(op, nrhs, c, ms);
+}
+
+// Applies op in configuration c a few times on scratch vectors; mean CUDA-event time.
+dg_status time_candidate(dg_operator *op, int nrhs, const Candidate &c, const void *x, void *y, cudaStream_t s,
+                         double *ms) {
+  const int sv = op->variant, sc = op->cpb, sf = op->fpb, st = op->tile, sb = op->brick;
+  op->variant = c.variant;
+  if (c.variant == DG_VARIANT_FUSED) op->tile = c.cpb;
+  else if (c.variant == DG_VARIANT_CELLWISE) op->brick = c.cpb;
+  else { op->cpb = c.cpb; op->fpb = c.fpb; }
+  double k3[3];
+  dg_status r = time_kernels(op, x, y, nrhs, s, 1, 3, k3);
+  op->variant = sv; op->cpb = sc; op->fpb = sf; op->tile = st; op->brick = sb;
+  if (r == DG_OK) *ms = k3[0] + k3[1] + k3[2];
+  return r;
+}
+
+bool scratch_vectors(const dg_operator *op, int nrhs, void **x, void **y, cudaStream_t s) {
+  const size_t bytes = (size_t)nrhs * op->ndofs * (op->precision == DG_FP64 ? 8 : 4);
+  *x = *y = nullptr;
+  if (cudaMalloc(x, bytes) != cudaSuccess || cudaMalloc(y, bytes) != cudaSuccess ||
+      cudaMemsetAsync(*x, 0, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (*x) cudaFree(*x);
+    if (*y) cudaFree(*y);
+    *x = *y = nullptr;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_operator_predict(const dg_operator *op, int nrhs, int variant, int cells_per_block, int faces_per_block,
+                              double *ms) {
+  if (!op || !ms || nrhs < 1 || nrhs > op->max_rhs || cells_per_block < 1) return fail(DG_ERR_INVALID_ARG);
+  if (variant == DG_VARIANT_THREE_KERNEL && faces_per_block < 1) return fail(DG_ERR_INVALID_ARG);
+  if (variant == DG_VARIANT_CELLWISE) {
+    const size_t sm = cellwise_smem_bytes(op->p, cells_per_block, op->precision == DG_FP64 ? 8 : 4);
+    if (sm == 0 || sm > kMaxSmemBlock) return fail(DG_ERR_UNSUPPORTED);
+  }
+  return predict(op, nrhs, {variant, cells_per_block, faces_per_block}, ms);
+}
+
+dg_status dg_operator_time(const dg_operator *op_c, int nrhs, int variant, int cells_per_block, int faces_per_block,
+                           void *stream, double *ms) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !ms || nrhs < 1 || nrhs > op->max_rhs || cells_per_block < 1) return fail(DG_ERR_INVALID_ARG);
+  if (variant == DG_VARIANT_THREE_KERNEL && faces_per_block < 1) return fail(DG_ERR_INVALID_ARG);
+  if (variant < DG_VARIANT_THREE_KERNEL || variant > DG_VARIANT_CELLWISE || !variant_ok(op, variant))
+    return fail(DG_ERR_UNSUPPORTED);
+  if (variant == DG_VARIANT_CELLWISE) {
+    const size_t sm = cellwise_smem_bytes(op->p, cells_per_block, op->precision == DG_FP64 ? 8 : 4);
+    if (sm == 0 || sm > kMaxSmemBlock) return fail(DG_ERR_UNSUPPORTED);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  void *x, *y;
+  if (!scratch_vectors(op, nrhs, &x, &y, s)) return fail(DG_ERR_OOM);
+  dg_status r = time_candidate(op, nrhs, {variant, cells_per_block, faces_per_block}, x, y, s, ms);
+  cudaStreamSynchronize(s);
+  cudaFree(x);
+  cudaFree(y);
+  return r;
+}
+
+dg_status dg_operator_autotune_prior(dg_operator *op, int nrhs, int measure, void *stream, dg_tune_result *out) {
+  if (!op || !out || nrhs < 1 || nrhs > op->max_rhs || measure < 1) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+  memset(out, 0, sizeof(*out));
+  std::vector<Candidate> cand;
+  enumerate_candidates(op, cand);
+  std::vector<std::pair<double, int>> ranked;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    double ms;
+    if (predict(op, nrhs, cand[i], &ms) == DG_OK) ranked.push_back({ms, (int)i});
+  }
+  dg_get_last_error();  // predictions of configurations that cannot launch are skipped
+  if (ranked.empty()) return fail(DG_ERR_UNSUPPORTED);
+  std::sort(ranked.begin(), ranked.end());
+  cudaStream_t s = (cudaStream_t)stream;
+  void *x, *y;
+  if (!scratch_vectors(op, nrhs, &x, &y, s)) return fail(DG_ERR_OOM);
+  dg_status st = DG_OK;
+  double best = 1e30;
+  int bi = -1;
+  int taken[4] = {0, 0, 0, 0};  // per variant: its `measure` best-ranked blockings are timed
+  for (size_t i = 0; i < ranked.size() && st == DG_OK; ++i) {
+    const Candidate &c = cand[ranked[i].second];
+    if (taken[c.variant] >= measure) continue;
+    ++taken[c.variant];
+    double ms;
+    st = time_candidate(op, nrhs, c, x, y, s, &ms);
+    if (st != DG_OK) break;
+    ++out->candidates;
+    if (ms < best) { best = ms; bi = ranked[i].second; }
+  }
+  if (st == DG_OK) {
+    const Candidate &c = cand[bi];
+    op->variant = c.variant;
+    if (c.variant == DG_VARIANT_FUSED) op->tile = c.cpb;
+    else if (c.variant == DG_VARIANT_CELLWISE) op->brick = c.cpb;
+    else { op->cpb = c.cpb; op->fpb = c.fpb; }
+    out->variant = c.variant;
+    out->cells_per_block = c.cpb;
+    out->faces_per_block = c.fpb;
+    out->ms_best = best;
+    out->ms_default = ranked[0].first;  // the model's own prediction for its first choice
   }
   cudaStreamSynchronize(s);
   cudaFree(x);

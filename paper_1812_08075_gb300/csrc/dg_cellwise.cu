@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256) k_cellwise(const ScalarArgs<T> a, const C
 
 template <int P, typename T, int BZ>
 cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof,
-                cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+                cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
   constexpr int M = P, M2 = M * M, M3 = M2 * M;
   constexpr int bx = 8, by = 4, bz = BZ, nb = bx * by * bz;
   CTab<P, T> tb;
@@ -432,6 +432,13 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
   int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
   if (grid > nitems) grid = nitems;
   if (grid_out) *grid_out = (int)grid;
+  if (q) {
+    q->blocks = grid;
+    q->threads = nb;
+    q->blocks_per_sm = per_sm;
+    q->items = nitems;
+    return cudaSuccess;
+  }
   if (ev) cudaEventRecord(ev[0], s);
   k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, nbx, nby, nbricks, nitems);
   if (ev) {
@@ -459,29 +466,31 @@ size_t cellwise_smem_bytes(int p, int cells, int es) {
 
 template <int P, typename T>
 static cudaError_t run_bz(int bz, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
-                          int64_t sdof, cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+                          int64_t sdof, cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
   switch (bz) {
-    case 2: return dgc::run<P, T, 2>(a, ht, x, y, nrhs, sdof, s, ev, grid_out);
-    case 4: return dgc::run<P, T, 4>(a, ht, x, y, nrhs, sdof, s, ev, grid_out);
-    case 8: return dgc::run<P, T, 8>(a, ht, x, y, nrhs, sdof, s, ev, grid_out);
+    case 2: return dgc::run<P, T, 2>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
+    case 4: return dgc::run<P, T, 4>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
+    case 8: return dgc::run<P, T, 8>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
 cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
-                                  int64_t sdof, int cells, cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+                                  int64_t sdof, int cells, cudaStream_t s, const cudaEvent_t *ev, int *grid_out,
+                                  LaunchInfo *q) {
   if (ht.m != p || ht.p != p) return cudaErrorInvalidValue;
   const int bz = cellwise_bz(cells);
   switch (p) {
-    case 2: return run_bz<2, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out);
-    case 3: return run_bz<3, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out);
+    case 2: return run_bz<2, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
+    case 3: return run_bz<3, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_cellwise_apply<float>(int, const ScalarArgs<float> &, const HostTables &, const float *,
-                                                  float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *);
+                                                  float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *,
+                                                  LaunchInfo *);
 template cudaError_t launch_cellwise_apply<double>(int, const ScalarArgs<double> &, const HostTables &,
                                                    const double *, double *, int, int64_t, int, cudaStream_t,
-                                                   const cudaEvent_t *, int *);
+                                                   const cudaEvent_t *, int *, LaunchInfo *);

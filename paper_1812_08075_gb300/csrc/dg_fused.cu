@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(1024) k_fused(const ScalarArgs<T> a, const FTa
 
 template <int P, typename T>
 cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof, int tile,
-                cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+                cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
   FTab<P, T> tb;
   for (int i = 0; i < P * P; ++i) { tb.interp[i] = (T)ht.interp[i]; tb.dcol[i] = (T)ht.dcol[i]; }
   for (int i = 0; i < P; ++i) {
@@ -375,6 +375,13 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
   int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
   if (grid > nitems) grid = nitems;
   if (grid_out) *grid_out = (int)grid;
+  if (q) {
+    q->blocks = grid;
+    q->threads = threads;
+    q->blocks_per_sm = per_sm;
+    q->items = nitems;
+    return cudaSuccess;
+  }
   if (ev) cudaEventRecord(ev[0], s);
   k<<<(unsigned)grid, threads, sm, s>>>(a, tb, x, y, sdof, tile, tiles_x, nitems);
   if (ev) {
@@ -389,19 +396,22 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
 
 template <typename T>
 cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
-                               int64_t sdof, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out) {
+                               int64_t sdof, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out,
+                               LaunchInfo *q) {
   if (ht.m != p || ht.p != p) return cudaErrorInvalidValue;
   switch (p) {
-    case 2: return dgf::run<2, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 3: return dgf::run<3, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 4: return dgf::run<4, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 5: return dgf::run<5, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
-    case 6: return dgf::run<6, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out);
+    case 2: return dgf::run<2, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out, q);
+    case 3: return dgf::run<3, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out, q);
+    case 4: return dgf::run<4, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out, q);
+    case 5: return dgf::run<5, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out, q);
+    case 6: return dgf::run<6, T>(a, ht, x, y, nrhs, sdof, tile, s, ev, grid_out, q);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_fused_apply<float>(int, const ScalarArgs<float> &, const HostTables &, const float *,
-                                               float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *);
+                                               float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *,
+                                               LaunchInfo *);
 template cudaError_t launch_fused_apply<double>(int, const ScalarArgs<double> &, const HostTables &, const double *,
-                                                double *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *);
+                                                double *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *,
+                                                LaunchInfo *);

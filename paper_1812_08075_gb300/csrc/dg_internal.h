@@ -75,12 +75,23 @@ struct ScalarArgs {
   T sc, ss;                 // face flux / symmetry coefficients (forward: -1, theta)
 };
 
+// Launch shape of one kernel, filled instead of launching when a launcher gets a non-NULL
+// query (used by the cost model): blocks launched, threads per block, resident blocks per
+// SM (occupancy calculator) and, for persistent kernels, work items per launch.
+struct LaunchInfo {
+  int64_t blocks = 0;
+  int threads = 0;
+  int blocks_per_sm = 0;
+  int64_t items = 0;
+};
+
 // Launchers (dg_scalar.cu). Return cudaError_t of the launch.
 template <typename T>
 cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a,
                                 const T *x, T *y, T *rvol, T *traces, T *fres, int nrhs,
                                 int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
-                                int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
+                                int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
+                                LaunchInfo *query = nullptr);
 
 // Adjoint of the scalar operator (dg_adjoint.cu, FP64): y = A^T r with a.sc/a.ss set for
 // the transpose, and, when x is non-NULL, dkappa at every volume and face point for the
@@ -96,14 +107,15 @@ cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<d
 // neighbours' face data from their coefficients, so no scratch memory is used.
 template <typename T>
 cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
-                               int64_t stride_dofs, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out);
+                               int64_t stride_dofs, int tile, cudaStream_t s, const cudaEvent_t *ev, int *grid_out,
+                               LaunchInfo *query = nullptr);
 
 // One-thread-per-cell persistent apply for affine meshes, degree k <= 2 (dg_cellwise.cu):
 // bricks of 8 x 4 x (cells / 32) cells per block, cells = 64, 128 or 256.
 template <typename T>
 cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
                                   int64_t stride_dofs, int cells, cudaStream_t s, const cudaEvent_t *ev,
-                                  int *grid_out);
+                                  int *grid_out, LaunchInfo *query = nullptr);
 size_t cellwise_smem_bytes(int p, int cells, int es);  // 0 if (p, cells) is not supported
 
 // Cell-block Jacobi preconditioner by fast diagonalisation (dg_precond.cu): host tables

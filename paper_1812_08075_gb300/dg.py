@@ -31,6 +31,7 @@ EXPORTED = [
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
+    "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior",
 ]
 
 
@@ -105,6 +106,9 @@ def lib():
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_diagonal.argtypes = [vp, vp, vp]
         L.dg_operator_block_jacobi.argtypes = [vp, vp, vp, i32, vp]
+        L.dg_operator_predict.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
+        L.dg_operator_time.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.dg_operator_autotune_prior.argtypes = [vp, i32, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
@@ -236,6 +240,27 @@ def dg_operator_diagonal(op: int, diag_ptr: int, stream: Optional[int]):
 
 def dg_operator_block_jacobi(op: int, r_ptr: int, z_ptr: int, nrhs: int, stream: Optional[int]):
     _check(lib().dg_operator_block_jacobi(op, r_ptr, z_ptr, nrhs, stream), "dg_operator_block_jacobi")
+
+
+def dg_operator_predict(op: int, nrhs: int, variant: int, cells_per_block: int, faces_per_block: int = 0) -> float:
+    ms = ctypes.c_double()
+    _check(lib().dg_operator_predict(op, nrhs, variant, cells_per_block, faces_per_block, ctypes.byref(ms)),
+           "dg_operator_predict")
+    return ms.value
+
+
+def dg_operator_time(op: int, nrhs: int, variant: int, cells_per_block: int, faces_per_block: int = 0,
+                     stream: Optional[int] = None) -> float:
+    ms = ctypes.c_double()
+    _check(lib().dg_operator_time(op, nrhs, variant, cells_per_block, faces_per_block, stream, ctypes.byref(ms)),
+           "dg_operator_time")
+    return ms.value
+
+
+def dg_operator_autotune_prior(op: int, nrhs: int, measure: int, stream: Optional[int] = None):
+    r = dg_tune_result()
+    _check(lib().dg_operator_autotune_prior(op, nrhs, measure, stream, ctypes.byref(r)), "dg_operator_autotune_prior")
+    return {f: getattr(r, f) for f, _ in dg_tune_result._fields_}
 
 
 def dg_operator_profile(op: int, enable: bool):
