@@ -63,6 +63,7 @@ def _load():
         lib.oracle_apply_cells.argtypes = [P, ctypes.c_int, dp, ctypes.c_int64, dp, dp, ctypes.c_int]
         lib.oracle_dkappa.argtypes = [P, dp, dp, dp, dp]
         lib.oracle_rhs.argtypes = [P, dp, dp, dp]
+        lib.oracle_semilinear.argtypes = [P, ctypes.c_double, ctypes.c_int, dp, dp, dp]
         lib.oracle_assemble_coo.argtypes = [P, ctypes.c_int64, dp, dp, dp]
         lib.oracle_assemble_coo.restype = ctypes.c_int64
         _lib = lib
@@ -185,6 +186,17 @@ class Problem:
         if _load().oracle_rhs(ctypes.byref(s), _ptr(fv), _ptr(gf), _ptr(F)):
             raise RuntimeError("oracle_rhs failed")
         return F
+
+    def semilinear(self, w: np.ndarray, beta: float, u0: Optional[np.ndarray] = None) -> np.ndarray:
+        """u0 None: A w + beta (w^3, v) (residual operator); else A w + 3 beta (u0^2 w, v)
+        (its Jacobian action at u0)."""
+        s, keep = self._struct()
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        u = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+        y = np.zeros(self.ndofs())
+        if _load().oracle_semilinear(ctypes.byref(s), float(beta), 0 if u is None else 1, _ptr(u), _ptr(w), _ptr(y)):
+            raise RuntimeError("oracle_semilinear failed")
+        return y
 
     def block_jacobi(self, r: np.ndarray) -> np.ndarray:
         """z with A_cc z_c = r_c for every cell c, A_cc the cell's diagonal block of the

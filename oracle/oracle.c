@@ -845,3 +845,49 @@ int oracle_rhs(const oracle_problem *pb, const double *f_vol, const double *g_fa
   }
   return 0;
 }
+
+/* Semilinear reaction (the nonlinear Jacobian action of Sec. 3's discussion, with a cubic
+ * reaction chosen here): residual operator r(u)(v) = a(u, v) + beta (u^3, v), and its
+ * Jacobian action at a linearisation point u0, J(u0) w = A w + 3 beta (u0^2 w, v).
+ * mode 0: y = A w + beta (w^3, v) (u0 unused); mode 1: y = A w + 3 beta (u0^2 w, v).
+ * The reaction integrals use the operator's Gauss rule and full basis evaluation. */
+int oracle_semilinear(const oracle_problem *pb, double beta, int mode, const double *u0, const double *w,
+                      double *y) {
+  if (pb->problem != 0 || (mode != 0 && mode != 1) || (mode == 1 && !u0)) return 1;
+  int st = oracle_apply(pb, 0, w, y);
+  if (st) return st;
+  octx o;
+  if (ctx_init(&o, pb)) return 1;
+  const int P3 = o.P3, m = o.m, L = o.L;
+  double *we = malloc(sizeof(double) * 3 * L);
+  if (!we) return 2;
+  double *ue = we + L, *ye = we + 2 * L;
+  static __thread double phi[OMAXP3], g[OMAXP3][3];
+  for (int64_t c = 0; c < o.ncell; ++c) {
+    double V[8][3], J[3][3], Ji[3][3], xi[3];
+    gather(&o, c, w, we);
+    if (mode == 1) gather(&o, c, u0, ue);
+    memset(ye, 0, sizeof(double) * L);
+    cell_vertices(&o, c, V);
+    for (int q2 = 0; q2 < m; ++q2)
+      for (int q1 = 0; q1 < m; ++q1)
+        for (int q0 = 0; q0 < m; ++q0) {
+          xi[0] = o.s[q0]; xi[1] = o.s[q1]; xi[2] = o.s[q2];
+          const double W = o.w[q0] * o.w[q1] * o.w[q2];
+          map_jacobian(V, xi, J);
+          const double dJ = det3(J);
+          inv3(J, dJ, Ji);
+          basis3d(o.p, o.zv, xi, Ji, phi, g);
+          double wq = 0.0, uq = 0.0;
+          for (int j = 0; j < P3; ++j) {
+            wq += we[j] * phi[j];
+            if (mode == 1) uq += ue[j] * phi[j];
+          }
+          const double coef = mode == 0 ? beta * wq * wq * wq : 3.0 * beta * uq * uq * wq;
+          for (int i = 0; i < P3; ++i) ye[i] += W * dJ * coef * phi[i];
+        }
+    scatter_add(&o, c, ye, y);
+  }
+  free(we);
+  return 0;
+}

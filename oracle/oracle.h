@@ -81,6 +81,11 @@ int oracle_dkappa(const oracle_problem *pb, const double *x, const double *r,
  * Dirichlet boundary faces (NULL = 0). */
 int oracle_rhs(const oracle_problem *pb, const double *f_vol, const double *g_face, double *F);
 
+/* Semilinear reaction (scalar problem): mode 0: y = A w + beta (w^3, v), the residual
+ * operator r(w); mode 1: y = A w + 3 beta (u0^2 w, v), its Jacobian action at u0. */
+int oracle_semilinear(const oracle_problem *pb, double beta, int mode, const double *u0, const double *w,
+                      double *y);
+
 /* COO assembly of A from per-cell and per-face local matrices. Returns the number of
  * entries written, or -(needed) if cap is too small, or a value < -(1<<60) on error. */
 int64_t oracle_assemble_coo(const oracle_problem *pb, int64_t cap, int64_t *rows,

@@ -504,3 +504,29 @@ def test_block_jacobi_inverts_single_cell_columns():
     # B = blockdiag(A)^-1 is symmetric for theta = -1
     u, v = wl.uniform_vector(orc.ndofs(), 1), wl.uniform_vector(orc.ndofs(), 2)
     assert abs(u @ orc.block_jacobi(v) - v @ orc.block_jacobi(u)) <= 1e-12 * abs(u @ orc.block_jacobi(v))
+
+
+@pytest.mark.parametrize("k,c,beta", [(1, 1.0, 2.0), (2, 0.5, -1.5), (3, 0.0, 4.0)])
+def test_semilinear_constant_state_closed_form(k, c, beta):
+    # u = a everywhere, no Dirichlet faces: the stiffness and every face term vanish, so
+    # the residual r(u) = c a (1, v) + beta a^3 (1, v) sums to (c a + beta a^3) |Omega|,
+    # exactly (the integrand is constant), on a perturbed mesh as well
+    n = (3, 2, 4)
+    orc = oracle.Problem(*n, k, c=c, dirichlet_mask=0, vertices=wl.perturbed_vertices(*n, seed=1))
+    a = 0.7
+    y = orc.semilinear(np.full(orc.ndofs(), a), beta)
+    assert abs(y.sum() - (c * a + beta * a ** 3)) <= 1e-12
+
+
+def test_semilinear_jacobian_is_the_derivative_of_the_residual():
+    # J(u0) w against the central difference of r(u) = A u + beta (u^3, v): for the cubic
+    # reaction the difference is exact up to beta eps^2 (w^3, v)
+    n, k, beta, eps = (3, 3, 2), 2, 3.0, 1e-4
+    orc = oracle.Problem(*n, k, vertices=wl.perturbed_vertices(*n, seed=1))
+    u0, w = wl.uniform_vector(orc.ndofs(), 1), wl.uniform_vector(orc.ndofs(), 2)
+    J = orc.semilinear(w, beta, u0=u0)
+    fd = (orc.semilinear(u0 + eps * w, beta) - orc.semilinear(u0 - eps * w, beta)) / (2 * eps)
+    assert np.abs(J - fd).max() <= 1e-7 * np.abs(J).max()
+    # beta = 0 reduces both to the linear apply
+    assert np.abs(orc.semilinear(w, 0.0) - orc.apply(w)).max() == 0.0
+    assert np.abs(orc.semilinear(w, 0.0, u0=u0) - orc.apply(w)).max() == 0.0
