@@ -49,6 +49,7 @@ enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
 enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2, DG_VARIANT_CELLWISE = 3 };
 enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1, DG_PRECOND_BLOCK_JACOBI = 2 };
+enum { DG_SEMILINEAR_RESIDUAL = 1, DG_SEMILINEAR_JACOBIAN = 2 };
 
 /* Interior-penalty factor gamma_F (Sec. 5.2).
  *   DG_PEN_CONFIG: gamma_F = alpha * k * (k+1) / h_a with h_a = 1/n_a the nominal cell
@@ -231,6 +232,20 @@ dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void
  * gives the full link bandwidth; pageable memory also works. */
 dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host, int nrhs,
                         void *stream);
+
+/* Semilinear reaction: the operator of Eq. (diffreac_weak) plus a cubic reaction
+ * beta (u^3, v) (the paper discusses the Jacobian action of nonlinear problems in Sec. 3
+ * without fixing one; this is the reading chosen here). One vector, FP64 scalar operators
+ * with k+1 points; geometry affine or recomputed in the kernels (trilinear meshes); kappa
+ * honoured.
+ *   DG_SEMILINEAR_RESIDUAL: y = A w + beta (w^3, v), the residual operator at w (u0 unused);
+ *   DG_SEMILINEAR_JACOBIAN: y = A w + 3 beta (u0^2 w, v), its Jacobian action at the
+ *     linearisation point u0 on the direction w: u0 and w are evaluated at the Gauss
+ *     points in the same kernel (Sec. 3's two-input fusion).
+ * w, u0, y: device [ndofs] FP64, 16-byte aligned, y distinct from both. Errors:
+ * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (Stokes, FP32, over-integration), DG_ERR_CUDA. */
+dg_status dg_apply_semilinear(const dg_operator *op, int mode, double beta, const void *u0,
+                              const void *w, void *y, void *stream);
 
 /* Data terms of Eq. (diffreac_weak) moved to the right-hand side (scalar problem):
  *   F(v) = (f, v) + theta (g, n.kappa grad v)_{Gamma_D} + gamma_F (g, v)_{Gamma_D},

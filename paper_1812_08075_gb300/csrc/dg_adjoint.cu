@@ -100,11 +100,14 @@ constexpr size_t cell_adj_smem(int cpb) {
   return align16<double>(sizeof(Tab<P, M, double>)) + size_t(cpb) * (8 * M * M * M + 36) * sizeof(double);
 }
 
+// nlmode (block-uniform): 0 linear; 1 adds beta (r^3, v) (the residual operator of the
+// semilinear reaction); 2 adds 3 beta (x^2 r, v) (its Jacobian action at x, which is then
+// evaluated at the Gauss points together with r: the two-input evaluation of Sec. 3).
 template <int P, int GEO, bool KAPPA, bool DK>
 __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<double> a, const double *__restrict__ r,
                                                   const double *__restrict__ x, double *__restrict__ rvol,
                                                   double *__restrict__ tr_r, double *__restrict__ tr_x,
-                                                  double *__restrict__ dk_vol, int cpb) {
+                                                  double *__restrict__ dk_vol, int cpb, int nlmode, double beta) {
   using T = double;
   constexpr int M = P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<double> a, co
     }
   }
   to_gauss<P, M>(r + c0 * P3, A0, A1, Ur, tb.interp, nc);
-  if (DK) to_gauss<P, M>(x + c0 * P3, A0, A1, Ux, tb.interp, nc);
+  if (DK || nlmode == 2) to_gauss<P, M>(x + c0 * P3, A0, A1, Ux, tb.interp, nc);
   write_traces<P, M>(Ur, tr_r + c0 * 12 * M2, tb, nc);
   if (DK) write_traces<P, M>(Ux, tr_x + c0 * 12 * M2, tb, nc);
   for (int i = tid; i < nc * M3; i += nt) {
@@ -143,10 +146,11 @@ __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<double> a, co
       g2 = fma(tb.dcol[q2 * M + k], u[q0 + q1 * M + k * M2], g2);
     }
     const T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
-    T G[6], mw;
+    T G[6], mw, wdet;
     if (GEO == GEO_AFFINE) {
       G[0] = W * a.vol_g[0]; G[1] = 0; G[2] = 0; G[3] = W * a.vol_g[1]; G[4] = 0; G[5] = W * a.vol_g[2];
       mw = W * a.vol_m;
+      wdet = W / T((double)a.nx * a.ny * a.nz);
     } else {
       T J[3][3], A[3][3];
       dgg::jacobian_from_coeffs(CC + c * 36, tb.s[q0], tb.s[q1], tb.s[q2], J);
@@ -158,6 +162,11 @@ __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<double> a, co
 #pragma unroll
         for (int cc = rr; cc < 3; ++cc) G[e++] = sW * fma(A[rr][0], A[cc][0], fma(A[rr][1], A[cc][1], A[rr][2] * A[cc][2]));
       mw = a.c * W * det;
+      wdet = W * det;
+    }
+    if (nlmode) {  // the reaction's linearised weight at this point
+      const T uq = nlmode == 2 ? Ux[i] : Ur[i];
+      mw = fma((nlmode == 2 ? T(3) * beta : beta) * wdet, uq * uq, mw);
     }
     const T Gr0 = fma(G[0], g0, fma(G[1], g1, G[2] * g2));
     const T Gr1 = fma(G[1], g0, fma(G[3], g1, G[4] * g2));
@@ -412,7 +421,7 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 template <int P, int GEO, bool KAPPA, bool DK>
 cudaError_t run(const ScalarArgs<double> &a, double theta, const double *r, const double *x, double *y,
                 double *dk_vol, double *dk_face, double *rvol, double *tr_r, double *tr_x, double *fres, int cpb,
-                int fpb, cudaStream_t s, const cudaEvent_t *ev) {
+                int fpb, cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta) {
   constexpr int M = P, M2 = M * M, M3 = M * M * M;
   cudaError_t e;
   {
@@ -420,7 +429,8 @@ cudaError_t run(const ScalarArgs<double> &a, double theta, const double *r, cons
     auto k = k_cell_adj<P, GEO, KAPPA, DK>;
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], s);
-    k<<<(unsigned)((a.ncell + cpb - 1) / cpb), threads_for(cpb * M3), sm, s>>>(a, r, x, rvol, tr_r, tr_x, dk_vol, cpb);
+    k<<<(unsigned)((a.ncell + cpb - 1) / cpb), threads_for(cpb * M3), sm, s>>>(a, r, x, rvol, tr_r, tr_x, dk_vol, cpb,
+                                                                              nlmode, beta);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -446,8 +456,9 @@ cudaError_t run(const ScalarArgs<double> &a, double theta, const double *r, cons
 template <int P>
 cudaError_t run_p(int geo, bool kappa, bool dk, const ScalarArgs<double> &a, double theta, const double *r,
                   const double *x, double *y, double *dkv, double *dkf, double *rvol, double *trr, double *trx,
-                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev) {
-#define DGA_RUN(G, K, D) return run<P, G, K, D>(a, theta, r, x, y, dkv, dkf, rvol, trr, trx, fres, cpb, fpb, s, ev)
+                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta) {
+#define DGA_RUN(G, K, D) \
+  return run<P, G, K, D>(a, theta, r, x, y, dkv, dkf, rvol, trr, trx, fres, cpb, fpb, s, ev, nlmode, beta)
   if (geo == GEO_AFFINE) {
     if (kappa) { if (dk) DGA_RUN(GEO_AFFINE, true, true); DGA_RUN(GEO_AFFINE, true, false); }
     if (dk) DGA_RUN(GEO_AFFINE, false, true);
@@ -464,14 +475,15 @@ cudaError_t run_p(int geo, bool kappa, bool dk, const ScalarArgs<double> &a, dou
 cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<double> &a, double theta,
                                   const double *r, const double *x, double *y, double *dk_vol, double *dk_face,
                                   double *rvol, double *tr_r, double *tr_x, double *fres, int cpb, int fpb,
-                                  cudaStream_t s, const cudaEvent_t *ev) {
+                                  cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta) {
   const bool dk = x != nullptr && dk_vol != nullptr && dk_face != nullptr;
+  if ((nlmode == 2 && !x) || (nlmode && dk)) return cudaErrorInvalidValue;
   switch (p) {
-    case 2: return dga::run_p<2>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev);
-    case 3: return dga::run_p<3>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev);
-    case 4: return dga::run_p<4>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev);
-    case 5: return dga::run_p<5>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev);
-    case 6: return dga::run_p<6>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev);
+    case 2: return dga::run_p<2>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev, nlmode, beta);
+    case 3: return dga::run_p<3>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev, nlmode, beta);
+    case 4: return dga::run_p<4>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev, nlmode, beta);
+    case 5: return dga::run_p<5>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev, nlmode, beta);
+    case 6: return dga::run_p<6>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, ev, nlmode, beta);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -485,6 +485,25 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   return DG_OK;
 }
 
+dg_status dg_apply_semilinear(const dg_operator *op_c, int mode, double beta, const void *u0, const void *w, void *y,
+                              void *stream) {
+  dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (!op || !w || !y || w == y || (u0 && u0 == y)) return fail(DG_ERR_INVALID_ARG);
+  if (mode != DG_SEMILINEAR_RESIDUAL && mode != DG_SEMILINEAR_JACOBIAN) return fail(DG_ERR_INVALID_ARG);
+  if (mode == DG_SEMILINEAR_JACOBIAN && !u0) return fail(DG_ERR_INVALID_ARG);
+  if (!aligned16(w) || !aligned16(y) || (u0 && !aligned16(u0)) || !(beta == beta)) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem != DG_SCALAR || op->precision != DG_FP64 || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
+  const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
+  const cudaEvent_t *ev = next_events(op);
+  cudaError_t e = launch_scalar_adjoint(
+      op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, false), op->theta, (const double *)w,
+      mode == DG_SEMILINEAR_JACOBIAN ? (const double *)u0 : nullptr, (double *)y, nullptr, nullptr,
+      (double *)op->d_rvol, (double *)op->d_tr, nullptr, (double *)op->d_fres, op->cpb, op->fpb, (cudaStream_t)stream,
+      ev, mode == DG_SEMILINEAR_JACOBIAN ? 2 : 1, beta);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  return DG_OK;
+}
+
 dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face, void *F, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !F || F == f_vol || F == g_face || !aligned16(F)) return fail(DG_ERR_INVALID_ARG);

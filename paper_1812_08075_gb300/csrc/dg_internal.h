@@ -97,10 +97,13 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
 // the transpose, and, when x is non-NULL, dkappa at every volume and face point for the
 // forward form's theta (passed separately). Geometry is affine or recomputed from
 // a.verts (geo = GEO_AFFINE or GEO_RECOMPUTE).
+// nlmode 1 / 2 (with forward coefficients): the semilinear reaction's residual term
+// beta (r^3, v) / Jacobian term 3 beta (x^2 r, v) added to the volume integral.
 cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<double> &a, double theta,
                                   const double *r, const double *x, double *y, double *dk_vol,
                                   double *dk_face, double *rvol, double *tr_r, double *tr_x,
-                                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
+                                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
+                                  int nlmode = 0, double beta = 0.0);
 
 // Persistent single-pass apply for affine meshes (dg_fused.cu): one launch of one wave of
 // blocks that loop over (right-hand side, row of cells) work items; each cell gathers its

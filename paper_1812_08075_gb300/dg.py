@@ -24,6 +24,7 @@ DG_FP64, DG_FP32 = 0, 1
 DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
 DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED, DG_VARIANT_CELLWISE = 0, 1, 2, 3
 DG_PRECOND_NONE, DG_PRECOND_JACOBI, DG_PRECOND_BLOCK_JACOBI = 0, 1, 2
+DG_SEMILINEAR_RESIDUAL, DG_SEMILINEAR_JACOBIAN = 1, 2
 
 EXPORTED = [
     "dg_status_string", "dg_get_last_error", "dg_mesh_create", "dg_mesh_destroy", "dg_operator_create",
@@ -31,7 +32,7 @@ EXPORTED = [
     "dg_apply_host", "dg_apply_adjoint", "dg_reference_tables", "dg_operator_profile", "dg_operator_kernel_times",
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
-    "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior",
+    "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
 ]
 
 
@@ -106,6 +107,7 @@ def lib():
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_diagonal.argtypes = [vp, vp, vp]
         L.dg_operator_block_jacobi.argtypes = [vp, vp, vp, i32, vp]
+        L.dg_apply_semilinear.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp, vp]
         L.dg_operator_predict.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_time.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_autotune_prior.argtypes = [vp, i32, i32, vp, ctypes.POINTER(dg_tune_result)]
@@ -379,6 +381,19 @@ class Operator:
         dg_rhs(self.handle, None if f_vol is None else _dev_ptr(f_vol, self.dtype, "f_vol"),
                None if g_face is None else _dev_ptr(g_face, self.dtype, "g_face"), F.data_ptr(), _stream_ptr(stream))
         return F
+
+    def semilinear(self, w, beta, u0=None, stream=None):
+        """u0 None: A w + beta (w^3, v); else A w + 3 beta (u0^2 w, v) (FP64 CUDA tensors)."""
+        import torch
+        if w.numel() != self.ndofs:
+            raise ValueError("w has the wrong size")
+        y = torch.empty_like(w)
+        mode = DG_SEMILINEAR_RESIDUAL if u0 is None else DG_SEMILINEAR_JACOBIAN
+        _check(lib().dg_apply_semilinear(self.handle, mode, float(beta),
+                                         None if u0 is None else _dev_ptr(u0, self.dtype, "u0"),
+                                         _dev_ptr(w, self.dtype, "w"), _dev_ptr(y, self.dtype, "y"),
+                                         _stream_ptr(stream)), "dg_apply_semilinear")
+        return y
 
     def block_jacobi(self, r, z=None, stream=None):
         """z = A_cc^-1 r per cell (cell-block Jacobi) for r of shape [ndofs] or [nrhs, ndofs]."""
