@@ -109,11 +109,15 @@ static void lagrange_1d(int n, const double *z, double t, double *val, double *d
 typedef struct {
   const oracle_problem *pb;
   int n[3];
-  int p, m, pp;            /* basis points, quad points, pressure basis points */
+  int p, m, pp;            /* basis points, quad points, pressure basis points (isotropic) */
   int P3, PP3, L;          /* local sizes */
   int64_t ncell;
   double s[OMAXM], w[OMAXM];
   double zv[OMAXP], zp[OMAXP];
+  /* per direction (equal to the above unless the degrees are anisotropic) */
+  int aniso;
+  int ka[3], pa[3], ma[3];
+  double sa[3][OMAXM], wa[3][OMAXM], za[3][OMAXP];
 } octx;
 
 static int ctx_init(octx *o, const oracle_problem *pb) {
@@ -130,6 +134,26 @@ static int ctx_init(octx *o, const oracle_problem *pb) {
   o->ncell = (int64_t)pb->nx * pb->ny * pb->nz;
   if (oracle_gauss_rule(o->m, o->s, o->w)) return 1;
   if (oracle_gll_nodes(pb->k, o->zv)) return 1;
+  o->aniso = pb->kaxis[0] != 0 || pb->kaxis[1] != 0 || pb->kaxis[2] != 0;
+  for (int d = 0; d < 3; ++d) {
+    if (o->aniso) {
+      const int kd = pb->kaxis[d];
+      if (kd < 1 || kd + 1 > OMAXP || kd + 1 > OMAXM || pb->problem != 0 || pb->kappa_vol || pb->kappa_face) return 1;
+      o->ka[d] = kd;
+      o->pa[d] = kd + 1;
+      o->ma[d] = kd + 1;
+      if (oracle_gauss_rule(o->ma[d], o->sa[d], o->wa[d])) return 1;
+      if (oracle_gll_nodes(kd, o->za[d])) return 1;
+    } else {
+      o->ka[d] = pb->k;
+      o->pa[d] = o->p;
+      o->ma[d] = o->m;
+      memcpy(o->sa[d], o->s, sizeof(o->s));
+      memcpy(o->wa[d], o->w, sizeof(o->w));
+      memcpy(o->za[d], o->zv, sizeof(o->zv));
+    }
+  }
+  if (o->aniso) o->P3 = o->pa[0] * o->pa[1] * o->pa[2];
   if (pb->problem == 1) {
     o->pp = pb->k; /* pressure degree k-1 */
     if (oracle_gll_nodes(pb->k - 1, o->zp)) return 1;
@@ -226,16 +250,34 @@ static void basis3d(int n, const double *z, const double xi[3], double Ji[3][3],
       }
 }
 
+/* basis3d with its own node set per direction: pa[d] nodes za[d] (anisotropic degrees). */
+static void basis3d_axes(const int pa[3], const double za[3][OMAXP], const double xi[3], double Ji[3][3],
+                         double *phi, double (*g)[3]) {
+  double v[3][OMAXP], dv[3][OMAXP];
+  for (int d = 0; d < 3; ++d) lagrange_1d(pa[d], za[d], xi[d], v[d], dv[d]);
+  int j = 0;
+  for (int j2 = 0; j2 < pa[2]; ++j2)
+    for (int j1 = 0; j1 < pa[1]; ++j1)
+      for (int j0 = 0; j0 < pa[0]; ++j0, ++j) {
+        phi[j] = v[0][j0] * v[1][j1] * v[2][j2];
+        if (g) {
+          double gr[3] = {dv[0][j0] * v[1][j1] * v[2][j2], v[0][j0] * dv[1][j1] * v[2][j2],
+                          v[0][j0] * v[1][j1] * dv[2][j2]};
+          for (int i = 0; i < 3; ++i) g[j][i] = Ji[0][i] * gr[0] + Ji[1][i] * gr[1] + Ji[2][i] * gr[2];
+        }
+      }
+}
+
 /* Measures |T| and |F| by the same Gauss rule (penalty mode 1). */
 static double cell_measure(const octx *o, int64_t c) {
   double V[8][3], J[3][3], xi[3], vol = 0.0;
   cell_vertices(o, c, V);
-  for (int q2 = 0; q2 < o->m; ++q2)
-    for (int q1 = 0; q1 < o->m; ++q1)
-      for (int q0 = 0; q0 < o->m; ++q0) {
-        xi[0] = o->s[q0]; xi[1] = o->s[q1]; xi[2] = o->s[q2];
+  for (int q2 = 0; q2 < o->ma[2]; ++q2)
+    for (int q1 = 0; q1 < o->ma[1]; ++q1)
+      for (int q0 = 0; q0 < o->ma[0]; ++q0) {
+        xi[0] = o->sa[0][q0]; xi[1] = o->sa[1][q1]; xi[2] = o->sa[2][q2];
         map_jacobian(V, xi, J);
-        vol += o->w[q0] * o->w[q1] * o->w[q2] * det3(J);
+        vol += o->wa[0][q0] * o->wa[1][q1] * o->wa[2][q2] * det3(J);
       }
   return vol;
 }
@@ -264,19 +306,19 @@ static double face_measure(const octx *o, int64_t c, int a, int side) {
   int t1, t2;
   tangential_axes(a, &t1, &t2);
   cell_vertices(o, c, V);
-  for (int qt = 0; qt < o->m; ++qt)
-    for (int qs = 0; qs < o->m; ++qs) {
-      xi[a] = side ? 1.0 : 0.0; xi[t1] = o->s[qs]; xi[t2] = o->s[qt];
+  for (int qt = 0; qt < o->ma[t2]; ++qt)
+    for (int qs = 0; qs < o->ma[t1]; ++qs) {
+      xi[a] = side ? 1.0 : 0.0; xi[t1] = o->sa[t1][qs]; xi[t2] = o->sa[t2][qt];
       map_jacobian(V, xi, J);
       face_area_vector(J, a, side, nv);
-      area += o->w[qs] * o->w[qt] * sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      area += o->wa[t1][qs] * o->wa[t2][qt] * sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
     }
   return area;
 }
 
 /* gamma_F, Sec. 5.2 (mode 1) or alpha*k(k+1)/h_a with h_a = 1/n_a (mode 0). */
 static double penalty(const octx *o, int a, int64_t cm, int sidem, int64_t cp) {
-  int k = o->pb->k;
+  int k = o->ka[a];  /* the degree along the face normal (k in every direction if isotropic) */
   if (o->pb->pen_mode == 0) return o->pb->pen_alpha * k * (k + 1) * (double)o->n[a];
   double F = face_measure(o, cm, a, sidem);
   double T = cell_measure(o, cm);
@@ -297,15 +339,15 @@ static void vol_scalar(const octx *o, int64_t c, const double *xe, double *ye) {
   static __thread double phi[OMAXP3], g[OMAXP3][3];
   const int P3 = o->P3, m = o->m;
   cell_vertices(o, c, V);
-  for (int q2 = 0; q2 < m; ++q2)
-    for (int q1 = 0; q1 < m; ++q1)
-      for (int q0 = 0; q0 < m; ++q0) {
-        xi[0] = o->s[q0]; xi[1] = o->s[q1]; xi[2] = o->s[q2];
-        double W = o->w[q0] * o->w[q1] * o->w[q2];
+  for (int q2 = 0; q2 < o->ma[2]; ++q2)
+    for (int q1 = 0; q1 < o->ma[1]; ++q1)
+      for (int q0 = 0; q0 < o->ma[0]; ++q0) {
+        xi[0] = o->sa[0][q0]; xi[1] = o->sa[1][q1]; xi[2] = o->sa[2][q2];
+        double W = o->wa[0][q0] * o->wa[1][q1] * o->wa[2][q2];
         map_jacobian(V, xi, J);
         double dJ = det3(J);
         inv3(J, dJ, Ji);
-        basis3d(o->p, o->zv, xi, Ji, phi, g);
+        basis3d_axes(o->pa, o->za, xi, Ji, phi, g);
         double u = 0, gu[3] = {0, 0, 0};
         for (int j = 0; j < P3; ++j) {
           u += xe[j] * phi[j];
@@ -335,7 +377,7 @@ static void side_eval(const octx *o, int64_t c, int a, int side, int qs, int qt,
   int t1, t2;
   tangential_axes(a, &t1, &t2);
   cell_vertices(o, c, V);
-  xi[a] = side ? 1.0 : 0.0; xi[t1] = o->s[qs]; xi[t2] = o->s[qt];
+  xi[a] = side ? 1.0 : 0.0; xi[t1] = o->sa[t1][qs]; xi[t2] = o->sa[t2][qt];
   map_jacobian(V, xi, J);
   double dJ = det3(J);
   inv3(J, dJ, Ji);
@@ -347,7 +389,7 @@ static void side_eval(const octx *o, int64_t c, int a, int side, int qs, int qt,
     *ds_out = ds;
     nrm_in = nrm_out;
   }
-  basis3d(o->p, o->zv, xi, Ji, sd->phi, sd->g);
+  basis3d_axes(o->pa, o->za, xi, Ji, sd->phi, sd->g);
   for (int j = 0; j < o->P3; ++j)
     sd->dn[j] = sd->g[j][0] * nrm_in[0] + sd->g[j][1] * nrm_in[1] + sd->g[j][2] * nrm_in[2];
   if (o->pb->problem == 1) basis3d(o->pp, o->zp, xi, NULL, sd->ppsi, NULL);
@@ -366,13 +408,15 @@ static void face_scalar(const octx *o, int a, int64_t cm, int sidem, int64_t cp,
                         const double *xm, const double *xp, double *ym, double *yp,
                         double sc, double ss) {
   static __thread side_data dm, dp;
-  const int P3 = o->P3, m = o->m;
+  const int P3 = o->P3;
+  int t1, t2;
+  tangential_axes(a, &t1, &t2);
   double gam = penalty(o, a, cm, sidem, cp);
-  for (int qt = 0; qt < m; ++qt)
-    for (int qs = 0; qs < m; ++qs) {
+  for (int qt = 0; qt < o->ma[t2]; ++qt)
+    for (int qs = 0; qs < o->ma[t1]; ++qs) {
       double n[3], ds;
       side_eval(o, cm, a, sidem, qs, qt, NULL, n, &ds, &dm);
-      double W = o->w[qs] * o->w[qt] * ds;
+      double W = o->wa[t1][qs] * o->wa[t2][qt] * ds;
       double um = 0, gnm = 0;
       for (int j = 0; j < P3; ++j) { um += xm[j] * dm.phi[j]; gnm += xm[j] * dm.dn[j]; }
       double km = kappa_face_at(o, cm, 2 * a + sidem, qs, qt);
@@ -643,7 +687,7 @@ int oracle_apply_cells(const oracle_problem *pb, int transpose, const double *x,
 int oracle_dkappa(const oracle_problem *pb, const double *x, const double *r,
                   double *dk_vol, double *dk_face) {
   octx o;
-  if (ctx_init(&o, pb) || pb->problem != 0) return 1;
+  if (ctx_init(&o, pb) || pb->problem != 0 || o.aniso) return 1;
   const int P3 = o.P3, m = o.m, m2 = m * m, m3 = m * m * m;
   static __thread side_data dm, dp;
   double *phi = malloc(sizeof(double) * P3 * 4);
@@ -792,7 +836,7 @@ int64_t oracle_assemble_coo(const oracle_problem *pb, int64_t cap, int64_t *rows
 
 int oracle_rhs(const oracle_problem *pb, const double *f_vol, const double *g_face, double *F) {
   octx o;
-  if (ctx_init(&o, pb) || pb->problem != 0) return 1;
+  if (ctx_init(&o, pb) || pb->problem != 0 || o.aniso) return 1;
   const int P3 = o.P3, m = o.m, m2 = m * m, m3 = m * m * m;
   static __thread side_data dm;
   double *phi = malloc(sizeof(double) * P3 * 4);
@@ -857,7 +901,7 @@ int oracle_semilinear(const oracle_problem *pb, double beta, int mode, const dou
   int st = oracle_apply(pb, 0, w, y);
   if (st) return st;
   octx o;
-  if (ctx_init(&o, pb)) return 1;
+  if (ctx_init(&o, pb) || o.aniso) return 1;
   const int P3 = o.P3, m = o.m, L = o.L;
   double *we = malloc(sizeof(double) * 3 * L);
   if (!we) return 2;

@@ -21,6 +21,10 @@
  *     Gauss rule;
  *   - per-quadrature-point scalar kappa: volume [ncell][m^3], face [ncell][6][m^2]
  *     (each cell's own trace side, local faces -x,+x,-y,+y,-z,+z);
+ *   - anisotropic degrees (Sec. 2.1's vector k, scalar problem): k_a per direction with
+ *     k_a + 1 Gauss points; penalty mode 0 uses the degree along the face normal,
+ *     gamma_F = alpha k_a (k_a + 1) n_a (the trace inverse inequality of a tensor-product
+ *     polynomial scales with it), mode 1 likewise with k_a (k_a + d - 1);
  *   - Stokes: velocity Q_k x3 then pressure Q_{k-1}, vector [u: ncell x 3 x p^3 | p:
  *     ncell x k^3]; viscous block = scalar SIPG with kappa = mu, c = 0 on each component,
  *     face terms on interior and Dirichlet faces only.
@@ -51,6 +55,10 @@ typedef struct {
   const double *vertices; /* [(nx+1)(ny+1)(nz+1)][3] or NULL for the unit cube */
   const double *kappa_vol;  /* [ncell][m^3] or NULL (kappa = 1) */
   const double *kappa_face; /* [ncell][6][m^2] or NULL (kappa = 1) */
+  int32_t kaxis[3];       /* anisotropic degrees (k_0, k_1, k_2), all >= 1, or all 0 for k in
+                             every direction; anisotropic: scalar problem, k_a + 1 Gauss points
+                             per direction, kappa = 1, cell DOFs j0 + p0 (j1 + p1 j2) */
+  int32_t reserved;
 } oracle_problem;
 
 /* 1D rules on [0,1]. Return 0 on success. */

@@ -152,15 +152,17 @@ def div_1d(bq: Basis1D, bu: Basis1D, n: int, bc_lo: bool, bc_hi: bool):
 
 
 def _perm(nx, ny, nz, p):
-    """Kronecker index (ix fastest over nx*p, then iy, then iz) -> cell-major index."""
-    ix = np.arange(nx * p)
-    iy = np.arange(ny * p)
-    iz = np.arange(nz * p)
+    """Kronecker index (ix fastest over nx*p0, then iy, then iz) -> cell-major index; p is
+    the number of basis points per direction, or a triple (p0, p1, p2)."""
+    p0, p1, p2 = (p, p, p) if np.isscalar(p) else p
+    ix = np.arange(nx * p0)
+    iy = np.arange(ny * p1)
+    iz = np.arange(nz * p2)
     IZ, IY, IX = np.meshgrid(iz, iy, ix, indexing="ij")
-    cx, j0 = IX // p, IX % p
-    cy, j1 = IY // p, IY % p
-    cz, j2 = IZ // p, IZ % p
-    g = (cx + nx * (cy + ny * cz)) * p ** 3 + j0 + p * (j1 + p * j2)
+    cx, j0 = IX // p0, IX % p0
+    cy, j1 = IY // p1, IY % p1
+    cz, j2 = IZ // p2, IZ % p2
+    g = (cx + nx * (cy + ny * cz)) * (p0 * p1 * p2) + j0 + p0 * (j1 + p1 * j2)
     return g.ravel()
 
 
@@ -173,17 +175,21 @@ def gamma_axis(k, n_a, alpha, pen_mode):
     return alpha * k * (k + 1) * n_a if pen_mode == 0 else alpha * k * (k + 2) * n_a
 
 
-def scalar_matrix(nx, ny, nz, k, c=1.0, theta=-1.0, alpha=2.0, pen_mode=0, mask=0b111111, kappa=1.0):
-    """Affine unit-cube SIPG matrix (constant kappa) in the cell-major DOF order."""
-    b = Basis1D(gll_points(k))
+def scalar_matrix(nx, ny, nz, k, c=1.0, theta=-1.0, alpha=2.0, pen_mode=0, mask=0b111111, kappa=1.0,
+                  degrees=None):
+    """Affine unit-cube SIPG matrix (constant kappa) in the cell-major DOF order; degrees
+    (k_0, k_1, k_2) gives each direction its own basis and the face penalty the degree along
+    the face normal."""
+    ks = tuple(degrees) if degrees is not None else (k, k, k)
+    bs = [Basis1D(gll_points(ka)) for ka in ks]
     n = (nx, ny, nz)
-    M = [mass_1d(b, b, n[a], 1.0 / n[a]) for a in range(3)]
-    S = [sipg_1d(b, n[a], 1.0 / n[a], gamma_axis(k, n[a], alpha, pen_mode) / kappa, theta,
+    M = [mass_1d(bs[a], bs[a], n[a], 1.0 / n[a]) for a in range(3)]
+    S = [sipg_1d(bs[a], n[a], 1.0 / n[a], gamma_axis(ks[a], n[a], alpha, pen_mode) / kappa, theta,
                  bool(mask >> (2 * a) & 1), bool(mask >> (2 * a + 1) & 1)) for a in range(3)]
     K = (kappa * (sp.kron(M[2], sp.kron(M[1], S[0])) + sp.kron(M[2], sp.kron(S[1], M[0]))
                   + sp.kron(S[2], sp.kron(M[1], M[0])))
          + c * sp.kron(M[2], sp.kron(M[1], M[0])))
-    perm = _perm(nx, ny, nz, k + 1)
+    perm = _perm(nx, ny, nz, tuple(ka + 1 for ka in ks))
     N = K.shape[0]
     return _reorder(K, perm, perm, N, N)
 
