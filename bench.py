@@ -250,12 +250,14 @@ def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
         f = sum(st.flops) * nrhs
         peak = pk["fp32_tflops"] if prec == dg.DG_FP32 else pk["fp64_tflops"]
         byt = st.dofs_bytes * nrhs
+        t_roof = max(f / (peak * 1e12), sum(st.bytes) * nrhs / (pk["hbm_gbs"] * 1e9))
         res[tag] = {"dof_s": nrhs * op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "variant":
                     VARIANT_NAMES[st.variant],
                     "persistent_grid": st.persistent_grid, "tflops": f / (ms * 1e-3) / 1e12,
                     "frac_alu_peak": f / (ms * 1e-3) / 1e12 / peak,
                     "hbm_gbs_algorithmic": byt / (ms * 1e-3) / 1e9,
-                    "frac_hbm": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "kernel_ms": kt}
+                    "frac_hbm": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    "roofline_frac": t_roof / (ms * 1e-3), "kernel_ms": kt}
         del op, xx, yy
     return res
 
@@ -304,6 +306,52 @@ def adjoint_apply(n_cells=64, k=3):
     return {"workload": f"{n_cells}^3 trilinear cells, Q{k}, log-normal kappa at every point, FP64",
             "ndofs": op.ndofs, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
             "adjoint_dof_s": op.ndofs / (ms_adj * 1e-3), "geometry": "recomputed in the adjoint kernels"}
+
+
+def event_ms(fn, reps=20, warm=3):
+    """Mean CUDA-event milliseconds of fn() on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def next_rows_apply(n_cells=64, k=3):
+    """The widened rows on config 5's mesh (64^3 trilinear, Q3, FP64): the residual's data
+    terms (dg_rhs), the semilinear reaction's residual operator and Jacobian action
+    (dg_apply_semilinear), and the cell-block Jacobi preconditioner on the affine mesh."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    n = (n_cells,) * 3
+    op = dg.Operator(dg.Mesh(*n, wl.perturbed_vertices(*n, seed=1)), k)
+    m = k + 1
+    u0 = torch.from_numpy(wl.uniform_vector(op.ndofs, 3)).cuda()
+    w = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    f = torch.from_numpy(wl.uniform_vector(op.mesh.ncell * m ** 3, 5)).cuda()
+    g = torch.from_numpy(wl.uniform_vector(op.mesh.ncell * 6 * m ** 2, 6)).cuda()
+    y = torch.empty_like(w)
+    ms_fwd = event_ms(lambda: op.apply(w, y))
+    ms_rhs = event_ms(lambda: op.rhs(f, g))
+    ms_res = event_ms(lambda: op.semilinear(w, 2.0))
+    ms_jac = event_ms(lambda: op.semilinear(w, 2.0, u0=u0))
+    aff = dg.Operator(dg.Mesh(*n), k)
+    ms_bj = event_ms(lambda: aff.block_jacobi(w, y))
+    aff32 = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32)
+    w32, y32 = w.float(), torch.empty_like(w.float())
+    ms_bj32 = event_ms(lambda: aff32.block_jacobi(w32, y32))
+    return {"workload": f"{n_cells}^3 trilinear cells (block Jacobi: affine), Q{k}, FP64 unless stated",
+            "ndofs": op.ndofs, "forward_apply_ms": ms_fwd, "rhs_ms": ms_rhs,
+            "semilinear_residual_ms": ms_res, "semilinear_jacobian_ms": ms_jac,
+            "block_jacobi_fp64_ms": ms_bj, "block_jacobi_fp32_ms": ms_bj32,
+            "note": "semilinear and rhs recompute the geometry in the kernels; the forward apply reads stored geometry"}
 
 
 def run_solve(args):
@@ -430,11 +478,16 @@ def run_ours(args, rank, world, dist):
                 xx = torch.from_numpy(wl.uniform_vector(o.ndofs, 0)).to("cuda", o.dtype)
                 yy = torch.empty_like(xx)
                 ms_k, kt_k, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
-                f = sum(o.stats().flops)
+                st_k = o.stats()
+                f, byt = sum(st_k.flops), sum(st_k.bytes)
                 peak = pk["fp64_tflops"] if prec == dg.DG_FP64 else pk["fp32_tflops"]
+                t_roof = max(f / (peak * 1e12), byt / (pk["hbm_gbs"] * 1e9))
                 sweep[f"Q{kk}_{tag}"] = {"dof_s": o.ndofs / (ms_k * 1e-3), "ms": ms_k,
                                          "tflops": f / (ms_k * 1e-3) / 1e12,
                                          "frac_alu_peak": f / (ms_k * 1e-3) / 1e12 / peak,
+                                         "hbm_gbs_model": byt / (ms_k * 1e-3) / 1e9,
+                                         "roofline_frac": t_roof / (ms_k * 1e-3),
+                                         "bound": "alu" if f / (peak * 1e12) >= byt / (pk["hbm_gbs"] * 1e9) else "hbm",
                                          "kernel_ms": kt_k}
                 del o, xx, yy
         out["sweep"] = sweep
@@ -504,7 +557,8 @@ def main():
             from paper_1812_08075_gb300 import build as libbuild
             libbuild.build()
             print(json.dumps({"mode": "extras", "stokes": stokes_apply(peaks(), n_cells=args.stokes_cells),
-                              "adjoint": adjoint_apply(n_cells=args.adjoint_cells)}), flush=True)
+                              "adjoint": adjoint_apply(n_cells=args.adjoint_cells),
+                              "next_rows": next_rows_apply(n_cells=args.adjoint_cells)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -134,6 +134,19 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
                              dg_operator **out);
 dg_status dg_operator_destroy(dg_operator *op);
 
+/* Scalar operator with anisotropic degrees (Sec. 2.1's vector k): degrees[a] = k_a in 1..5
+ * per direction, k_a + 1 GLL basis points and k_a + 1 Gauss points per direction, cell DOFs
+ * j0 + p0 (j1 + p1 j2), the face penalty taking the degree along the face normal
+ * (DG_PEN_CONFIG: alpha k_a (k_a + 1) / h_a; DG_PEN_PAPER: alpha k_a (k_a + 2) / h_a on the
+ * uniform lattice). Affine meshes (vertices NULL) and the scalar problem only; the apply runs
+ * the three-kernel structure with run-time extents. dg_apply, dg_apply_host, dg_operator_stats
+ * and unpreconditioned dg_cg_solve / dg_refine_solve accept it; kappa, the adjoint, dg_rhs,
+ * dg_apply_semilinear, the preconditioners, variants and the tuners return
+ * DG_ERR_UNSUPPORTED. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3],
+                                   const dg_penalty *penalty, const dg_coefficients *coef,
+                                   dg_operator **out);
+
 /* Number of DOFs of one vector of this operator. */
 dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n);
 

@@ -78,6 +78,7 @@ dg_status dg_mesh_destroy(dg_mesh *mesh) {
 }  // extern "C"
 
 static void free_op(dg_operator *o) {
+  if (o && o->d_antab) cudaFree(o->d_antab);
   if (!o) return;
   void *ptrs[] = {o->d_tab, o->d_verts, o->d_gamma, o->d_cellvol, o->d_gvol, o->d_gface,
                   o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh, o->d_tr2};
@@ -284,6 +285,52 @@ dg_status dg_operator_destroy(dg_operator *op) {
   return DG_OK;
 }
 
+dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3], const dg_penalty *pen,
+                                   const dg_coefficients *co, dg_operator **out) {
+  if (!mesh || !degrees || !pen || !co || !out) return fail(DG_ERR_INVALID_ARG);
+  int kmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (degrees[a] < 1 || degrees[a] + 1 > DG_MAXP) return fail(DG_ERR_INVALID_ARG);
+    kmax = degrees[a] > kmax ? degrees[a] : kmax;
+  }
+  if (!mesh->affine || co->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  // an isotropic operator of the largest degree supplies the mesh bookkeeping and scratch
+  // large enough for every per-direction size (p0 p1 p2 <= (k_max+1)^3, likewise the traces)
+  dg_status st = dg_operator_create(mesh, kmax, 0, pen, co, out);
+  if (st != DG_OK) return st;
+  dg_operator *o = *out;
+  HostTables ht[3];
+  const int n[3] = {o->nx, o->ny, o->nz};
+  int npts = 1;
+  for (int a = 0; a < 3; ++a) {
+    const int k = degrees[a];
+    if (dg_build_tables(k, k + 1, false, &ht[a])) { free_op(o); *out = nullptr; return fail(DG_ERR_UNSUPPORTED); }
+    o->kax[a] = k;
+    // the penalty of a face takes the degree along its normal
+    o->gamma_axis[a] = pen->mode == DG_PEN_CONFIG ? pen->alpha * k * (k + 1) * n[a] : pen->alpha * k * (k + 2) * n[a];
+    npts *= k + 1;
+  }
+  const bool f64 = o->precision == DG_FP64;
+  std::vector<unsigned char> host(f64 ? aniso_tab_bytes<double>() : aniso_tab_bytes<float>());
+  int ts = 0;
+  if ((f64 ? aniso_tables<double>(ht, host.data(), &ts) : aniso_tables<float>(ht, host.data(), &ts)) != 0 ||
+      cudaMalloc(&o->d_antab, host.size()) != cudaSuccess ||
+      cudaMemcpy(o->d_antab, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    free_op(o);
+    *out = nullptr;
+    return fail(DG_ERR_OOM);
+  }
+  o->aniso = 1;
+  o->an_npts = npts;
+  o->an_ts = ts;
+  o->ndofs = o->ncell * npts;
+  o->variant = DG_VARIANT_THREE_KERNEL;
+  o->cpb = 256 / npts > 0 ? 256 / npts : 1;
+  o->fpb = 256 / (DG_MAXM * DG_MAXM) > 0 ? 256 / (DG_MAXM * DG_MAXM) : 1;
+  return DG_OK;
+}
+
 dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n) {
   if (!op || !n) return fail(DG_ERR_INVALID_ARG);
   *n = op->ndofs;
@@ -292,6 +339,7 @@ dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n) {
 
 dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const void *kappa_face) {
   if (!op) return fail(DG_ERR_INVALID_ARG);
+  if (op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if ((kappa_vol && !aligned16(kappa_vol)) || (kappa_face && !aligned16(kappa_face))) return fail(DG_ERR_INVALID_ARG);
   if ((kappa_vol == nullptr) != (kappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
@@ -312,7 +360,9 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   out->ncell = op->ncell;
   out->nface = op->nface;
   const int es = op->precision == DG_FP64 ? 8 : 4;
-  if (op->problem == DG_STOKES)
+  if (op->aniso)
+    aniso_work_model(op->kax, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
+  else if (op->problem == DG_STOKES)
     stokes_work_model(op->p, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
   else if (op->variant == DG_VARIANT_FUSED)
     fused_work_model(op->p, op->ncell, op->nbface, out->flops, out->bytes, es);
@@ -373,6 +423,19 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
       e = launch_stokes_apply<float>(op->p, scalar_args<float>(op, transpose), (float)op->mu, (const float *)x,
                                      (float *)y, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres, nrhs,
                                      sdof, srv, str, op->cpb, op->fpb, s, ev);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+    return DG_OK;
+  }
+  if (op->aniso) {
+    const int64_t sv = op->ncell * op->an_npts, st = op->ncell * op->an_ts;
+    if (op->precision == DG_FP64)
+      e = launch_aniso_apply<double>(scalar_args<double>(op, transpose), op->d_antab, op->an_npts, op->an_ts,
+                                     (const double *)x, (double *)y, (double *)op->d_rvol, (double *)op->d_tr,
+                                     (double *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev);
+    else
+      e = launch_aniso_apply<float>(scalar_args<float>(op, transpose), op->d_antab, op->an_npts, op->an_ts,
+                                    (const float *)x, (float *)y, (float *)op->d_rvol, (float *)op->d_tr,
+                                    (float *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;
   }
@@ -462,6 +525,7 @@ dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_hos
 dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x, void *y, void *dkappa_vol,
                            void *dkappa_face, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !r || !y || r == y || (x && x == y)) return fail(DG_ERR_INVALID_ARG);
   if (!aligned16(r) || !aligned16(y) || (x && !aligned16(x))) return fail(DG_ERR_INVALID_ARG);
   if ((dkappa_vol == nullptr) != (dkappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
@@ -488,6 +552,7 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
 dg_status dg_apply_semilinear(const dg_operator *op_c, int mode, double beta, const void *u0, const void *w, void *y,
                               void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !w || !y || w == y || (u0 && u0 == y)) return fail(DG_ERR_INVALID_ARG);
   if (mode != DG_SEMILINEAR_RESIDUAL && mode != DG_SEMILINEAR_JACOBIAN) return fail(DG_ERR_INVALID_ARG);
   if (mode == DG_SEMILINEAR_JACOBIAN && !u0) return fail(DG_ERR_INVALID_ARG);
@@ -506,6 +571,7 @@ dg_status dg_apply_semilinear(const dg_operator *op_c, int mode, double beta, co
 
 dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face, void *F, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !F || F == f_vol || F == g_face || !aligned16(F)) return fail(DG_ERR_INVALID_ARG);
   if ((f_vol && !aligned16(f_vol)) || (g_face && !aligned16(g_face))) return fail(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
@@ -524,6 +590,7 @@ dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face,
 }
 
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block) {
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_CELLWISE || cells_per_block < 0 || faces_per_block < 0)
     return fail(DG_ERR_INVALID_ARG);
   const int v = resolve_variant(op, variant);
@@ -579,6 +646,7 @@ static dg_status time_kernels(dg_operator *op, const void *x, void *y, int nrhs,
 }
 
 dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_result *out) {
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !out || nrhs < 1 || nrhs > op->max_rhs) return fail(DG_ERR_INVALID_ARG);
   memset(out, 0, sizeof(*out));
   const size_t es = op->precision == DG_FP64 ? 8 : 4;
@@ -794,7 +862,7 @@ dg_status predict_t(const dg_operator *op, int nrhs, const Candidate &c, double 
 }
 
 dg_status predict(const dg_operator *op, int nrhs, const Candidate &c, double *ms) {
-  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE || op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!variant_ok(op, c.variant)) return fail(DG_ERR_UNSUPPORTED);
   return op->precision == DG_FP64 ? predict_t<double>(op, nrhs, c, ms) : predict_t<float>(op, nrhs, c, ms);
 }
@@ -846,6 +914,7 @@ dg_status dg_operator_predict(const dg_operator *op, int nrhs, int variant, int 
 dg_status dg_operator_time(const dg_operator *op_c, int nrhs, int variant, int cells_per_block, int faces_per_block,
                            void *stream, double *ms) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
+  if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !ms || nrhs < 1 || nrhs > op->max_rhs || cells_per_block < 1) return fail(DG_ERR_INVALID_ARG);
   if (variant == DG_VARIANT_THREE_KERNEL && faces_per_block < 1) return fail(DG_ERR_INVALID_ARG);
   if (variant < DG_VARIANT_THREE_KERNEL || variant > DG_VARIANT_CELLWISE || !variant_ok(op, variant))
@@ -866,7 +935,7 @@ dg_status dg_operator_time(const dg_operator *op_c, int nrhs, int variant, int c
 
 dg_status dg_operator_autotune_prior(dg_operator *op, int nrhs, int measure, void *stream, dg_tune_result *out) {
   if (!op || !out || nrhs < 1 || nrhs > op->max_rhs || measure < 1) return fail(DG_ERR_INVALID_ARG);
-  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE) return fail(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || op->geo == GEO_RECOMPUTE || op->aniso) return fail(DG_ERR_UNSUPPORTED);
   memset(out, 0, sizeof(*out));
   std::vector<Candidate> cand;
   enumerate_candidates(op, cand);

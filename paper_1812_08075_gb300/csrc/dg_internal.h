@@ -131,6 +131,19 @@ template <typename T>
 cudaError_t launch_block_jacobi(const dg_operator *op, const double *tab, const T *dinv, const T *r, T *z, int nrhs,
                                 double *partial, int stride, int *blocks, cudaStream_t s);
 
+// Anisotropic degrees on affine cells (dg_aniso.cu): per-direction tables (host buffer of
+// aniso_tab_bytes<T>() bytes; returns the trace words per cell) and the three-kernel apply.
+template <typename T>
+size_t aniso_tab_bytes();
+template <typename T>
+int aniso_tables(const HostTables ht[3], void *host_tab, int *trace_size);
+template <typename T>
+cudaError_t launch_aniso_apply(const ScalarArgs<T> &a, const void *dtab, int npts, int trace_size, const T *x, T *y,
+                               T *rvol, T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
+                               int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
+void aniso_work_model(const int kax[3], int64_t ncell, int64_t nface, int64_t nbface, double flops[3],
+                      double bytes[3], int es);
+
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
@@ -211,6 +224,12 @@ struct dg_operator {
   void *sv_scal = nullptr;  // per right-hand-side scalars
   void *sv_dinv = nullptr;  // inverse diagonal of A (Jacobi preconditioner), operator precision
   std::vector<double> bj_tab;  // block-Jacobi tables (empty until first use)
+  // anisotropic degrees (dg_operator_create_aniso): per-direction tables on the device,
+  // points per cell and trace words per cell; the isotropic fields describe k_max
+  int aniso = 0;
+  int kax[3] = {0, 0, 0};
+  void *d_antab = nullptr;
+  int an_npts = 0, an_ts = 0;
   void *d_bjinv = nullptr;     // their inverse eigenvalue sums on the device, operator precision
   void *sv_graph = nullptr; // cached CUDA graph of a chunk of CG iterations (cudaGraphExec_t)
   void *sv_graph_key = nullptr;

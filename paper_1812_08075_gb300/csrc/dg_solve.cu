@@ -383,6 +383,7 @@ dg_status diagonal_by_colours(dg_operator *op, T *out, bool invert, cudaStream_t
 }
 
 dg_status ensure_block_jacobi(dg_operator *op) {
+  if (op->aniso) return dg_record_error(DG_ERR_UNSUPPORTED);
   if (!op->bj_tab.empty() && op->d_bjinv) return DG_OK;
   if (block_jacobi_tables(op, op->bj_tab) != 0) {
     op->bj_tab.clear();
@@ -671,7 +672,7 @@ extern "C" {
 dg_status dg_operator_diagonal(const dg_operator *op_c, void *diag, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !diag || ((uintptr_t)diag & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
-  if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || op->aniso) return dg_record_error(DG_ERR_UNSUPPORTED);
   cudaStream_t s = (cudaStream_t)stream;
   if (op->precision == DG_FP64) return diagonal_by_colours<double>(op, (double *)diag, false, s);
   return diagonal_by_colours<float>(op, (float *)diag, false, s);
@@ -699,7 +700,7 @@ dg_status dg_cg_solve(const dg_operator *op_c, const void *b, void *x, int nrhs,
   if (nrhs < 1 || nrhs > op->max_rhs || opt->max_iters < 1 || !(opt->rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
   if (opt->precond < DG_PRECOND_NONE || opt->precond > DG_PRECOND_BLOCK_JACOBI) return dg_record_error(DG_ERR_INVALID_ARG);
   if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
-  if (op->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  if (op->problem != DG_SCALAR || (op->aniso && opt->precond != DG_PRECOND_NONE)) return dg_record_error(DG_ERR_UNSUPPORTED);
   cudaStream_t s = (cudaStream_t)stream;
   dg_status st;
   if (op->precision == DG_FP64) st = cg_run<double>(op, (const double *)b, (double *)x, nrhs, *opt, false, true, info, s);
@@ -715,6 +716,7 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
   if (nrhs < 1 || nrhs > op64->max_rhs || nrhs > op32->max_rhs || max_outer < 1 || !(rtol > 0)) return dg_record_error(DG_ERR_INVALID_ARG);
   if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
   if (op64->problem != DG_SCALAR || op32->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  if ((op64->aniso || op32->aniso) && inner->precond != DG_PRECOND_NONE) return dg_record_error(DG_ERR_UNSUPPORTED);
   const int64_t n = op64->ndofs;
   const size_t nv = (size_t)nrhs * n;
   // FP64 residual and A x; FP32 right-hand side and correction of the inner solve

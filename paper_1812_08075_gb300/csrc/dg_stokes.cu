@@ -106,7 +106,8 @@ constexpr int kTr = 42;  // trace / face-residual slots per cell: 3 x (6 faces x
 
 template <int P, typename T>
 __host__ __device__ constexpr size_t cell_smem(int cpb) {
-  return align16<T>(sizeof(Tabs<P, P, T>)) + size_t(cpb) * (3 * P * P * P + (P - 1) * (P - 1) * (P - 1) + 8 * P * P * P) * sizeof(T);
+  return align16<T>(sizeof(Tabs<P, P, T>)) +
+         (size_t(cpb) * (3 * P * P * P + (P - 1) * (P - 1) * (P - 1) + 8 * P * P * P) + 4 * P * P * P) * sizeof(T);
 }
 
 template <int P, typename T>
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, cons
   T *Xp = Xu + cpb * 3 * P3;
   T *T1 = Xp + cpb * PP3, *T2 = T1 + cpb * M3, *PG = T2 + cpb * M3, *U = PG + cpb * M3;
   T *F = U + cpb * M3, *DV = F + 3 * cpb * M3;
+  T *WG = DV + cpb * M3;  // per point: W mu G_dd (3) and W detJ, shared by the block's cells
   const int tid = threadIdx.x, nt = blockDim.x;
   x += blockIdx.y * sx;
   rvol += blockIdx.y * sr;
@@ -130,10 +132,18 @@ __global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, cons
   for (int i = tid; i < nc * 3 * P3; i += nt) Xu[i] = x[c0 * 3 * P3 + i];
   for (int i = tid; i < nc * PP3; i += nt) Xp[i] = x[a.ncell * 3 * P3 + c0 * PP3 + i];
   for (int i = tid; i < nc * M3; i += nt) DV[i] = T(0);
-  __syncthreads();
-  to_gauss<PP, M>(Xp, PP3, T1, T2, PG, tb.interp_p, nc);
   const T hinv[3] = {T(a.nx), T(a.ny), T(a.nz)};
   const T V = T(1) / (hinv[0] * hinv[1] * hinv[2]);
+  __syncthreads();  // tables loaded
+  for (int q = tid; q < M3; q += nt) {
+    const T W = tb.w[q % M] * tb.w[(q / M) % M] * tb.w[q / M2];
+    WG[q] = W * mu * a.vol_g[0];
+    WG[M3 + q] = W * mu * a.vol_g[1];
+    WG[2 * M3 + q] = W * mu * a.vol_g[2];
+    WG[3 * M3 + q] = W * V;
+  }
+  __syncthreads();
+  to_gauss<PP, M>(Xp, PP3, T1, T2, PG, tb.interp_p, nc);
   for (int comp = 0; comp < 3; ++comp) {
     to_gauss<P, M>(Xu + comp * P3, 3 * P3, T1, T2, U, tb.interp, nc);
     T *tr = traces + c0 * (kTr * M2);
@@ -166,12 +176,10 @@ __global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, cons
         g1 = fma(tb.dcol[q1 * M + r], u[q0 + r * M + q2 * M2], g1);
         g2 = fma(tb.dcol[q2 * M + r], u[q0 + q1 * M + r * M2], g2);
       }
-      const T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
-      const T Wmu = W * mu;
-      T f[3] = {(Wmu * a.vol_g[0]) * g0, (Wmu * a.vol_g[1]) * g1, (Wmu * a.vol_g[2]) * g2};
+      T f[3] = {WG[q] * g0, WG[M3 + q] * g1, WG[2 * M3 + q] * g2};
       const T gd = comp == 0 ? g0 : (comp == 1 ? g1 : g2);
       // -(p, d_comp v_comp): coefficient of the reference derivative d_comp is -W V/h p
-      f[comp] = fma(-W * V * hinv[comp], PG[i], f[comp]);
+      f[comp] = fma(-WG[3 * M3 + q] * hinv[comp], PG[i], f[comp]);
       DV[i] = fma(hinv[comp], gd, DV[i]);
       F[i] = f[0];
       F[cpb * M3 + i] = f[1];

@@ -33,6 +33,7 @@ EXPORTED = [
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
     "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
+    "dg_operator_create_aniso",
 ]
 
 
@@ -107,6 +108,8 @@ def lib():
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_diagonal.argtypes = [vp, vp, vp]
         L.dg_operator_block_jacobi.argtypes = [vp, vp, vp, i32, vp]
+        L.dg_operator_create_aniso.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dg_penalty),
+                                               ctypes.POINTER(dg_coefficients), ctypes.POINTER(ctypes.c_void_p)]
         L.dg_apply_semilinear.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp, vp]
         L.dg_operator_predict.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_time.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
@@ -156,6 +159,14 @@ def dg_operator_create(mesh: int, degree: int, quad_points_1d: int, penalty: dg_
     h = ctypes.c_void_p()
     _check(lib().dg_operator_create(mesh, degree, quad_points_1d, ctypes.byref(penalty), ctypes.byref(coef),
                                     ctypes.byref(h)), "dg_operator_create")
+    return h.value
+
+
+def dg_operator_create_aniso(mesh: int, degrees, penalty: dg_penalty, coef: dg_coefficients) -> int:
+    h = ctypes.c_void_p()
+    ks = (ctypes.c_int32 * 3)(*degrees)
+    _check(lib().dg_operator_create_aniso(mesh, ks, ctypes.byref(penalty), ctypes.byref(coef), ctypes.byref(h)),
+           "dg_operator_create_aniso")
     return h.value
 
 
@@ -334,7 +345,8 @@ class Operator:
     def __init__(self, mesh: Mesh, degree: int, *, quad_points: int = 0, c: float = 1.0, mu: float = 1.0,
                  theta: float = -1.0, penalty_mode: int = DG_PEN_CONFIG, penalty_alpha: float = 2.0,
                  dirichlet_mask: int = 0b111111, precision: int = DG_FP64, max_rhs: int = 1,
-                 problem: int = DG_SCALAR, geometry: int = DG_GEOM_AUTO):
+                 problem: int = DG_SCALAR, geometry: int = DG_GEOM_AUTO, degrees=None):
+        """degrees=(k_0, k_1, k_2): anisotropic degrees (dg_operator_create_aniso; degree unused)."""
         import torch
         self.mesh = mesh
         self.degree = degree
@@ -343,7 +355,10 @@ class Operator:
         self.max_rhs = max_rhs
         pen = dg_penalty(penalty_mode, 0, penalty_alpha)
         co = dg_coefficients(problem, precision, dirichlet_mask, max_rhs, geometry, 0, c, mu, theta)
-        self.handle = dg_operator_create(mesh.handle, degree, quad_points, pen, co)
+        if degrees is not None:
+            self.handle = dg_operator_create_aniso(mesh.handle, degrees, pen, co)
+        else:
+            self.handle = dg_operator_create(mesh.handle, degree, quad_points, pen, co)
         self.ndofs = dg_operator_ndofs(self.handle)
         self._kappa = (None, None)
 
