@@ -146,6 +146,7 @@ static void default_blocking(dg_operator *o) {
   o->fpb = 256 / M2 > 0 ? 256 / M2 : 1;
   const int lines = o->p * o->p;  // threads per cell of the fused kernel
   o->tile = 256 / lines > 0 ? 256 / lines : 1;
+  o->brick = o->precision == DG_FP32 ? 256 : 128;  // cellwise bricks (measured best at Q1, Q2)
 }
 
 static bool fused_ok(const dg_operator *o) {

@@ -112,8 +112,17 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
 
 // The brick is 8 x 4 x BZ cells (a warp spans 8 x 4 cells); its shape is a template
 // parameter so that every shared-memory slot is an immediate offset from one address.
+// Resident blocks the compiler must allow for: FP32 Q1 and FP32 Q2 with bricks of 256
+// cells are held to 128 registers (16 warps per SM; Q1 needs no more, Q2 spills a little
+// and measured faster); the others take what they need.
 template <int P, typename T, int BZ>
-__global__ void __launch_bounds__(256) k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x,
+constexpr int cellwise_min_blocks() {
+  if (sizeof(T) == 4 && P == 2) return 512 / (32 * BZ);
+  return (P == 3 && sizeof(T) == 4 && BZ == 8) ? 2 : 1;
+}
+
+template <int P, typename T, int BZ>
+__global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x,
                                                   T *__restrict__ y, int64_t sdof, int nbx, int nby, int64_t nbricks,
                                                   int64_t nitems) {
   constexpr int M = P, P2 = P * P, P3 = P2 * P, M2 = M * M, M3 = M2 * M;
@@ -151,6 +160,15 @@ __global__ void __launch_bounds__(256) k_cellwise(const ScalarArgs<T> a, const C
       if (ry >= nay || rz >= naz) continue;
       const T *src = xr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
       T *dst = xs + row * bx * sX;
+      if constexpr (sX == P3 && sizeof(T) == 4) {
+        if ((nax * P3) % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+          // the staged row is laid out as in memory: copy it as 16-byte vectors
+          const float4 *s4 = reinterpret_cast<const float4 *>(src);
+          float4 *d4 = reinterpret_cast<float4 *>(dst);
+          for (int j = lane; j < nax * P3 / 4; j += 32) d4[j] = __ldg(s4 + j);
+          continue;
+        }
+      }
       for (int j = lane; j < nax * P3; j += 32) {
         const int cl = j / P3;
         dst[cl * sX + (j - cl * P3)] = __ldg(src + j);
@@ -384,6 +402,14 @@ __global__ void __launch_bounds__(256) k_cellwise(const ScalarArgs<T> a, const C
       if (ry >= nay || rz >= naz) continue;
       T *dst = yr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
       const T *src = xs + row * bx * sX;
+      if constexpr (sX == P3 && sizeof(T) == 4) {
+        if ((nax * P3) % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+          const float4 *s4 = reinterpret_cast<const float4 *>(src);
+          float4 *d4 = reinterpret_cast<float4 *>(dst);
+          for (int j = lane; j < nax * P3 / 4; j += 32) d4[j] = s4[j];
+          continue;
+        }
+      }
       for (int j = lane; j < nax * P3; j += 32) {
         const int cl = j / P3;
         dst[j] = src[cl * sX + (j - cl * P3)];
