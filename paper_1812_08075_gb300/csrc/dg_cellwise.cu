@@ -112,13 +112,15 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
 
 // The brick is 8 x 4 x BZ cells (a warp spans 8 x 4 cells); its shape is a template
 // parameter so that every shared-memory slot is an immediate offset from one address.
-// Resident blocks the compiler must allow for: FP32 Q1 and FP32 Q2 with bricks of 256
-// cells are held to 128 registers (16 warps per SM; Q1 needs no more, Q2 spills a little
-// and measured faster); the others take what they need.
+// Resident blocks the compiler must allow for (measured at 128^3 x 16 right-hand sides):
+// FP32 Q1 and FP32 Q2 with bricks of 256 cells are held to 128 registers (16 warps per SM;
+// Q1 needs no more, Q2 spills a little and is still fastest), Q2 with bricks of 128 cells to
+// 168 (12 warps); the others take what they need.
 template <int P, typename T, int BZ>
 constexpr int cellwise_min_blocks() {
   if (sizeof(T) == 4 && P == 2) return 512 / (32 * BZ);
-  return (P == 3 && sizeof(T) == 4 && BZ == 8) ? 2 : 1;
+  if (sizeof(T) == 4 && P == 3) return BZ == 8 ? 2 : (BZ == 4 ? 3 : 1);  // 128 / 168 / any registers
+  return 1;
 }
 
 template <int P, typename T, int BZ>
