@@ -395,6 +395,16 @@ def run_solve(args):
     x = torch.zeros_like(b)
     torch.cuda.synchronize()
     t = time.perf_counter()
+    ok, info = dg.dg_mixed_cg_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, args.delta,
+                                    dg.dg_cg_options(args.solve_rtol, 100000, 50, 1, args.precond), stream)
+    torch.cuda.synchronize()
+    t_rel = time.perf_counter() - t
+    out["mixed_reliable"] = {"seconds": t_rel, "converged": ok, "fp32_iters_max": max(i["iters"] for i in info),
+                             "updates_max": max(i["outer"] for i in info), "relres_max": max(check(x)),
+                             "delta": args.delta}
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
     ok, info = dg.dg_cg_solve(op64.handle, b.data_ptr(), x.data_ptr(), nrhs,
                               dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, p64), stream)
     torch.cuda.synchronize()
@@ -402,6 +412,7 @@ def run_solve(args):
     out["fp64_cg"] = {"seconds": t64, "converged": ok, "iters_max": max(i["iters"] for i in info),
                       "relres_max": max(check(x))}
     out["speedup_mixed_over_fp64"] = t64 / t_mixed
+    out["speedup_reliable_over_fp64"] = t64 / t_rel
     print(json.dumps(out), flush=True)
 
 
@@ -533,6 +544,8 @@ def main():
     ap.add_argument("--fp64-max-iters", type=int, default=20000)
     ap.add_argument("--precond", type=int, default=0, choices=(0, 1, 2),
                     help="0: none, 1: point Jacobi, 2: cell-block Jacobi (both solvers)")
+    ap.add_argument("--delta", type=float, default=0.1,
+                    help="reliable-update threshold of the mixed CG (FP32 residual reduction per update)")
     ap.add_argument("--precond-fp64", type=int, default=None, choices=(0, 1, 2),
                     help="preconditioner of the FP64 CG if it differs from --precond")
     args = ap.parse_args()

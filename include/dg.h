@@ -352,6 +352,21 @@ dg_status dg_refine_solve(const dg_operator *op64, const dg_operator *op32, cons
                           double *x, int nrhs, double rtol, int max_outer,
                           const dg_cg_options *inner, dg_solve_info *info, void *stream);
 
+/* Mixed-precision CG with reliable updates (residual replacement): FP32 CG iterations with
+ * op32 (batched, chunks captured in a CUDA graph as in dg_cg_solve, FP64 inner products,
+ * optional preconditioner) that continue across updates. An update adds the FP32 correction
+ * to the FP64 solution x, recomputes the residual b - A x in FP64 with op64, and replaces
+ * the FP32 residual by it while keeping the search direction; it runs at the end of a chunk
+ * when a right-hand side's FP32 residual has fallen by `delta` (0 < delta < 1) since the last
+ * one, or when the FP32 recursion reports convergence. Convergence is declared only on the
+ * FP64 residual (||b - A x|| <= opt->rtol ||b||). Unlike dg_refine_solve, no Krylov space is
+ * restarted. opt->max_iters bounds the FP32 iterations. info: iters = FP32 iterations,
+ * outer = updates, relres = FP64 relative residual. Errors as dg_refine_solve. */
+dg_status dg_mixed_cg_solve(const dg_operator *op64, const dg_operator *op32, const double *b,
+                            double *x, int nrhs, double delta, const dg_cg_options *opt,
+                            dg_solve_info *info, void *stream);
+
+
 /* y = A x for the FP64 scalar operator on the affine nx x ny x nz unit-cube mesh (the
  * same operator as dg_operator_create with vertices = NULL, DG_PEN_CONFIG penalty
  * alpha*k(k+1)/h_a, kappa = 1, one right-hand side), without any device allocation.

@@ -161,6 +161,25 @@ __global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, const T *
   block_partial2(s, t, prz, prr);
 }
 
+// r.z (z = D^-1 r, dinv NULL: z = r) and r.r without writing a direction (reliable updates).
+template <typename T>
+__global__ void k_refresh(const T *__restrict__ r, const T *__restrict__ dinv, double *prz, double *prr, int64_t n) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  double s = 0.0, t = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = r[off + i];
+    s = fma((double)v, (double)(dinv ? dinv[i] * v : v), s);
+    t = fma((double)v, (double)v, t);
+  }
+  block_partial2(s, t, prz, prr);
+}
+
+// Per rhs: reactivate (1) or stop (0) from a host flag array after a reliable update.
+__global__ void k_set_active(Scalars *S, const int *flags, int nrhs) {
+  const int r = threadIdx.x;
+  if (r < nrhs) S->active[r] = flags[r];
+}
+
 __global__ void k_init_scalars(Scalars *S, int nrhs, double rtol) {
   const int r = threadIdx.x;
   if (r >= nrhs) return;
@@ -655,6 +674,194 @@ dg_status cg_run(dg_operator *op, const T *b, T *x, int nrhs, const dg_cg_option
   return result;
 }
 
+// Mixed-precision CG with reliable updates (residual replacement, van der Vorst & Ye):
+// FP32 CG iterations with the FP32 operator on A d = r, continued across updates; at an
+// update the FP32 correction is added to the FP64 solution, the residual is recomputed in
+// FP64 with the FP64 operator and replaces the FP32 one, and the search direction is kept,
+// so the Krylov information survives (a refinement step restarts CG instead). An update
+// runs when a right-hand side's FP32 residual has fallen by delta since the last one, or
+// when the FP32 recursion thinks it has converged; convergence is only declared on the
+// FP64 residual. Inner products accumulate in FP64 throughout.
+dg_status mixed_cg_run(dg_operator *op64, dg_operator *op32, const double *b, double *x, int nrhs,
+                       const dg_cg_options &o, double delta, dg_solve_info *info, cudaStream_t s) {
+  const int64_t n = op64->ndofs;
+  const size_t nv = (size_t)nrhs * n;
+  dg_status st = ensure_workspace(op32, sizeof(float));
+  if (st != DG_OK) return st;
+  // FP64 residual and A x (op64), FP32 accumulated correction (op32)
+  const size_t need64 = nv * 2 * sizeof(double);
+  if (op64->sv_aux_bytes < need64) {
+    if (op64->sv_aux) cudaFree(op64->sv_aux);
+    op64->sv_aux = nullptr;
+    op64->sv_aux_bytes = 0;
+    if (cudaMalloc(&op64->sv_aux, need64) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+    op64->sv_aux_bytes = need64;
+  }
+  if (op32->sv_aux_bytes < nv * sizeof(float)) {
+    if (op32->sv_aux) cudaFree(op32->sv_aux);
+    op32->sv_aux = nullptr;
+    op32->sv_aux_bytes = 0;
+    if (cudaMalloc(&op32->sv_aux, nv * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+    op32->sv_aux_bytes = nv * sizeof(float);
+  }
+  if (!op64->sv_scal && cudaMalloc(&op64->sv_scal, sizeof(Workspace)) != cudaSuccess) {
+    cudaGetLastError();
+    return dg_record_error(DG_ERR_OOM);
+  }
+  double *r64 = (double *)op64->sv_aux, *ax64 = r64 + nv;
+  float *r32 = (float *)op32->sv_vec, *p = r32 + op32->max_rhs * n, *Ap = p + op32->max_rhs * n;
+  float *x32 = (float *)op32->sv_aux;
+  const float *dinv = nullptr;
+  float *z = nullptr;
+  if (o.precond == DG_PRECOND_JACOBI) {
+    if ((st = ensure_inverse_diagonal<float>(op32, s)) != DG_OK) return st;
+    dinv = (const float *)op32->sv_dinv;
+  } else if (o.precond == DG_PRECOND_BLOCK_JACOBI) {
+    if ((st = ensure_block_jacobi(op32)) != DG_OK) return st;
+    z = Ap + op32->max_rhs * n;
+  }
+  Workspace *W32 = (Workspace *)op32->sv_scal, *W64 = (Workspace *)op64->sv_scal;
+  Scalars *S32 = &W32->S, *S64 = &W64->S;
+  const bool v4 = use_v4<float>(n, x32, r32);
+  const dim3 g(grid_vec(v4 ? n / 4 : n, nrhs), nrhs), g64(grid_vec(n, nrhs), nrhs);
+  int *dflags = nullptr;
+  if (cudaMalloc(&dflags, 16 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return dg_record_error(DG_ERR_OOM); }
+  std::vector<int> flags(nrhs, 1), converged(nrhs, 0), updates(nrhs, 0);
+  std::vector<double> rr_ref(nrhs, 0.0), relres(nrhs, 1.0);
+  Scalars h32, h64;
+  cudaStream_t cs = s;
+  bool own_stream = false;
+  dg_status result = DG_ERR_NOT_CONVERGED;
+  // FP64 residual of the current x: r64 = b - A64 x, its norm and ||b|| (into S64)
+  auto true_residual = [&]() -> dg_status {
+    dg_status e = dg_apply_internal(op64, x, ax64, nrhs, cs, false);
+    if (e != DG_OK) return e;
+    k_residual<double, false><<<g64, kThreads, 0, cs>>>(b, ax64, r64, n);
+    k_dot<double, false><<<g64, kThreads, 0, cs>>>(r64, r64, W64->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, cs>>>(W64->partial, S64->rr, g64.x);
+    SCK(cudaMemcpyAsync(&h64, S64, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+    SCK(cudaStreamSynchronize(cs));
+    for (int i = 0; i < nrhs; ++i) {
+      relres[i] = h64.bb[i] > 0 ? sqrt(h64.rr[i] / h64.bb[i]) : 0.0;
+      converged[i] = relres[i] <= o.rtol;
+    }
+    return DG_OK;
+  };
+  // r32 = (float) r64, x32 = 0, and r.z, r.r of the new residual (the direction is kept)
+  auto replace_residual = [&]() -> dg_status {
+    k_to_float<<<grid_for((int64_t)nv), kThreads, 0, cs>>>(r64, r32, (int64_t)nv);
+    SCK(cudaMemsetAsync(x32, 0, nv * sizeof(float), cs));
+    if (z) {
+      int nb = 0;
+      SCK(launch_block_jacobi<float>(op32, op32->bj_tab.data(), (const float *)op32->d_bjinv, r32, z, nrhs,
+                                     W32->partial, kMaxBlocks, &nb, cs));
+      k_reduce<<<nrhs, kThreads, 0, cs>>>(W32->partial, S32->rz, nb);
+      launch_dot<float>(v4, g, cs, r32, r32, W32->partial2, n);
+      k_reduce<<<nrhs, kThreads, 0, cs>>>(W32->partial2, S32->rr, g.x);
+    } else {
+      k_refresh<float><<<g64, kThreads, 0, cs>>>(r32, dinv, W32->partial, W32->partial2, n);
+      k_reduce<<<nrhs, kThreads, 0, cs>>>(W32->partial, S32->rz, g64.x);
+      k_reduce<<<nrhs, kThreads, 0, cs>>>(W32->partial2, S32->rr, g64.x);
+    }
+    SCK(cudaGetLastError());
+    return DG_OK;
+  };
+  do {
+    if (o.use_graph && s == 0) {  // the legacy stream cannot be captured
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamSynchronize(0) != cudaSuccess) { result = dg_record_error(DG_ERR_CUDA); break; }
+      own_stream = true;
+    }
+    k_zero_scalars<<<1, 128, 0, cs>>>(S64);
+    k_dot<double, false><<<g64, kThreads, 0, cs>>>(b, b, W64->partial, n);
+    k_reduce<<<nrhs, kThreads, 0, cs>>>(W64->partial, S64->bb, g64.x);
+    if ((st = true_residual()) != DG_OK) { result = st; break; }
+    // start: p = z = M^-1 r32 with the scalars of the FP32 recursion
+    k_to_float<<<grid_for((int64_t)nv), kThreads, 0, cs>>>(r64, r32, (int64_t)nv);
+    SCK(cudaMemsetAsync(x32, 0, nv * sizeof(float), cs));
+    k_zero_scalars<<<1, 128, 0, cs>>>(S32);
+    SCK(cudaMemcpyAsync(S32->bb, S64->bb, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, cs));
+    if ((st = start_directions<float>(op32, v4, g, r32, p, dinv, z, W32, nrhs, cs)) != DG_OK) { result = st; break; }
+    // the FP32 recursion stops a right-hand side at half the target (then an update checks it)
+    k_init_scalars<<<1, 32, 0, cs>>>(S32, nrhs, 0.5 * o.rtol);
+    for (int i = 0; i < nrhs; ++i) flags[i] = !converged[i];
+    SCK(cudaMemcpyAsync(dflags, flags.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, cs));
+    k_set_active<<<1, 32, 0, cs>>>(S32, dflags, nrhs);
+    SCK(cudaMemcpyAsync(&h32, S32, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+    SCK(cudaStreamSynchronize(cs));
+    for (int i = 0; i < nrhs; ++i) rr_ref[i] = h32.rr[i];
+    const int chunk = o.chunk > 0 ? o.chunk : 25;
+    void *key = (void *)((uintptr_t)x32 ^ ((uintptr_t)r32 << 1) ^ ((uintptr_t)op32->kappa_vol << 2) ^
+                         ((uintptr_t)dinv << 5) ^ ((uintptr_t)z << 7) ^ ((uintptr_t)nrhs << 48) ^
+                         ((uintptr_t)chunk << 56) ^ (uintptr_t)0x5a5a);
+    if (o.use_graph && (op32->sv_graph == nullptr || op32->sv_graph_key != key)) {
+      drop_graph(op32);
+      const bool prof = op32->prof;
+      op32->prof = false;
+      cudaGraph_t graph;
+      SCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      dg_status est = enqueue<float>(v4, op32, x32, r32, p, Ap, dinv, z, W32, nrhs, chunk, cs);
+      cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      op32->prof = prof;
+      if (est != DG_OK) { result = est; break; }
+      if (ce != cudaSuccess) { result = dg_record_error(DG_ERR_CUDA); break; }
+      cudaGraphExec_t exec;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) { result = dg_record_error(DG_ERR_CUDA); break; }
+      op32->sv_graph = (void *)exec;
+      op32->sv_graph_key = key;
+    }
+    bool all = true;
+    for (int i = 0; i < nrhs; ++i) all = all && converged[i];
+    int done = 0;
+    while (!all && done < o.max_iters) {
+      if (o.use_graph) {
+        SCK(cudaGraphLaunch((cudaGraphExec_t)op32->sv_graph, cs));
+      } else if ((st = enqueue<float>(v4, op32, x32, r32, p, Ap, dinv, z, W32, nrhs, chunk, cs)) != DG_OK) {
+        result = st;
+        break;
+      }
+      done += chunk;
+      SCK(cudaMemcpyAsync(&h32, S32, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+      SCK(cudaStreamSynchronize(cs));
+      bool update = done >= o.max_iters;
+      for (int i = 0; i < nrhs; ++i)
+        if (!converged[i] && (!h32.active[i] || h32.rr[i] <= delta * delta * rr_ref[i])) update = true;
+      if (!update) continue;
+      k_add_correction<<<grid_for((int64_t)nv), kThreads, 0, cs>>>(x, x32, (int64_t)nv);
+      if ((st = true_residual()) != DG_OK) { result = st; break; }
+      if ((st = replace_residual()) != DG_OK) { result = st; break; }
+      all = true;
+      for (int i = 0; i < nrhs; ++i) {
+        flags[i] = !converged[i] && !h32.breakdown[i];
+        if (!converged[i]) ++updates[i];
+        all = all && converged[i];
+      }
+      SCK(cudaMemcpyAsync(dflags, flags.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, cs));
+      k_set_active<<<1, 32, 0, cs>>>(S32, dflags, nrhs);
+      SCK(cudaMemcpyAsync(&h32, S32, sizeof(Scalars), cudaMemcpyDeviceToHost, cs));
+      SCK(cudaStreamSynchronize(cs));
+      for (int i = 0; i < nrhs; ++i) rr_ref[i] = h32.rr[i];
+    }
+    if (st != DG_OK && result != DG_ERR_NOT_CONVERGED) break;
+    result = all ? DG_OK : DG_ERR_NOT_CONVERGED;
+    for (int i = 0; i < nrhs; ++i) {
+      info[i].iters = h32.iters[i];
+      info[i].outer = updates[i];
+      info[i].converged = converged[i];
+      info[i].breakdown = h32.breakdown[i];
+      info[i].relres = relres[i];
+    }
+  } while (0);
+  cudaFree(dflags);
+  if (own_stream) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  return result;
+}
+
 }  // namespace
 
 void dg_solver_release(dg_operator *op) {
@@ -783,6 +990,20 @@ dg_status dg_refine_solve(const dg_operator *op64_c, const dg_operator *op32_c, 
     info[i].breakdown = 0;
   }
   return ok ? DG_OK : dg_record_error(DG_ERR_NOT_CONVERGED);
+}
+
+dg_status dg_mixed_cg_solve(const dg_operator *op64_c, const dg_operator *op32_c, const double *b, double *x,
+                            int nrhs, double delta, const dg_cg_options *opt, dg_solve_info *info, void *stream) {
+  dg_operator *op64 = const_cast<dg_operator *>(op64_c), *op32 = const_cast<dg_operator *>(op32_c);
+  if (!op64 || !op32 || !b || !x || !opt || !info || (const void *)b == (const void *)x) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op64->precision != DG_FP64 || op32->precision != DG_FP32 || op64->ndofs != op32->ndofs) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op64->max_rhs || nrhs > op32->max_rhs || !(opt->rtol > 0) || opt->max_iters < 1) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (!(delta > 0) || delta >= 1 || opt->precond < DG_PRECOND_NONE || opt->precond > DG_PRECOND_BLOCK_JACOBI) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (((uintptr_t)b & 15u) || ((uintptr_t)x & 15u)) return dg_record_error(DG_ERR_INVALID_ARG);
+  if (op64->problem != DG_SCALAR || op32->problem != DG_SCALAR) return dg_record_error(DG_ERR_UNSUPPORTED);
+  if ((op64->aniso || op32->aniso) && opt->precond != DG_PRECOND_NONE) return dg_record_error(DG_ERR_UNSUPPORTED);
+  dg_status st = mixed_cg_run(op64, op32, b, x, nrhs, *opt, delta, info, (cudaStream_t)stream);
+  return st == DG_OK ? DG_OK : dg_record_error(st);
 }
 
 }  // extern "C"

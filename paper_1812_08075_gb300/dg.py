@@ -33,7 +33,7 @@ EXPORTED = [
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
     "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
-    "dg_operator_create_aniso",
+    "dg_operator_create_aniso", "dg_mixed_cg_solve",
 ]
 
 
@@ -116,6 +116,8 @@ def lib():
         L.dg_operator_autotune_prior.argtypes = [vp, i32, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_operator_autotune.argtypes = [vp, i32, vp, ctypes.POINTER(dg_tune_result)]
         L.dg_cg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dg_cg_options), ctypes.POINTER(dg_solve_info), vp]
+        L.dg_mixed_cg_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, ctypes.POINTER(dg_cg_options),
+                                        ctypes.POINTER(dg_solve_info), vp]
         L.dg_refine_solve.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, i32, ctypes.POINTER(dg_cg_options),
                                       ctypes.POINTER(dg_solve_info), vp]
         L.dg_apply_affine_static.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -223,6 +225,15 @@ def dg_cg_solve(op: int, b_ptr: int, x_ptr: int, nrhs: int, opt: dg_cg_options, 
     infos = (dg_solve_info * nrhs)()
     st = lib().dg_cg_solve(op, b_ptr, x_ptr, nrhs, ctypes.byref(opt), infos, stream)
     return _solve_result(st, infos, "dg_cg_solve")
+
+
+def dg_mixed_cg_solve(op64: int, op32: int, b_ptr: int, x_ptr: int, nrhs: int, delta: float, opt: dg_cg_options,
+                      stream: Optional[int]):
+    """Mixed-precision CG with reliable updates: (ok, infos); raises on errors other than
+    non-convergence."""
+    infos = (dg_solve_info * nrhs)()
+    st = lib().dg_mixed_cg_solve(op64, op32, b_ptr, x_ptr, nrhs, delta, ctypes.byref(opt), infos, stream)
+    return _solve_result(st, infos, "dg_mixed_cg_solve")
 
 
 def dg_refine_solve(op64: int, op32: int, b_ptr: int, x_ptr: int, nrhs: int, rtol: float, max_outer: int,

@@ -162,3 +162,46 @@ def test_refinement_with_jacobi_inner_solves():
     xs = x.cpu().numpy()
     for r in range(nrhs):
         assert np.linalg.norm(b[r] - orc.apply(xs[r])) <= 1.05e-10 * np.linalg.norm(b[r])
+
+
+@pytest.mark.parametrize("precond", [dg.DG_PRECOND_NONE, dg.DG_PRECOND_BLOCK_JACOBI])
+def test_mixed_cg_reliable_updates_matches_scipy(precond):
+    n, k, nrhs = (8, 6, 5), 2, 3
+    op64 = dg.Operator(dg.Mesh(*n), k, max_rhs=nrhs)
+    op32 = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    b = torch.from_numpy(rhs(n, k, nrhs)).cuda()
+    x = torch.zeros_like(b)
+    opt = dg.dg_cg_options(1e-10, 20000, 20, 1, precond)
+    ok, info = dg.dg_mixed_cg_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, 0.1, opt, None)
+    assert ok and all(i["converged"] for i in info)
+    A = oracle.Problem(*n, k).assemble()
+    bn, xn = b.cpu().numpy(), x.cpu().numpy()
+    for r in range(nrhs):
+        assert np.linalg.norm(bn[r] - A @ xn[r]) <= 1.01e-10 * np.linalg.norm(bn[r])
+        assert info[r]["relres"] <= 1e-10 and info[r]["outer"] >= 1
+    # no restarts: about as many FP32 iterations as FP64 CG needs, fewer than refinement
+    x64 = torch.zeros_like(b)
+    ok64, info64 = dg.dg_cg_solve(op64.handle, b.data_ptr(), x64.data_ptr(), nrhs,
+                                  dg.dg_cg_options(1e-10, 20000, 20, 1, precond), None)
+    xr = torch.zeros_like(b)
+    okr, infor = dg.dg_refine_solve(op64.handle, op32.handle, b.data_ptr(), xr.data_ptr(), nrhs, 1e-10, 30,
+                                    dg.dg_cg_options(1e-3, 20000, 20, 1, precond), None)
+    it_mixed = max(i["iters"] for i in info)
+    it64 = max(i["iters"] for i in info64)
+    it_ref = max(i["iters"] for i in infor)
+    print(f"precond {precond}: reliable-update FP32 iterations {it_mixed}, FP64 CG {it64}, refinement {it_ref}")
+    assert ok64 and okr and it_mixed <= 1.25 * it64 and it_mixed < it_ref
+
+
+def test_mixed_cg_reliable_updates_argument_errors():
+    op64 = dg.Operator(dg.Mesh(2, 2, 2), 1)
+    op32 = dg.Operator(dg.Mesh(2, 2, 2), 1, precision=dg.DG_FP32)
+    b = torch.ones(op64.ndofs, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    for delta in (0.0, 1.0, -0.5):
+        with pytest.raises(dg.DGError):
+            dg.dg_mixed_cg_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), 1, delta,
+                                 dg.dg_cg_options(1e-8, 100, 10, 1, 0), None)
+    with pytest.raises(dg.DGError):  # operators swapped
+        dg.dg_mixed_cg_solve(op32.handle, op64.handle, b.data_ptr(), x.data_ptr(), 1, 0.1,
+                             dg.dg_cg_options(1e-8, 100, 10, 1, 0), None)
