@@ -277,8 +277,11 @@ dg_status dg_rhs(const dg_operator *op, const void *f_vol, const void *g_face, v
  *   x and the output arrays are non-NULL, dkappa_vol[c][q] = r^T dA/dkappa_vol[c][q] x
  *   and dkappa_face[c][lf][q] likewise (layouts as dg_operator_set_kappa).
  * Geometry is recomputed from the vertex coordinates inside the kernels (nothing
- * stored is required). One right-hand side. Errors: DG_ERR_INVALID_ARG,
- * DG_ERR_UNSUPPORTED (Stokes), DG_ERR_CUDA. */
+ * stored is required). Stokes and FP32 operators give y = A^T r only (their forward
+ * kernels with the flux and symmetry coefficients exchanged; the Stokes coupling is its
+ * own transpose), and require dkappa NULL. One right-hand side. Errors:
+ * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (dkappa on Stokes or FP32, anisotropic degrees,
+ * over-integration), DG_ERR_CUDA. */
 dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y,
                            void *dkappa_vol, void *dkappa_face, void *stream);
 

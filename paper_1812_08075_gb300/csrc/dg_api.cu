@@ -531,6 +531,12 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   if (!aligned16(r) || !aligned16(y) || (x && !aligned16(x))) return fail(DG_ERR_INVALID_ARG);
   if ((dkappa_vol == nullptr) != (dkappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (dkappa_vol && (!x || !aligned16(dkappa_vol) || !aligned16(dkappa_face))) return fail(DG_ERR_INVALID_ARG);
+  if (op->problem == DG_STOKES || op->precision == DG_FP32) {
+    // no kappa to differentiate: y = A^T r is the forward operator with the flux and
+    // symmetry coefficients exchanged (the Stokes coupling [[., B^T], [B, 0]] is symmetric)
+    if (dkappa_vol) return fail(DG_ERR_UNSUPPORTED);
+    return apply_impl(op, r, y, 1, (cudaStream_t)stream, true);
+  }
   if (op->problem != DG_SCALAR || op->precision != DG_FP64 || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
   const int M2 = op->m * op->m;
   if (dkappa_vol && !op->d_tr2) {

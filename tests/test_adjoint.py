@@ -138,3 +138,80 @@ def test_finite_differences_full_config5():
             worst = max(worst, abs(fd - g) / max(abs(g), 1e-3 * float(grad.abs().max())))
     print(f"worst FD relative error {worst:.2e}")
     assert worst <= 1e-6
+
+
+# ------------------------------------------- A^T r against finite differences on every config
+
+def fd_gradient_check(op, x, b, idxs, h=1e-6):
+    """Largest relative error of dL/dx = A^T (A x - b) from dg_apply_adjoint against central
+    differences of L = 0.5 ||A x - b||^2 (formed from y+ - y- so that nothing cancels)."""
+    r = op.apply(x) - b
+    g = torch.empty_like(x)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g.data_ptr(), None, None, None)
+    worst = 0.0
+    for idx in idxs:
+        xp, xm = x.clone(), x.clone()
+        xp[idx] += h
+        xm[idx] -= h
+        yp, ym = op.apply(xp), op.apply(xm)
+        fd = float(0.5 * ((yp - ym) * (yp + ym - 2 * b)).sum() / (2 * h))
+        gi = float(g[idx])
+        worst = max(worst, abs(fd - gi) / max(abs(gi), 1e-3 * float(g.abs().max())))
+    return worst
+
+
+def test_finite_differences_config1():
+    op = dg.Operator(dg.Mesh(4, 4, 4), 2)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    b = torch.from_numpy(wl.uniform_vector(op.ndofs, 1)).cuda()
+    assert fd_gradient_check(op, x, b, np.random.default_rng(1).choice(op.ndofs, 24, replace=False)) <= 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_finite_differences_config2(k):
+    n = (64, 64, 64)
+    op = dg.Operator(dg.Mesh(*n, wl.perturbed_vertices(*n, seed=1)), k)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    b = torch.from_numpy(wl.uniform_vector(op.ndofs, 1)).cuda()
+    assert fd_gradient_check(op, x, b, np.random.default_rng(k).choice(op.ndofs, 6, replace=False)) <= 1e-6
+
+
+def test_stokes_adjoint_matches_oracle_transpose():
+    n, k = (3, 2, 4), 3
+    for theta in (-1.0, 1.0):
+        op = dg.Operator(dg.Mesh(*n), k, problem=dg.DG_STOKES, dirichlet_mask=0b111101, theta=theta)
+        orc = oracle.Problem(*n, k, problem="stokes", dirichlet_mask=0b111101, theta=theta)
+        r = wl.uniform_vector(op.ndofs, 2)
+        y = torch.empty(op.ndofs, dtype=torch.float64, device="cuda")
+        rd = torch.from_numpy(r).cuda()
+        dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y.data_ptr(), None, None, None)
+        assert relerr(y.cpu().numpy(), orc.apply(r, transpose=True)) <= TOL64
+
+
+def test_finite_differences_config3_stokes():
+    n = (32, 32, 32)
+    op = dg.Operator(dg.Mesh(*n), 3, problem=dg.DG_STOKES, dirichlet_mask=0b111101)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
+    b = torch.from_numpy(wl.uniform_vector(op.ndofs, 1)).cuda()
+    rng = np.random.default_rng(3)
+    nvel = op.mesh.ncell * 3 * 64
+    idxs = np.concatenate([rng.choice(nvel, 8, replace=False), nvel + rng.choice(op.ndofs - nvel, 4, replace=False)])
+    assert fd_gradient_check(op, x, b, idxs) <= 1e-6
+
+
+def test_finite_differences_config4_and_fp32_transpose():
+    # 128^3 affine Q2: FD of the FP64 operator's gradient; the FP32 operator's transposed
+    # apply (the persistent cellwise kernel with exchanged coefficients) against it at 1e-5
+    n = (128, 128, 128)
+    op = dg.Operator(dg.Mesh(*n), 2)
+    x = torch.from_numpy(wl.refinement_rhs(*n, 27, seeds=[0])[0]).cuda()
+    b = torch.from_numpy(wl.uniform_vector(op.ndofs, 1)).cuda()
+    assert fd_gradient_check(op, x, b, np.random.default_rng(4).choice(op.ndofs, 6, replace=False)) <= 1e-6
+    op32 = dg.Operator(dg.Mesh(*n), 2, precision=dg.DG_FP32)
+    r = b
+    g64 = torch.empty_like(r)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g64.data_ptr(), None, None, None)
+    r32 = r.float()
+    g32 = torch.empty_like(r32)
+    dg.dg_apply_adjoint(op32.handle, r32.data_ptr(), None, g32.data_ptr(), None, None, None)
+    assert float((g32.double() - g64).abs().max() / g64.abs().max()) <= 1e-5

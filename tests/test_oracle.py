@@ -559,3 +559,14 @@ def test_anisotropic_with_equal_degrees_is_the_isotropic_operator_on_a_perturbed
     iso = oracle.Problem(*n, k, vertices=verts).apply(x)
     ani = oracle.Problem(*n, k, vertices=verts, degrees=(k, k, k)).apply(x)
     assert np.abs(iso - ani).max() == 0.0
+
+
+def test_stokes_transpose_equals_assembled_transpose():
+    # theta = +1 makes the viscous block non-symmetric; the pressure coupling [[., B^T], [B, 0]]
+    # is its own transpose, so A^T swaps the viscous face coefficients only
+    p = oracle.Problem(2, 3, 2, 3, problem="stokes", theta=1.0, dirichlet_mask=0b111101)
+    A = p.assemble()
+    x = wl.uniform_vector(p.ndofs(), 1)
+    yt = p.apply(x, transpose=True)
+    np.testing.assert_allclose(yt, A.T @ x, rtol=0, atol=1e-13 * abs(yt).max())
+    assert abs(A - A.T).max() > 1e-3 * abs(A).max()
