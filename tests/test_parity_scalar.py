@@ -243,6 +243,20 @@ def test_cellwise_fp32_bricks_and_rhs(brick):
     assert run_cellwise((21, 7, 17), 2, dg.DG_FP32, nrhs=3, brick=brick, theta=1.0, mask=0b011110) <= TOL32
 
 
+def test_config4_fp64_full_size_sampled():
+    # the FP64 operator of config 4 (128^3 affine cells, Q2): residuals of the refinement
+    # and the all-FP64 CG; 16 right-hand sides through the tuned three-kernel apply
+    n, k, nrhs = (128, 128, 128), 2, 16
+    op = dg.Operator(dg.Mesh(*n), k, max_rhs=nrhs)
+    b = wl.refinement_rhs(*n, 27, seeds=range(nrhs))
+    y = op.apply(torch.from_numpy(b).cuda()).cpu().numpy().reshape(nrhs, op.mesh.ncell, 27)
+    cells = wl.sample_cells(op.mesh.ncell, 48, seed=18)
+    orc = oracle.Problem(*n, k)
+    for r in (0, 9, 15):
+        ref = orc.apply_cells(b[r], cells)
+        assert float(np.abs(y[r][cells] - ref).max() / np.abs(ref).max()) <= TOL64
+
+
 def test_config4_fp32_16rhs_full_size_sampled():
     # 128^3 affine cells, Q2, FP32, 16 right-hand sides in one persistent launch
     n, k, nrhs = (128, 128, 128), 2, 16
