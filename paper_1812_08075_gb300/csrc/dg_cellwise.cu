@@ -258,7 +258,6 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
     // per axis: volume contraction, own traces, then the face terms of the two faces
     auto axis = [&](auto Dc, T *trb) {
       constexpr int D = decltype(Dc)::value;
-      T own[4][M2];  // u and du/dxi_D on the lower (0, 1) and upper (2, 3) face
       if (act) {
 #pragma unroll
         for (int t2 = 0; t2 < M; ++t2)
@@ -289,7 +288,6 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
               u0 = fma(tb.e0[r], v[r], u0); g0 = fma(tb.d0[r], v[r], g0);
               u1 = fma(tb.e1[r], v[r], u1); g1 = fma(tb.d1[r], v[r], g1);
             }
-            own[0][pt] = u0; own[1][pt] = g0; own[2][pt] = u1; own[3][pt] = g1;
             trb[(0 * M2 + pt) * nb + tid] = u0;
             trb[(1 * M2 + pt) * nb + tid] = g0;
             trb[(2 * M2 + pt) * nb + tid] = u1;
@@ -333,7 +331,20 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
 #pragma unroll
             for (int t1 = 0; t1 < M; ++t1) {
               const int pt = t1 + M * t2;
-              const T uo = own[2 * s][pt], dno = own[2 * s + 1][pt];
+              // this cell's own trace, recomputed from its Gauss-point values (cheaper than
+              // keeping it live in registers across the barrier)
+              T uo, dno;
+              {
+                T v0 = u[lidx<M, D>(0, t1, t2)];
+                uo = (s ? tb.e1[0] : tb.e0[0]) * v0;
+                dno = (s ? tb.d1[0] : tb.d0[0]) * v0;
+#pragma unroll
+                for (int r = 1; r < M; ++r) {
+                  const T vr = u[lidx<M, D>(r, t1, t2)];
+                  uo = fma(s ? tb.e1[r] : tb.e0[r], vr, uo);
+                  dno = fma(s ? tb.d1[r] : tb.d0[r], vr, dno);
+                }
+              }
               const T hb = tb.hbw[D][pt], pwv = tb.pw[D][pt];
               T Rv, Rn;
               if (bnd) {
