@@ -146,7 +146,8 @@ static void default_blocking(dg_operator *o) {
   o->fpb = 256 / M2 > 0 ? 256 / M2 : 1;
   const int lines = o->p * o->p;  // threads per cell of the fused kernel
   o->tile = 256 / lines > 0 ? 256 / lines : 1;
-  o->brick = o->precision == DG_FP32 ? 256 : 128;  // cellwise bricks (measured best at Q1, Q2)
+  // cellwise bricks, the measured best: 8 x 4 x 8 cells for FP32 Q2, 8 x 4 x 4 otherwise
+  o->brick = (o->precision == DG_FP32 && o->p == 3) ? 256 : 128;
 }
 
 static bool fused_ok(const dg_operator *o) {

@@ -194,7 +194,7 @@ def run_cellwise(n, k, precision, nrhs=1, brick=0, theta=-1.0, mask=0b111111, c=
     op = dg.Operator(dg.Mesh(*n), k, precision=precision, max_rhs=nrhs, theta=theta, dirichlet_mask=mask, c=c)
     op.set_variant(dg.DG_VARIANT_CELLWISE, brick)
     st = op.stats()
-    assert st.variant == dg.DG_VARIANT_CELLWISE and st.cells_per_block == (brick or (256 if precision == dg.DG_FP32 else 128))
+    assert st.variant == dg.DG_VARIANT_CELLWISE and st.cells_per_block == (brick or (256 if precision == dg.DG_FP32 and k == 2 else 128))
     orc = oracle.Problem(*n, k, theta=theta, dirichlet_mask=mask, c=c)
     xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(nrhs)])
     y = op.apply(torch.from_numpy(xs).to("cuda", op.dtype)).double().cpu().numpy()
