@@ -130,6 +130,17 @@ void block_jacobi_inverse_sums(int p, const std::vector<double> &tab, std::vecto
 template <typename T>
 cudaError_t launch_block_jacobi(const dg_operator *op, const double *tab, const T *dinv, const T *r, T *z, int nrhs,
                                 double *partial, int stride, int *blocks, cudaStream_t s);
+// The same fused into preconditioned CG for FP32 operators with k <= 2 (block_jacobi_fusable):
+//   BJ_UPDATE: r -= alpha Ap in place, z = A_cc^-1 r in registers, partials of r.z into prz
+//     and of r.r into prr ([rhs * stride + block], *blocks blocks per right-hand side);
+//   BJ_DIRECTION: z = A_cc^-1 r, x += alpha p, p = z + beta p (p only where active).
+// alpha, beta, active: device arrays indexed by right-hand side.
+enum { BJ_APPLY = 0, BJ_UPDATE = 1, BJ_DIRECTION = 2 };
+bool block_jacobi_fusable(const dg_operator *op);
+cudaError_t launch_block_jacobi_fused(const dg_operator *op, const double *tab, const float *dinv, int mode, float *r,
+                                      const float *Ap, float *x, float *p, const double *alpha, const double *beta,
+                                      const int *active, int nrhs, double *prz, double *prr, int stride, int *blocks,
+                                      cudaStream_t s);
 
 // Anisotropic degrees on affine cells (dg_aniso.cu): per-direction tables (host buffer of
 // aniso_tab_bytes<T>() bytes; returns the trace words per cell) and the three-kernel apply.

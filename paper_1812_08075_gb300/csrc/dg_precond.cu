@@ -240,89 +240,187 @@ __device__ __forceinline__ void bj_sweep_pos(const BJTab<P, T> &tb, int pos, con
   }
 }
 
-template <int P, typename T>
+// The per-cell kernel also runs fused into the vector updates of preconditioned CG: the
+// block inverse is local to a cell, so it can be applied where r is produced and where
+// the direction is formed instead of in a pass of its own over r and z.
+//   BJ_APPLY:     z = A_cc^-1 r, partials of r.z.
+//   BJ_UPDATE:    r -= alpha Ap in place, z = A_cc^-1 r in registers (not stored), and
+//                 the partials of r.z and r.r.
+//   BJ_DIRECTION: z = A_cc^-1 r again, then x += alpha p and p = z + beta p with the old p
+//                 (p only while the right-hand side is active).
+// alpha, beta and the active flags are per right-hand side (device). A right-hand side
+// with alpha = 0 is left unchanged and contributes zero partials. V4: the rows of x, r,
+// Ap, p move as 16-byte vectors (FP32, sdof a multiple of 4, 16-byte aligned buffers);
+// the element order of every sum is the same with and without V4.
+template <typename T>
+struct BJFuse {
+  const double *alpha, *beta;
+  const int *active;
+  const T *Ap;
+  T *x, *p;
+  double *prr;  // r.r partials (BJ_UPDATE)
+};
+
+template <int P, typename T, int MODE, bool V4>
 __global__ void __launch_bounds__(128) k_block_jacobi_cell(const BJTab<P, T> tb, const T *__restrict__ dinv,
-                                                           const T *__restrict__ r, T *__restrict__ z, int nx, int ny,
-                                                           int nz, int64_t ncell, int64_t sdof, double *partial,
-                                                           int stride) {
+                                                           const T *__restrict__ r_in, T *__restrict__ rz_out,
+                                                           const BJFuse<T> fu, int nx, int ny, int nz, int64_t ncell,
+                                                           int64_t sdof, double *partial, int stride) {
   constexpr int P3 = P * P * P, sX = P3 | 1, NB = 128;
-  __shared__ T st[NB * sX];
+  __shared__ __align__(16) T st[NB * sX];
   auto position = [](int c, int n) { return n == 1 ? 3 : (c == 0 ? 1 : (c == n - 1 ? 2 : 0)); };
-  const int tid = threadIdx.x;
+  auto sidx = [](int i) { const int c = i / P3; return c * sX + (i - c * P3); };  // chunk element -> row slot
+  const int tid = threadIdx.x, rhs = blockIdx.y;
+  const T *src = MODE == BJ_UPDATE ? rz_out : r_in;  // BJ_UPDATE updates r in place (r_in unused)
   const int64_t nchunks = (ncell + NB - 1) / NB;
-  double dot = 0.0;
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  const T a = MODE == BJ_APPLY ? T(0) : (T)fu.alpha[rhs];
+  const bool act = MODE == BJ_DIRECTION ? fu.active[rhs] != 0 : true;
+  double dot = 0.0, dot2 = 0.0;
+  const bool work = MODE == BJ_APPLY || a != T(0);
+  for (int64_t ch = blockIdx.x; work && ch < nchunks; ch += gridDim.x) {
     const int64_t c0 = ch * NB;
-    const int nc = (int)min((int64_t)NB, ncell - c0);
-    const T *rr = r + blockIdx.y * sdof + c0 * P3;
-    T *zz = z + blockIdx.y * sdof + c0 * P3;
-    __syncthreads();  // the previous chunk's z rows were read out
-    for (int i = tid; i < nc * P3; i += NB) {
-      const int c = i / P3;
-      st[c * sX + (i - c * P3)] = rr[i];
-    }
-    __syncthreads();
-    if (tid < nc) {
-      const int64_t cell = c0 + tid, cyz = cell / nx;
-      const int px = position((int)(cell - cyz * nx), nx), py = position((int)(cyz % ny), ny),
-                pz = position((int)(cyz / ny), nz);
-      T u[P3], v[P3];
-#pragma unroll
-      for (int i = 0; i < P3; ++i) u[i] = st[tid * sX + i];
-      bj_sweep_pos<P, T, 0, true>(tb, px, u, v);
-      bj_sweep_pos<P, T, 1, true>(tb, py, v, u);
-      bj_sweep_pos<P, T, 2, true>(tb, pz, u, v);
-      const T *di = dinv + (16 * px + 4 * py + pz) * P3;
-#pragma unroll
-      for (int i = 0; i < P3; ++i) v[i] *= __ldg(di + i);
-      bj_sweep_pos<P, T, 2, false>(tb, pz, v, u);
-      bj_sweep_pos<P, T, 1, false>(tb, py, u, v);
-      bj_sweep_pos<P, T, 0, false>(tb, px, v, u);
-      T g = T(0);  // r.z of the cell (FP32 groups for FP32 vectors), then FP64
-#pragma unroll
-      for (int i = 0; i < P3; ++i) {
-        g = fma(st[tid * sX + i], u[i], g);
-        st[tid * sX + i] = u[i];
+    const int nc = (int)min((int64_t)NB, ncell - c0), ne = nc * P3, n4 = V4 ? ne / 4 : 0;
+    const int64_t off = rhs * sdof + c0 * P3;
+    __syncthreads();  // the previous chunk's rows were read out
+    if (act) {  // stage r (after r -= alpha Ap for BJ_UPDATE)
+      if constexpr (V4) {
+        for (int i = tid; i < n4; i += NB) {
+          float4 v = ((const float4 *)(src + off))[i];
+          if constexpr (MODE == BJ_UPDATE) {
+            const float4 q = ((const float4 *)(fu.Ap + off))[i];
+            v = make_float4(fmaf(-a, q.x, v.x), fmaf(-a, q.y, v.y), fmaf(-a, q.z, v.z), fmaf(-a, q.w, v.w));
+            ((float4 *)(rz_out + off))[i] = v;
+          }
+          st[sidx(4 * i)] = v.x;
+          st[sidx(4 * i + 1)] = v.y;
+          st[sidx(4 * i + 2)] = v.z;
+          st[sidx(4 * i + 3)] = v.w;
+        }
       }
-      dot += (double)g;
+      for (int i = 4 * n4 + tid; i < ne; i += NB) {
+        T v = src[off + i];
+        if constexpr (MODE == BJ_UPDATE) {
+          v = fma(-a, fu.Ap[off + i], v);
+          rz_out[off + i] = v;
+        }
+        st[sidx(i)] = v;
+      }
+      __syncthreads();
+      if (tid < nc) {
+        const int64_t cell = c0 + tid, cyz = cell / nx;
+        const int px = position((int)(cell - cyz * nx), nx), py = position((int)(cyz % ny), ny),
+                  pz = position((int)(cyz / ny), nz);
+        T u[P3], v[P3];
+#pragma unroll
+        for (int i = 0; i < P3; ++i) u[i] = st[tid * sX + i];
+        bj_sweep_pos<P, T, 0, true>(tb, px, u, v);
+        bj_sweep_pos<P, T, 1, true>(tb, py, v, u);
+        bj_sweep_pos<P, T, 2, true>(tb, pz, u, v);
+        const T *di = dinv + (16 * px + 4 * py + pz) * P3;
+#pragma unroll
+        for (int i = 0; i < P3; ++i) v[i] *= __ldg(di + i);
+        bj_sweep_pos<P, T, 2, false>(tb, pz, v, u);
+        bj_sweep_pos<P, T, 1, false>(tb, py, u, v);
+        bj_sweep_pos<P, T, 0, false>(tb, px, v, u);
+        T g = T(0), h = T(0);  // r.z and r.r of the cell (FP32 groups for FP32 vectors), then FP64
+#pragma unroll
+        for (int i = 0; i < P3; ++i) {
+          const T ri = st[tid * sX + i];
+          g = fma(ri, u[i], g);
+          if constexpr (MODE == BJ_UPDATE) h = fma(ri, ri, h);
+          if constexpr (MODE != BJ_UPDATE) st[tid * sX + i] = u[i];
+        }
+        dot += (double)g;
+        dot2 += (double)h;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int i = tid; i < nc * P3; i += NB) {
-      const int c = i / P3;
-      zz[i] = st[c * sX + (i - c * P3)];
+    if constexpr (MODE == BJ_APPLY) {
+      if constexpr (V4) {
+        for (int i = tid; i < n4; i += NB)
+          ((float4 *)(rz_out + off))[i] =
+              make_float4(st[sidx(4 * i)], st[sidx(4 * i + 1)], st[sidx(4 * i + 2)], st[sidx(4 * i + 3)]);
+      }
+      for (int i = 4 * n4 + tid; i < ne; i += NB) rz_out[off + i] = st[sidx(i)];
+    } else if constexpr (MODE == BJ_DIRECTION) {  // x += alpha p, p = z + beta p (old p)
+      const T b = act ? (T)fu.beta[rhs] : T(0);
+      if constexpr (V4) {
+        for (int i = tid; i < n4; i += NB) {
+          const float4 q = ((const float4 *)(fu.p + off))[i];
+          float4 *X = (float4 *)(fu.x + off) + i;
+          const float4 xv = *X;
+          *X = make_float4(fmaf(a, q.x, xv.x), fmaf(a, q.y, xv.y), fmaf(a, q.z, xv.z), fmaf(a, q.w, xv.w));
+          if (act)
+            ((float4 *)(fu.p + off))[i] = make_float4(fmaf(b, q.x, st[sidx(4 * i)]), fmaf(b, q.y, st[sidx(4 * i + 1)]),
+                                                      fmaf(b, q.z, st[sidx(4 * i + 2)]), fmaf(b, q.w, st[sidx(4 * i + 3)]));
+        }
+      }
+      for (int i = 4 * n4 + tid; i < ne; i += NB) {
+        const T q = fu.p[off + i];
+        fu.x[off + i] = fma(a, q, fu.x[off + i]);
+        if (act) fu.p[off + i] = fma(b, q, st[sidx(i)]);
+      }
     }
   }
-  if (partial) {
-    __shared__ double part[NB / 32];
+  if (MODE != BJ_DIRECTION && partial) {
+    __shared__ double part[2][NB / 32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
-    if ((tid & 31) == 0) part[tid >> 5] = dot;
+    for (int o = 16; o > 0; o >>= 1) {
+      dot += __shfl_down_sync(0xffffffffu, dot, o);
+      dot2 += __shfl_down_sync(0xffffffffu, dot2, o);
+    }
+    if ((tid & 31) == 0) { part[0][tid >> 5] = dot; part[1][tid >> 5] = dot2; }
     __syncthreads();
     if (tid == 0) {
-      double w = 0.0;
-      for (int i = 0; i < NB / 32; ++i) w += part[i];
-      partial[blockIdx.y * stride + blockIdx.x] = w;
+      double w = 0.0, w2 = 0.0;
+      for (int i = 0; i < NB / 32; ++i) { w += part[0][i]; w2 += part[1][i]; }
+      partial[rhs * stride + blockIdx.x] = w;
+      if (MODE == BJ_UPDATE) fu.prr[rhs * stride + blockIdx.x] = w2;
     }
   }
 }
 
 template <int P, typename T>
-cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int64_t ncell, const T *r, T *z, int nrhs,
-                   int64_t sdof, double *partial, int stride, int *blocks, cudaStream_t s) {
+BJTab<P, T> device_tab(const double *tab) {
   BJTab<P, T> tb;
   for (int d = 0; d < 3; ++d)
     for (int pos = 0; pos < 4; ++pos) {
       const double *src = tab + (d * 4 + pos) * (P * P + P);
       for (int i = 0; i < P * P; ++i) tb.S[d][pos][i] = (T)src[i];
     }
+  return tb;
+}
+
+// one wave of 16 blocks of 128 threads per SM over the right-hand sides, at most `stride`
+// blocks per right-hand side when partials are written
+inline int64_t cell_blocks(int64_t ncell, int nrhs, bool partial, int stride) {
+  const int64_t nchunks = (ncell + 127) / 128;
+  int64_t nb = (16 * 152) / nrhs > 0 ? (16 * 152) / nrhs : 1;
+  if (partial && nb > stride) nb = stride;
+  return nb > nchunks ? nchunks : nb;
+}
+
+template <typename T>
+bool vec4_ok(int64_t sdof, const void *a, const void *b, const void *c, const void *d) {
+  auto al = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
+  return sizeof(T) == 4 && sdof % 4 == 0 && al(a) && al(b) && al(c) && al(d);
+}
+
+template <int P, typename T>
+cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int64_t ncell, const T *r, T *z, int nrhs,
+                   int64_t sdof, double *partial, int stride, int *blocks, cudaStream_t s) {
+  const BJTab<P, T> tb = device_tab<P, T>(tab);
   if constexpr (P <= 3 && sizeof(T) == 4) {  // one thread per cell (FP64 stays on the lines: fewer registers, no divergence)
-    const int64_t nchunks = (ncell + 127) / 128;
-    int64_t nb = (16 * 152) / nrhs > 0 ? (16 * 152) / nrhs : 1;
-    if (partial && nb > stride) nb = stride;
-    if (nb > nchunks) nb = nchunks;
+    const int64_t nb = cell_blocks(ncell, nrhs, partial != nullptr, stride);
     if (blocks) *blocks = (int)nb;
-    k_block_jacobi_cell<P, T><<<dim3((unsigned)nb, nrhs), 128, 0, s>>>(tb, dinv, r, z, nx, ny, nz, ncell, sdof,
-                                                                        partial, stride);
+    const BJFuse<T> none{};
+    const dim3 g((unsigned)nb, nrhs);
+    if (vec4_ok<T>(sdof, r, z, z, z))
+      k_block_jacobi_cell<P, T, BJ_APPLY, true><<<g, 128, 0, s>>>(tb, dinv, r, z, none, nx, ny, nz, ncell, sdof, partial,
+                                                                  stride);
+    else
+      k_block_jacobi_cell<P, T, BJ_APPLY, false><<<g, 128, 0, s>>>(tb, dinv, r, z, none, nx, ny, nz, ncell, sdof,
+                                                                   partial, stride);
     return cudaGetLastError();
   }
   const int cpb = 256 / (P * P) > 0 ? 256 / (P * P) : 1;
@@ -336,6 +434,25 @@ cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int
   if (blocks) *blocks = (int)nb;
   k_block_jacobi<P, T><<<dim3((unsigned)nb, nrhs), threads, sm, s>>>(tb, dinv, r, z, nx, ny, nz, ncell, cpb, sdof,
                                                                       partial, stride);
+  return cudaGetLastError();
+}
+
+template <int P, int MODE>
+cudaError_t run_bj_fused(const double *tab, const float *dinv, const dg_operator *op, float *r, const BJFuse<float> &fu,
+                         int nrhs, double *prz, int stride, int *blocks, cudaStream_t s) {
+  const BJTab<P, float> tb = device_tab<P, float>(tab);
+  const int64_t sdof = op->ndofs, nb = cell_blocks(op->ncell, nrhs, true, stride);
+  if (blocks) *blocks = (int)nb;
+  const dim3 g((unsigned)nb, nrhs);
+  const bool v4 = MODE == BJ_UPDATE ? vec4_ok<float>(sdof, r, fu.Ap, r, r) : vec4_ok<float>(sdof, r, fu.x, fu.p, r);
+  const float *rin = MODE == BJ_UPDATE ? nullptr : r;
+  float *rout = MODE == BJ_UPDATE ? r : nullptr;
+  if (v4)
+    k_block_jacobi_cell<P, float, MODE, true><<<g, 128, 0, s>>>(tb, dinv, rin, rout, fu, op->nx, op->ny, op->nz,
+                                                                op->ncell, sdof, prz, stride);
+  else
+    k_block_jacobi_cell<P, float, MODE, false><<<g, 128, 0, s>>>(tb, dinv, rin, rout, fu, op->nx, op->ny, op->nz,
+                                                                 op->ncell, sdof, prz, stride);
   return cudaGetLastError();
 }
 
@@ -427,6 +544,21 @@ cudaError_t launch_block_jacobi(const dg_operator *op, const double *tab, const 
 #undef DG_BJ_CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+bool block_jacobi_fusable(const dg_operator *op) { return op->precision == DG_FP32 && op->p <= 3; }
+
+cudaError_t launch_block_jacobi_fused(const dg_operator *op, const double *tab, const float *dinv, int mode, float *r,
+                                      const float *Ap, float *x, float *p, const double *alpha, const double *beta,
+                                      const int *active, int nrhs, double *prz, double *prr, int stride, int *blocks,
+                                      cudaStream_t s) {
+  if (!block_jacobi_fusable(op) || (mode != BJ_UPDATE && mode != BJ_DIRECTION)) return cudaErrorInvalidValue;
+  const BJFuse<float> fu{alpha, beta, active, Ap, x, p, prr};
+  if (mode == BJ_UPDATE)
+    return op->p == 2 ? run_bj_fused<2, BJ_UPDATE>(tab, dinv, op, r, fu, nrhs, prz, stride, blocks, s)
+                      : run_bj_fused<3, BJ_UPDATE>(tab, dinv, op, r, fu, nrhs, prz, stride, blocks, s);
+  return op->p == 2 ? run_bj_fused<2, BJ_DIRECTION>(tab, dinv, op, r, fu, nrhs, nullptr, stride, blocks, s)
+                    : run_bj_fused<3, BJ_DIRECTION>(tab, dinv, op, r, fu, nrhs, nullptr, stride, blocks, s);
 }
 
 template cudaError_t launch_block_jacobi<double>(const dg_operator *, const double *, const double *, const double *,

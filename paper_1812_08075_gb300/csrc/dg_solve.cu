@@ -470,6 +470,23 @@ dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, con
     k_dot<T, V4><<<g, kThreads, 0, s>>>(p, Ap, W->partial, n);
     k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
     k_alpha<<<1, 32, 0, s>>>(S, nrhs);
+    if constexpr (sizeof(T) == 4) {
+      if (z && block_jacobi_fusable(op)) {
+        // the cell-block inverse inside the two vector passes: r -= alpha Ap with z = B r and
+        // the partials of r.z and r.r, then z = B r again with x += alpha p, p = z + beta p
+        // (12 vector passes per iteration instead of 15 with z stored)
+        int nb = 0;
+        const float *bjinv = (const float *)op->d_bjinv;
+        SCK(launch_block_jacobi_fused(op, op->bj_tab.data(), bjinv, BJ_UPDATE, r, Ap, x, p, S->alpha, S->beta,
+                                      S->active, nrhs, W->partial, W->partial2, kMaxBlocks, &nb, s));
+        k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, nb);
+        k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->rz_new, nb);
+        k_beta<<<1, 32, 0, s>>>(S, nrhs);
+        SCK(launch_block_jacobi_fused(op, op->bj_tab.data(), bjinv, BJ_DIRECTION, r, nullptr, x, p, S->alpha, S->beta,
+                                      S->active, nrhs, nullptr, nullptr, kMaxBlocks, nullptr, s));
+        continue;
+      }
+    }
     k_update<T, V4><<<g, kThreads, 0, s>>>(x, r, p, Ap, dinv, S, W->partial, W->partial2, n);
     if (z) {
       k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial2, S->rr, g.x);

@@ -63,10 +63,28 @@ def test_block_jacobi_positions_masks_and_thin_meshes(n, mask, c):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_block_jacobi_fp32(k):
-    err = run((5, 4, 3), k, precision=dg.DG_FP32, nrhs=3, per_cell=True)
-    print(f"block Jacobi FP32 Q{k}: rel err {err:.2e}")
+@pytest.mark.parametrize("n", [(5, 4, 3), (5, 3, 3)])
+def test_block_jacobi_fp32(k, n):
+    # (5, 3, 3) at k = 2: 1215 values per right-hand side, not a multiple of 4 (no 16-byte rows)
+    err = run(n, k, precision=dg.DG_FP32, nrhs=3, per_cell=True)
+    print(f"block Jacobi FP32 Q{k} {n}: rel err {err:.2e}")
     assert err <= TOL32
+
+
+def test_block_jacobi_fp32_many_chunks():
+    # one thread per cell over 381 chunks of 128 cells (the last one ragged), 16-byte rows
+    n, k, nrhs = (41, 36, 33), 2, 2
+    op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    rs = np.stack([wl.uniform_vector(op.ndofs, s) for s in (4, 5)])
+    z = op.block_jacobi(torch.from_numpy(rs).float().cuda()).double().cpu().numpy().reshape(nrhs, op.mesh.ncell, 27)
+    rn = rs.astype(np.float32).astype(np.float64).reshape(nrhs, op.mesh.ncell, 27)
+    orc = oracle.Problem(*n, k)
+    for cell in list(wl.sample_cells(op.mesh.ncell, 24, seed=6)) + [op.mesh.ncell - 1]:
+        for i in range(nrhs):
+            zc = np.zeros(op.ndofs)
+            zc[cell * 27:(cell + 1) * 27] = z[i, cell]
+            Az = orc.apply_cells(zc, np.array([cell]))[0]
+            assert np.abs(Az - rn[i, cell]).max() <= TOL32 * np.abs(rn[i, cell]).max()
 
 
 def test_block_jacobi_large_grid_stride():
@@ -140,3 +158,44 @@ def test_refinement_with_block_jacobi_inner_cg():
     bn, xn = b.cpu().numpy(), x.cpu().numpy()
     for r in range(nrhs):
         assert np.linalg.norm(bn[r] - A @ xn[r]) <= 1.01e-10 * np.linalg.norm(bn[r])
+
+
+def pcg_steps(A, precond, b, m):
+    """m steps of preconditioned CG from x = 0 in FP64 (the textbook recursion)."""
+    x, r = np.zeros_like(b), b.copy()
+    z = precond(r)
+    p, rz = z.copy(), r @ z
+    for _ in range(m):
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x
+
+
+@pytest.mark.parametrize("n,k", [((6, 5, 7), 2), ((8, 4, 6), 2), ((9, 5, 4), 1)])
+def test_fp32_block_jacobi_cg_steps_match_fp64_recursion(n, k):
+    # The FP32 CG applies the cell-block inverse inside its two vector passes (r -= alpha Ap
+    # with z = B r and the r.z, r.r partials; then x += alpha p, p = B r + beta p). After m
+    # iterations its x must be the FP64 recursion's x up to FP32 rounding: a wrong alpha,
+    # beta, x or p update would be off by O(1). (6, 5, 7): rows not a multiple of 4 values;
+    # (8, 4, 6): one full and one ragged chunk of 128 cells.
+    nrhs, m = 3, 6
+    op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    orc = oracle.Problem(*n, k)
+    A = orc.assemble()
+    bn = wl.refinement_rhs(*n, (k + 1) ** 3, seeds=range(nrhs)).astype(np.float32)
+    b = torch.from_numpy(bn).cuda()
+    x = torch.zeros_like(b)
+    opt = dg.dg_cg_options(1e-14, m, 1, 1, dg.DG_PRECOND_BLOCK_JACOBI)
+    ok, info = dg.dg_cg_solve(op.handle, b.data_ptr(), x.data_ptr(), nrhs, opt, None)
+    assert not ok and all(i["iters"] == m for i in info)
+    for r in range(nrhs):
+        ref = pcg_steps(A, orc.block_jacobi, bn[r].astype(np.float64), m)
+        err = relerr(x[r].double().cpu().numpy(), ref)
+        print(f"FP32 block-Jacobi CG, {m} steps, Q{k} {n}: rel err vs FP64 recursion {err:.2e}")
+        assert err <= 1e-4
