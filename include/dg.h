@@ -47,7 +47,7 @@ enum { DG_PEN_CONFIG = 0, DG_PEN_PAPER = 1 };
 enum { DG_SCALAR = 0, DG_STOKES = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
 enum { DG_GEOM_AUTO = 0, DG_GEOM_STORED = 1, DG_GEOM_RECOMPUTE = 2 };
-enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2, DG_VARIANT_CELLWISE = 3 };
+enum { DG_VARIANT_AUTO = 0, DG_VARIANT_THREE_KERNEL = 1, DG_VARIANT_FUSED = 2, DG_VARIANT_CELLWISE = 3, DG_VARIANT_DF64 = 4 };
 enum { DG_PRECOND_NONE = 0, DG_PRECOND_JACOBI = 1, DG_PRECOND_BLOCK_JACOBI = 2 };
 enum { DG_SEMILINEAR_RESIDUAL = 1, DG_SEMILINEAR_JACOBIAN = 2 };
 
@@ -103,7 +103,7 @@ typedef struct {
   int32_t threads_cell;
   int32_t threads_face;
   int32_t geometry;       /* DG_GEOM_* in effect (0 = affine fast path) */
-  int32_t variant;        /* DG_VARIANT_THREE_KERNEL, _FUSED or _CELLWISE */
+  int32_t variant;        /* DG_VARIANT_THREE_KERNEL, _FUSED, _CELLWISE or _DF64 */
   int32_t persistent_grid;/* blocks of the last fused (persistent) launch, 0 if none yet */
   int32_t reserved;
 } dg_stats;
@@ -166,6 +166,15 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
  *     face traces through shared memory; neighbours across the brick boundary are
  *     evaluated from their coefficients. Same operators as the fused variant, degree
  *     k <= 2; no scratch.
+ *   DG_VARIANT_DF64: the three kernels of an FP64 operator computing in double-float
+ *     arithmetic (each value an unevaluated sum of two FP32 numbers, about 48 significant
+ *     bits, built from error-free FP32 transformations) on the FP32 pipes, which run at
+ *     64 times the FP64 rate of this GPU. Vectors stay FP64 in memory and are converted
+ *     on load and store; tables and stored geometry get double-float copies on the first
+ *     use of the variant. Scalar FP64 operators with affine or stored geometry and
+ *     kappa = 1 (setting kappa returns the operator to DG_VARIANT_THREE_KERNEL); the
+ *     result agrees with the FP64 variant to a few 1e-14 relative. Never chosen by
+ *     DG_VARIANT_AUTO; dg_operator_autotune keeps it and tunes its blockings.
  *   DG_VARIANT_AUTO: cellwise for FP32 affine scalar operators of degree k <= 2, fused
  *     for other FP32 affine scalar operators, three-kernel otherwise.
  * cells_per_block (cells per block, cells per row tile of the fused kernel, or cells per

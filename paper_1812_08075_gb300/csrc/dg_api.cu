@@ -81,7 +81,8 @@ static void free_op(dg_operator *o) {
   if (o && o->d_antab) cudaFree(o->d_antab);
   if (!o) return;
   void *ptrs[] = {o->d_tab, o->d_verts, o->d_gamma, o->d_cellvol, o->d_gvol, o->d_gface,
-                  o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh, o->d_tr2};
+                  o->d_rvol, o->d_tr, o->d_fres, o->d_xh, o->d_yh, o->d_tr2,
+                  o->d_tab_df, o->d_gvol_df, o->d_gface_df};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
@@ -156,11 +157,49 @@ static bool fused_ok(const dg_operator *o) {
 
 static bool cellwise_ok(const dg_operator *o) { return fused_ok(o) && o->p <= 3; }
 
+// double-float three-kernel apply: FP64 scalar operators with affine or stored geometry
+// and kappa = 1 (setting kappa returns the operator to the FP64 three-kernel variant)
+static bool df64_ok(const dg_operator *o) {
+  return o->problem == DG_SCALAR && o->precision == DG_FP64 && !o->aniso && o->kappa_vol == nullptr &&
+         (o->geo == GEO_AFFINE || o->geo == GEO_STORED);
+}
+
+// Tables and stored geometry of the operator as double-float (DG_VARIANT_DF64), converted
+// once from the FP64 ones.
+static dg_status ensure_df64(dg_operator *o) {
+  if (o->d_tab_df) return DG_OK;
+  DevTables<df64> t;
+  fill_devtables(o->ht, t);
+  const int M = o->m, M2 = M * M, M3 = M2 * M;
+  void *tab = nullptr, *gv = nullptr, *gf = nullptr;
+  auto undo = [&](dg_status st) {
+    cudaGetLastError();
+    for (void *q : {tab, gv, gf})
+      if (q) cudaFree(q);
+    return fail(st);
+  };
+  if (cudaMalloc(&tab, sizeof(t)) != cudaSuccess) return undo(DG_ERR_OOM);
+  if (cudaMemcpy(tab, &t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) return undo(DG_ERR_CUDA);
+  if (o->geo == GEO_STORED) {
+    const int64_t nv = o->ncell * 7 * M3, nf = o->nface * 7 * M2;
+    if (cudaMalloc(&gv, nv * sizeof(df64)) != cudaSuccess || cudaMalloc(&gf, nf * sizeof(df64)) != cudaSuccess)
+      return undo(DG_ERR_OOM);
+    if (convert_to_df64((const double *)o->d_gvol, (df64 *)gv, nv, 0) != cudaSuccess ||
+        convert_to_df64((const double *)o->d_gface, (df64 *)gf, nf, 0) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess)
+      return undo(DG_ERR_CUDA);
+  }
+  o->d_tab_df = tab;
+  o->d_gvol_df = gv;
+  o->d_gface_df = gf;
+  return DG_OK;
+}
+
 static const size_t kMaxSmemBlock = 227 * 1024;  // opt-in shared memory per block
 
 static bool variant_ok(const dg_operator *o, int v) {
   return v == DG_VARIANT_THREE_KERNEL || (v == DG_VARIANT_FUSED && fused_ok(o)) ||
-         (v == DG_VARIANT_CELLWISE && cellwise_ok(o));
+         (v == DG_VARIANT_CELLWISE && cellwise_ok(o)) || (v == DG_VARIANT_DF64 && df64_ok(o));
 }
 
 static int resolve_variant(const dg_operator *o, int v) {
@@ -453,6 +492,16 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
     }
     return DG_OK;
   }
+  if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
+    ScalarArgs<df64> a = scalar_args<df64>(op, transpose);
+    a.tab = (const DevTables<df64> *)op->d_tab_df;
+    a.gvol = (const df64 *)op->d_gvol_df;
+    a.gface = (const df64 *)op->d_gface_df;
+    e = launch_scalar_apply<df64>(op->p, op->m, op->geo, false, a, (const double *)x, (double *)y, (df64 *)op->d_rvol,
+                                  (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s, ev);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+    return DG_OK;
+  }
   if (op->variant == DG_VARIANT_CELLWISE && cellwise_ok(op)) {
     if (op->precision == DG_FP64)
       e = launch_cellwise_apply<double>(op->p, scalar_args<double>(op, transpose), op->ht, (const double *)x,
@@ -599,10 +648,14 @@ dg_status dg_rhs(const dg_operator *op_c, const void *f_vol, const void *g_face,
 
 dg_status dg_operator_set_variant(dg_operator *op, int variant, int cells_per_block, int faces_per_block) {
   if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
-  if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_CELLWISE || cells_per_block < 0 || faces_per_block < 0)
+  if (!op || variant < DG_VARIANT_AUTO || variant > DG_VARIANT_DF64 || cells_per_block < 0 || faces_per_block < 0)
     return fail(DG_ERR_INVALID_ARG);
   const int v = resolve_variant(op, variant);
   if (!variant_ok(op, v)) return fail(DG_ERR_UNSUPPORTED);
+  if (v == DG_VARIANT_DF64) {
+    const dg_status st = ensure_df64(op);
+    if (st != DG_OK) return st;
+  }
   const size_t es = op->precision == DG_FP64 ? 8 : 4;
   const int M = op->m, P = op->p;
   if (v == DG_VARIANT_CELLWISE) {
@@ -674,13 +727,15 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
   const bool stokes = op->problem == DG_STOKES;
   do {
     if (cudaMemsetAsync(x, 0, bytes, s) != cudaSuccess) { st = fail(DG_ERR_CUDA); break; }
-    // default configuration, for reference
-    op->variant = resolve_variant(op, DG_VARIANT_AUTO);
+    // default configuration, for reference (an operator set to the double-float variant
+    // keeps it: only its blockings are tuned, the arithmetic is the caller's choice)
+    const bool df = save_v == DG_VARIANT_DF64;
+    op->variant = df ? DG_VARIANT_DF64 : resolve_variant(op, DG_VARIANT_AUTO);
     default_blocking(op);
     if ((st = time_kernels(op, x, y, nrhs, s, 2, 5, ms)) != DG_OK) break;
     out->ms_default = ms[0] + ms[1] + ms[2];
     // subproblem 1: cells per block of the cell-side kernels; subproblem 2: faces per block
-    op->variant = DG_VARIANT_THREE_KERNEL;
+    op->variant = df ? DG_VARIANT_DF64 : DG_VARIANT_THREE_KERNEL;
     default_blocking(op);
     double best_cell = 1e30, best_face = 1e30;
     int bc = op->cpb, bf = op->fpb;
@@ -708,8 +763,8 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     op->fpb = bf;
     if ((st = time_kernels(op, x, y, nrhs, s, 1, 5, ms)) != DG_OK) break;
     double best = ms[0] + ms[1] + ms[2];
-    int bv = DG_VARIANT_THREE_KERNEL, btile = save_t;
-    if (fused_ok(op)) {
+    int bv = op->variant, btile = save_t;
+    if (fused_ok(op) && !df) {
       op->variant = DG_VARIANT_FUSED;
       const int cand_t[] = {2, 4, 8, 16, 32, 64};
       const int P = op->p;
@@ -724,7 +779,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     }
     if (st != DG_OK) break;
     int bbrick = save_b;
-    if (cellwise_ok(op)) {
+    if (cellwise_ok(op) && !df) {
       op->variant = DG_VARIANT_CELLWISE;
       const int cand_b[] = {64, 128, 256};
       for (int i = 0; i < 3 && st == DG_OK; ++i) {
@@ -738,7 +793,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     }
     if (st != DG_OK) break;
     int bgeo = op->geo;
-    if (op->geo == GEO_STORED && op->precision == DG_FP64 && op->problem == DG_SCALAR && op->m == op->p) {
+    if (op->geo == GEO_STORED && op->precision == DG_FP64 && op->problem == DG_SCALAR && op->m == op->p && !df) {
       op->geo = GEO_RECOMPUTE;  // stored vs recomputed per-point geometry
       op->cpb = bc;
       op->fpb = bf;
@@ -755,7 +810,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     op->brick = bbrick;
     out->variant = bv;
     out->cells_per_block = bv == DG_VARIANT_FUSED ? btile : (bv == DG_VARIANT_CELLWISE ? bbrick : bc);
-    out->faces_per_block = bv == DG_VARIANT_THREE_KERNEL ? bf : 0;
+    out->faces_per_block = (bv == DG_VARIANT_THREE_KERNEL || bv == DG_VARIANT_DF64) ? bf : 0;
     out->ms_best = best;
   } while (0);
   if (st != DG_OK) {
@@ -924,9 +979,14 @@ dg_status dg_operator_time(const dg_operator *op_c, int nrhs, int variant, int c
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !ms || nrhs < 1 || nrhs > op->max_rhs || cells_per_block < 1) return fail(DG_ERR_INVALID_ARG);
-  if (variant == DG_VARIANT_THREE_KERNEL && faces_per_block < 1) return fail(DG_ERR_INVALID_ARG);
-  if (variant < DG_VARIANT_THREE_KERNEL || variant > DG_VARIANT_CELLWISE || !variant_ok(op, variant))
+  if ((variant == DG_VARIANT_THREE_KERNEL || variant == DG_VARIANT_DF64) && faces_per_block < 1)
+    return fail(DG_ERR_INVALID_ARG);
+  if (variant < DG_VARIANT_THREE_KERNEL || variant > DG_VARIANT_DF64 || !variant_ok(op, variant))
     return fail(DG_ERR_UNSUPPORTED);
+  if (variant == DG_VARIANT_DF64) {
+    const dg_status st = ensure_df64(op);
+    if (st != DG_OK) return st;
+  }
   if (variant == DG_VARIANT_CELLWISE) {
     const size_t sm = cellwise_smem_bytes(op->p, cells_per_block, op->precision == DG_FP64 ? 8 : 4);
     if (sm == 0 || sm > kMaxSmemBlock) return fail(DG_ERR_UNSUPPORTED);

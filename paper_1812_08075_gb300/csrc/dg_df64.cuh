@@ -1,0 +1,74 @@
+// Double-float arithmetic on the FP32 pipes for the df64 type (dg_internal.h).
+//
+// A value is hi + lo with two FP32 numbers. The operations are built from two error-free
+// transformations:
+//   TwoSum(a, b) = (s, e) with s = fl(a + b) and s + e = a + b exactly, in six
+//     additions and no branch (Knuth, TAOCP Vol. 2, Sec. 4.2.2, Theorem B);
+//   FastTwoSum(a, b) for |a| >= |b|, the same in three additions (Dekker, Numer. Math.
+//     18 (1971), 224-242);
+// and the fused multiply-add, which gives the rounding error of a product exactly:
+// a b - fl(a b) = fma(a, b, -fl(a b)).
+// Products keep the cross terms hi_a lo_b and lo_a hi_b and drop lo_a lo_b (2^-48
+// relative); sums add the low parts after a TwoSum of the high parts (the "sloppy"
+// double-double addition). The result has a relative error of a few 2^-48 per operation,
+// and in a cancelling sum an absolute error of a few 2^-48 times the operands.
+//
+// Every step uses the round-to-nearest intrinsics (__fadd_rn, __fsub_rn, __fmul_rn),
+// which the compiler never contracts into an FMA or reassociates: a contraction would
+// break the exactness of the transformations.
+#pragma once
+#include "dg_internal.h"
+
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// exact product of the high parts plus the two cross terms, as an unnormalised (p, e)
+__device__ __forceinline__ void df_prod(const df64 &a, const df64 &b, float &p, float &e) {
+  p = __fmul_rn(a.hi, b.hi);
+  e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+}
+
+__device__ __forceinline__ df64 operator*(const df64 &a, const df64 &b) {
+  float p, e;
+  df_prod(a, b, p, e);
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df64 operator+(const df64 &a, const df64 &b) {
+  const df64 s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df64 operator-(const df64 &a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(const df64 &a, const df64 &b) { return a + (-b); }
+__device__ __forceinline__ df64 &operator*=(df64 &a, const df64 &b) { return a = a * b; }
+
+// a b + c with one normalisation: the product's error term joins the low parts
+__device__ __forceinline__ df64 fma(const df64 &a, const df64 &b, const df64 &c) {
+  float p, e;
+  df_prod(a, b, p, e);
+  const df64 s = df_two_sum(p, c.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+// Conversions of the FP64 input and output vectors (identity for double and float).
+template <typename T>
+__device__ __forceinline__ T io_in(io_t<T> v) { return v; }
+template <>
+__device__ __forceinline__ df64 io_in<df64>(double v) {
+  const float h = __double2float_rn(v);
+  return df64(h, __double2float_rn(v - (double)h));
+}
+template <typename T>
+__device__ __forceinline__ io_t<T> io_out(T v) { return v; }
+__device__ __forceinline__ double io_out(df64 v) { return (double)v.hi + (double)v.lo; }

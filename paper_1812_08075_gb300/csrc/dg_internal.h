@@ -7,6 +7,25 @@
 
 #include "../../include/dg.h"
 
+// Double-float number: the unevaluated sum hi + lo of two FP32 values with |lo| at most
+// half an ulp of hi, about 48 significant bits and the FP32 exponent range. The kernel
+// variant DG_VARIANT_DF64 runs the FP64 operator's three kernels in this arithmetic on the
+// FP32 pipes (device arithmetic in dg_df64.cuh); its vectors stay FP64 in memory.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ df64(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+
+// Element type of the input and output vectors of kernels computing in T.
+template <typename T>
+struct IOType { using type = T; };
+template <>
+struct IOType<df64> { using type = double; };
+template <typename T>
+using io_t = typename IOType<T>::type;
+
 #define DG_MAXP 6  // basis points per direction (degree <= 5)
 #define DG_MAXM 7  // Gauss points per direction (k+1, or k+2 for over-integration)
 
@@ -88,7 +107,7 @@ struct LaunchInfo {
 // Launchers (dg_scalar.cu). Return cudaError_t of the launch.
 template <typename T>
 cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a,
-                                const T *x, T *y, T *rvol, T *traces, T *fres, int nrhs,
+                                const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres, int nrhs,
                                 int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
                                 LaunchInfo *query = nullptr);
@@ -120,6 +139,9 @@ cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTable
                                   int64_t stride_dofs, int cells, cudaStream_t s, const cudaEvent_t *ev,
                                   int *grid_out, LaunchInfo *query = nullptr);
 size_t cellwise_smem_bytes(int p, int cells, int es);  // 0 if (p, cells) is not supported
+
+// out[i] = in[i] as double-float (dg_scalar_df64.cu)
+cudaError_t convert_to_df64(const double *in, df64 *out, int64_t n, cudaStream_t s);
 
 // Cell-block Jacobi preconditioner by fast diagonalisation (dg_precond.cu): host tables
 // (per axis and cell position, S and L; -1 if the operator is not affine scalar SIPG with
@@ -242,6 +264,8 @@ struct dg_operator {
   void *d_antab = nullptr;
   int an_npts = 0, an_ts = 0;
   void *d_bjinv = nullptr;     // their inverse eigenvalue sums on the device, operator precision
+  // DG_VARIANT_DF64: tables and stored geometry as double-float (built on first use)
+  void *d_tab_df = nullptr, *d_gvol_df = nullptr, *d_gface_df = nullptr;
   void *sv_graph = nullptr; // cached CUDA graph of a chunk of CG iterations (cudaGraphExec_t)
   void *sv_graph_key = nullptr;
 };

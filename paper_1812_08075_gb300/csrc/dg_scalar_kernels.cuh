@@ -19,6 +19,7 @@
 //   k_back  - adds the six face residuals to R_vol along the normal direction and applies
 //             the transposed interpolation (A^(i),T, Algorithm 1 Part 3) to produce y.
 #pragma once
+#include "dg_df64.cuh"
 #include "dg_internal.h"
 
 namespace dgk {
@@ -54,7 +55,7 @@ __host__ __device__ constexpr size_t cell_smem_bytes(int cpb) {
 }
 
 template <int P, int M, typename T, int GEO, bool KAPPA>
-__global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<T> *__restrict__ x,
                                               T *__restrict__ rvol, T *__restrict__ traces,
                                               int cpb, int64_t sx, int64_t sr, int64_t st) {
   constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
@@ -72,8 +73,8 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const T *__
   const int nc = (int)min((int64_t)cpb, a.ncell - c0);
   load_tables(tb, a.tab);
   {
-    const T *xb = x + c0 * P3;
-    for (int i = tid; i < nc * P3; i += nt) S0[i] = xb[i];
+    const io_t<T> *xb = x + c0 * P3;
+    for (int i = tid; i < nc * P3; i += nt) S0[i] = io_in<T>(xb[i]);
   }
   __syncthreads();
   // axis 0: [c][j2][j1][j0] (P3) -> [c][j2][j1][q0]
@@ -419,7 +420,7 @@ __host__ __device__ constexpr size_t back_smem_bytes(int cpb) {
 
 template <int P, int M, typename T>
 __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__restrict__ rvol,
-                                              const T *__restrict__ fres, T *__restrict__ y, int cpb,
+                                              const T *__restrict__ fres, io_t<T> *__restrict__ y, int cpb,
                                               int64_t sy, int64_t sr, int64_t st) {
   constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
   __syncthreads();
   // axis 2: [c][q2][j1][j0] -> y [c][j2][j1][j0]
   {
-    T *yb = y + c0 * P3;
+    io_t<T> *yb = y + c0 * P3;
     for (int i = tid; i < nc * P3; i += nt) {
       const int c = i / P3, r = i - c * P3;
       const int j01 = r % (P * P), j2 = r / (P * P);
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
       T acc = tb.interp[j2] * src[0];
 #pragma unroll
       for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j2], src[q * P * P], acc);
-      yb[i] = acc;
+      yb[i] = io_out(acc);
     }
   }
 }

@@ -29,7 +29,7 @@ static cudaError_t query_launch(Kern k, dim3 grid, int threads, size_t sm, Launc
 }
 
 template <int P, int M, typename T, int GEO, bool KAPPA>
-static cudaError_t apply_pmk(const ScalarArgs<T> &a, const T *x, T *y, T *rvol, T *traces, T *fres,
+static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres,
                              int nrhs, int64_t sdof, int64_t srv, int64_t str, int cpb, int fpb,
                              cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q) {
   constexpr int M2 = M * M, M3 = M * M * M;
@@ -77,7 +77,7 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const T *x, T *y, T *rvol, 
 }
 
 template <int P, int M, typename T>
-static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const T *x, T *y, T *rvol,
+static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol,
                            T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
                            int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q) {
   if (geo == GEO_AFFINE) {
@@ -94,7 +94,7 @@ static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const T 
 }  // namespace dgk
 
 template <typename T>
-cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a, const T *x, T *y,
+cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y,
                                 T *rvol, T *traces, T *fres, int nrhs, int64_t stride_dofs,
                                 int64_t stride_rvol, int64_t stride_tr, int cpb, int fpb, cudaStream_t s,
                                 const cudaEvent_t *ev, LaunchInfo *query) {

@@ -22,7 +22,7 @@ DG_PEN_CONFIG, DG_PEN_PAPER = 0, 1
 DG_SCALAR, DG_STOKES = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_GEOM_AUTO, DG_GEOM_STORED, DG_GEOM_RECOMPUTE = 0, 1, 2
-DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED, DG_VARIANT_CELLWISE = 0, 1, 2, 3
+DG_VARIANT_AUTO, DG_VARIANT_THREE_KERNEL, DG_VARIANT_FUSED, DG_VARIANT_CELLWISE, DG_VARIANT_DF64 = 0, 1, 2, 3, 4
 DG_PRECOND_NONE, DG_PRECOND_JACOBI, DG_PRECOND_BLOCK_JACOBI = 0, 1, 2
 DG_SEMILINEAR_RESIDUAL, DG_SEMILINEAR_JACOBIAN = 1, 2
 

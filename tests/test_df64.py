@@ -1,0 +1,132 @@
+"""Double-float variant of the FP64 operator (DG_VARIANT_DF64: the three apply kernels in
+pairs-of-FP32 arithmetic with FP64 vectors) through the C ABI, against the oracle at the
+FP64 bound and against the FP64 variant."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_08075_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1812_08075_gb300 import build as libbuild, dg  # noqa: E402
+
+libbuild.build()
+
+# The FP64 bound. Double-float carries about 48 significant bits (unit roundoff 2^-48,
+# 3.6e-15); the sum factorisation chains a few dozen operations per output with mild
+# cancellation, so the expected error is a few 1e-14 relative to max |y|.
+TOL64 = 1e-12
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def df_operator(n, k, geom, nrhs=1, **kw):
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=nrhs, **kw)
+    op.set_variant(dg.DG_VARIANT_DF64)
+    assert op.stats().variant == dg.DG_VARIANT_DF64
+    return op, verts
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_df64_matches_oracle(k, geom):
+    n = (4, 3, 5)
+    op, verts = df_operator(n, k, geom)
+    x = wl.uniform_vector(op.ndofs, 0)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    err = relerr(y, oracle.Problem(*n, k, vertices=verts).apply(x))
+    print(f"df64 Q{k} {geom}: rel err vs oracle {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("mask,theta,c", [(0, -1.0, 1.0), (0b100110, 1.0, 0.0), (0b010101, 0.0, 2.5)])
+def test_df64_masks_theta_reaction_and_rhs(mask, theta, c):
+    n, k, nrhs = (5, 4, 3), 2, 3
+    op, _ = df_operator(n, k, "trilinear", nrhs=nrhs, dirichlet_mask=mask, theta=theta, c=c)
+    orc = oracle.Problem(*n, k, vertices=wl.perturbed_vertices(*n, seed=1), dirichlet_mask=mask, theta=theta, c=c)
+    xs = np.stack([wl.uniform_vector(op.ndofs, r) for r in range(nrhs)])
+    y = op.apply(torch.from_numpy(xs).cuda()).cpu().numpy()
+    for r in range(nrhs):
+        assert relerr(y[r], orc.apply(xs[r])) <= TOL64
+
+
+def test_df64_config2_full_size_sampled():
+    # 64^3 trilinear Q3, the benchmark workload, on 96 sampled cells
+    n, k = (64, 64, 64), 3
+    op, verts = df_operator(n, k, "trilinear")
+    x = wl.uniform_vector(op.ndofs, 0)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy().reshape(op.mesh.ncell, -1)
+    cells = wl.sample_cells(op.mesh.ncell, 96, seed=10)
+    ref = oracle.Problem(*n, k, vertices=verts).apply_cells(x, cells, nthreads=0)
+    err = float(np.abs(y[cells] - ref).max() / np.abs(ref).max())
+    print(f"df64 64^3 Q3 trilinear, sampled cells: rel err {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_df64_agrees_with_fp64_variant(k):
+    n = (24, 20, 18)
+    op, _ = df_operator(n, k, "trilinear")
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 3)).cuda()
+    y_df = op.apply(x)
+    op.set_variant(dg.DG_VARIANT_THREE_KERNEL)
+    y64 = op.apply(x)
+    err = float((y_df - y64).abs().max() / y64.abs().max())
+    print(f"df64 vs FP64 Q{k}: {err:.2e}")
+    assert err <= 1e-13
+
+
+def test_df64_blockings_and_autotune_keep_the_variant():
+    n, k = (12, 10, 9), 3
+    op, verts = df_operator(n, k, "trilinear")
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 1)).cuda()
+    ref = oracle.Problem(*n, k, vertices=verts).apply(x.cpu().numpy())
+    for cpb, fpb in [(1, 2), (2, 64), (8, 16)]:
+        op.set_variant(dg.DG_VARIANT_DF64, cpb, fpb)
+        assert relerr(op.apply(x).cpu().numpy(), ref) <= TOL64
+    res = op.autotune(nrhs=1)
+    assert res["variant"] == dg.DG_VARIANT_DF64 and op.stats().variant == dg.DG_VARIANT_DF64
+    assert relerr(op.apply(x).cpu().numpy(), ref) <= TOL64
+
+
+def test_df64_cg_solve():
+    # CG with the double-float operator reaches the FP64 target like the FP64 operator
+    n, k, nrhs = (6, 5, 7), 2, 2
+    b = torch.from_numpy(wl.refinement_rhs(*n, (k + 1) ** 3, seeds=range(nrhs))).cuda()
+    its = {}
+    for v in (dg.DG_VARIANT_THREE_KERNEL, dg.DG_VARIANT_DF64):
+        op = dg.Operator(dg.Mesh(*n), k, max_rhs=nrhs)
+        op.set_variant(v)
+        x = torch.zeros_like(b)
+        ok, info = dg.dg_cg_solve(op.handle, b.data_ptr(), x.data_ptr(), nrhs,
+                                  dg.dg_cg_options(1e-10, 5000, 20, 1, dg.DG_PRECOND_NONE), None)
+        assert ok
+        its[v] = max(i["iters"] for i in info)
+        A = oracle.Problem(*n, k).assemble()
+        for r in range(nrhs):
+            bn, xn = b[r].cpu().numpy(), x[r].cpu().numpy()
+            assert np.linalg.norm(bn - A @ xn) <= 1.01e-10 * np.linalg.norm(bn)
+    assert abs(its[dg.DG_VARIANT_DF64] - its[dg.DG_VARIANT_THREE_KERNEL]) <= 2
+
+
+def test_df64_where_it_does_not_apply():
+    for op in (dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32),
+               dg.Operator(dg.Mesh(3, 3, 3), 3, problem=dg.DG_STOKES),
+               dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, geometry=dg.DG_GEOM_RECOMPUTE)):
+        with pytest.raises(dg.DGError) as e:
+            op.set_variant(dg.DG_VARIANT_DF64)
+        assert e.value.status == dg.DG_ERR_UNSUPPORTED
+    # kappa returns the operator to the FP64 three-kernel variant
+    op, _ = df_operator((4, 4, 4), 2, "trilinear")
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, 3, seed=2)
+    op._kappa = (torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    op.set_kappa(*op._kappa)
+    assert op.stats().variant == dg.DG_VARIANT_THREE_KERNEL
