@@ -82,10 +82,11 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
     const int c = i / (P * P * M), r = i - c * (P * P * M);
     const int q0 = r % M, j12 = r / M;
     const T *src = S0 + c * P3 + j12 * P;
-    T acc = tb.interp[q0 * P] * src[0];
+    Acc<T> acc;
+    acc.init(tb.interp[q0 * P], src[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q0 * P + j], src[j], acc);
-    S1[i] = acc;
+    for (int j = 1; j < P; ++j) acc.add(tb.interp[q0 * P + j], src[j]);
+    S1[i] = acc.get();
   }
   __syncthreads();
   // axis 1: [c][j2][j1][q0] -> [c][j2][q1][q0]
@@ -93,10 +94,11 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
     const int c = i / (P * M2), r = i - c * (P * M2);
     const int q0 = r % M, q1 = (r / M) % M, j2 = r / M2;
     const T *src = S1 + c * (P * P * M) + j2 * (P * M) + q0;
-    T acc = tb.interp[q1 * P] * src[0];
+    Acc<T> acc;
+    acc.init(tb.interp[q1 * P], src[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q1 * P + j], src[j * M], acc);
-    S0[i] = acc;
+    for (int j = 1; j < P; ++j) acc.add(tb.interp[q1 * P + j], src[j * M]);
+    S0[i] = acc.get();
   }
   __syncthreads();
   // axis 2: [c][j2][q1][q0] -> U = [c][q2][q1][q0]
@@ -104,10 +106,11 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
     const int c = i / M3, r = i - c * M3;
     const int q01 = r % M2, q2 = r / M2;
     const T *src = S0 + c * (P * M2) + q01;
-    T acc = tb.interp[q2 * P] * src[0];
+    Acc<T> acc;
+    acc.init(tb.interp[q2 * P], src[0]);
 #pragma unroll
-    for (int j = 1; j < P; ++j) acc = fma(tb.interp[q2 * P + j], src[j * M2], acc);
-    S2[i] = acc;
+    for (int j = 1; j < P; ++j) acc.add(tb.interp[q2 * P + j], src[j * M2]);
+    S2[i] = acc.get();
   }
   __syncthreads();
   const T *U = S2;
@@ -125,10 +128,11 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
       else { base = qs + M * qt; stride = M2; }
       const T *row = side ? (qty ? tb.d1 : tb.e1) : (qty ? tb.d0 : tb.e0);
       const T *src = U + c * M3 + base;
-      T acc = row[0] * src[0];
+      Acc<T> acc;
+      acc.init(row[0], src[0]);
 #pragma unroll
-      for (int j = 1; j < M; ++j) acc = fma(row[j], src[j * stride], acc);
-      tr[i] = acc;
+      for (int j = 1; j < M; ++j) acc.add(row[j], src[j * stride]);
+      tr[i] = acc.get();
     }
   }
   // reference gradient at the Gauss points and the pointwise volume flux
@@ -136,15 +140,17 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
     const int c = i / M3, q = i - c * M3;
     const int q0 = q % M, q1 = (q / M) % M, q2 = q / M2;
     const T *u = U + c * M3;
-    T g0 = tb.dcol[q0 * M] * u[q1 * M + q2 * M2];
-    T g1 = tb.dcol[q1 * M] * u[q0 + q2 * M2];
-    T g2 = tb.dcol[q2 * M] * u[q0 + q1 * M];
+    Acc<T> a0, a1, a2;
+    a0.init(tb.dcol[q0 * M], u[q1 * M + q2 * M2]);
+    a1.init(tb.dcol[q1 * M], u[q0 + q2 * M2]);
+    a2.init(tb.dcol[q2 * M], u[q0 + q1 * M]);
 #pragma unroll
     for (int r = 1; r < M; ++r) {
-      g0 = fma(tb.dcol[q0 * M + r], u[r + q1 * M + q2 * M2], g0);
-      g1 = fma(tb.dcol[q1 * M + r], u[q0 + r * M + q2 * M2], g1);
-      g2 = fma(tb.dcol[q2 * M + r], u[q0 + q1 * M + r * M2], g2);
+      a0.add(tb.dcol[q0 * M + r], u[r + q1 * M + q2 * M2]);
+      a1.add(tb.dcol[q1 * M + r], u[q0 + r * M + q2 * M2]);
+      a2.add(tb.dcol[q2 * M + r], u[q0 + q1 * M + r * M2]);
     }
+    T g0 = a0.get(), g1 = a1.get(), g2 = a2.get();
     T f0, f1, f2;
     if (GEO == GEO_AFFINE) {
       T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
@@ -159,9 +165,11 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
         g0 *= kq; g1 *= kq; g2 *= kq;
       }
       const T G00 = G[0], G01 = G[M3], G02 = G[2 * M3], G11 = G[3 * M3], G12 = G[4 * M3], G22 = G[5 * M3];
-      f0 = fma(G00, g0, fma(G01, g1, G02 * g2));
-      f1 = fma(G01, g0, fma(G11, g1, G12 * g2));
-      f2 = fma(G02, g0, fma(G12, g1, G22 * g2));
+      Acc<T> b0, b1, b2;  // G g, summed from the last term as the nested FMAs would
+      b0.init(G02, g2); b0.add(G01, g1); b0.add(G00, g0);
+      b1.init(G12, g2); b1.add(G11, g1); b1.add(G01, g0);
+      b2.init(G22, g2); b2.add(G12, g1); b2.add(G02, g0);
+      f0 = b0.get(); f1 = b1.get(); f2 = b2.get();
     }
     S0[i] = f0;
     S1[i] = f1;
@@ -177,15 +185,16 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
       T mw;
       if (GEO == GEO_AFFINE) mw = (tb.w[q0] * tb.w[q1] * tb.w[q2]) * a.vol_m;
       else mw = a.gvol[(c0 + c) * (7 * M3) + 6 * M3 + q];
-      T acc = mw * U[i];
+      Acc<T> acc;
+      acc.init(mw, U[i]);
       const T *F0 = S0 + c * M3, *F1 = S1 + c * M3, *F2 = S3 + c * M3;
 #pragma unroll
       for (int r = 0; r < M; ++r) {
-        acc = fma(tb.dcol[r * M + q0], F0[r + q1 * M + q2 * M2], acc);
-        acc = fma(tb.dcol[r * M + q1], F1[q0 + r * M + q2 * M2], acc);
-        acc = fma(tb.dcol[r * M + q2], F2[q0 + q1 * M + r * M2], acc);
+        acc.add(tb.dcol[r * M + q0], F0[r + q1 * M + q2 * M2]);
+        acc.add(tb.dcol[r * M + q1], F1[q0 + r * M + q2 * M2]);
+        acc.add(tb.dcol[r * M + q2], F2[q0 + q1 * M + r * M2]);
       }
-      rv[i] = acc;
+      rv[i] = acc.get();
     }
   }
 }
@@ -226,7 +235,8 @@ __device__ __forceinline__ FaceId decode_face(const ScalarArgs<T> &a, int64_t f)
 
 template <int M, typename T>
 __host__ __device__ constexpr size_t face_smem_bytes(int fpb, int geo) {
-  return align16<T>(sizeof(SmemTables<1, M, T>)) + (geo == GEO_AFFINE ? 0 : size_t(9) * fpb * M * M * sizeof(T));
+  return align16<T>(sizeof(SmemTables<1, M, T>)) + align16<T>(fpb * sizeof(FaceId)) +
+         (geo == GEO_AFFINE ? 0 : size_t(9) * fpb * M * M * sizeof(T));
 }
 
 // trace / face-residual addressing: [cell][lf][qty][M^2]
@@ -241,12 +251,15 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   constexpr int M2 = M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &tb = *reinterpret_cast<SmemTables<1, M, T> *>(smem_raw);
-  T *SM = reinterpret_cast<T *>(smem_raw + align16<T>(sizeof(SmemTables<1, M, T>)));
+  // the block's faces, decoded once (64-bit divisions) and read by every point
+  FaceId *sF = reinterpret_cast<FaceId *>(smem_raw + align16<T>(sizeof(SmemTables<1, M, T>)));
+  T *SM = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sF) + align16<T>(fpb * sizeof(FaceId)));
   const int tid = threadIdx.x, nt = blockDim.x;
   traces += blockIdx.y * st;
   fres += blockIdx.y * st;
   const int64_t f0 = (int64_t)blockIdx.x * fpb;
   const int nf = (int)min((int64_t)fpb, a.nface - f0);
+  for (int i = tid; i < nf; i += nt) sF[i] = decode_face(a, f0 + i);
   // tables: only the weights are needed here (dcol on curved faces)
   for (int i = tid; i < M * M; i += nt) tb.dcol[i] = a.tab->dcol[i];
   for (int i = tid; i < M; i += nt) tb.w[i] = a.tab->w[i];
@@ -255,7 +268,7 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   if (GEO == GEO_AFFINE) {
     for (int i = tid; i < nf * M2; i += nt) {
       const int lfc = i / M2, qf = i - lfc * M2;
-      const FaceId F = decode_face(a, f0 + lfc);
+      const FaceId &F = sF[lfc];
       const int ax = F.axis;
       const int qs = qf % M, qt = qf / M;
       const T W = tb.w[qs] * tb.w[qt];
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   for (int i = tid; i < nf * 4 * M2; i += nt) {
     const int lfc = i / (4 * M2), r = i - lfc * (4 * M2);
     const int slot = r / M2, qf = r - slot * M2;
-    const FaceId F = decode_face(a, f0 + lfc);
+    const FaceId &F = sF[lfc];
     const int ax = F.axis;
     T v = T(0);
     if (slot < 2) {
@@ -318,32 +331,42 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   for (int i = tid; i < nf * M2; i += nt) {
     const int lfc = i / M2, qf = i - lfc * M2;
     const int64_t f = f0 + lfc;
-    const FaceId F = decode_face(a, f);
+    const FaceId &F = sF[lfc];
     const int ax = F.axis, t1 = F.t1, t2 = F.t2;
     const int qs = qf % M, qt = qf / M;
     const T *gf = a.gface + f * (7 * M2) + qf;
     const T *u0 = sU + lfc * 4 * M2;
     T *R = sR + lfc * 5 * M2;
     // tangential reference derivatives of side "-" (slot 0) or the single boundary side
-    T ds1 = tb.dcol[qs * M] * u0[qt * M], ds2 = tb.dcol[qt * M] * u0[qs];
+    Acc<T> d1, d2;
+    d1.init(tb.dcol[qs * M], u0[qt * M]);
+    d2.init(tb.dcol[qt * M], u0[qs]);
 #pragma unroll
     for (int r = 1; r < M; ++r) {
-      ds1 = fma(tb.dcol[qs * M + r], u0[r + qt * M], ds1);
-      ds2 = fma(tb.dcol[qt * M + r], u0[qs + r * M], ds2);
+      d1.add(tb.dcol[qs * M + r], u0[r + qt * M]);
+      d2.add(tb.dcol[qt * M + r], u0[qs + r * M]);
     }
+    const T ds1 = d1.get(), ds2 = d2.get();
     const T bm[3] = {gf[0], gf[M2], gf[2 * M2]};
-    const T gm = fma(bm[ax], u0[M2 + qf], fma(bm[t1], ds1, bm[t2] * ds2));
+    Acc<T> gacc;
+    gacc.init(bm[t2], ds2); gacc.add(bm[t1], ds1); gacc.add(bm[ax], u0[M2 + qf]);
+    const T gm = gacc.get();
     const T pw = gf[6 * M2];
     if (F.cm >= 0 && F.cp >= 0) {
       const T *u1 = u0 + 2 * M2;
-      T es1 = tb.dcol[qs * M] * u1[qt * M], es2 = tb.dcol[qt * M] * u1[qs];
+      Acc<T> e1, e2;
+      e1.init(tb.dcol[qs * M], u1[qt * M]);
+      e2.init(tb.dcol[qt * M], u1[qs]);
 #pragma unroll
       for (int r = 1; r < M; ++r) {
-        es1 = fma(tb.dcol[qs * M + r], u1[r + qt * M], es1);
-        es2 = fma(tb.dcol[qt * M + r], u1[qs + r * M], es2);
+        e1.add(tb.dcol[qs * M + r], u1[r + qt * M]);
+        e2.add(tb.dcol[qt * M + r], u1[qs + r * M]);
       }
+      const T es1 = e1.get(), es2 = e2.get();
       const T bp[3] = {gf[3 * M2], gf[4 * M2], gf[5 * M2]};
-      const T gp = fma(bp[ax], u1[M2 + qf], fma(bp[t1], es1, bp[t2] * es2));
+      Acc<T> pacc;
+      pacc.init(bp[t2], es2); pacc.add(bp[t1], es1); pacc.add(bp[ax], u1[M2 + qf]);
+      const T gp = pacc.get();
       T km = T(1), kp = T(1);
       if (KAPPA) {
         km = a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf];
@@ -385,27 +408,30 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   // value residual of each side: Rv + dcol^T (tangential terms)
   for (int i = tid; i < nf * M2; i += nt) {
     const int lfc = i / M2, qf = i - lfc * M2;
-    const FaceId F = decode_face(a, f0 + lfc);
+    const FaceId &F = sF[lfc];
     const int ax = F.axis;
     const int qs = qf % M, qt = qf / M;
     const T *R = sR + lfc * 5 * M2;
-    T vm = R[qf], vp = -R[qf];
+    Acc<T> vm;
+    vm.set(R[qf]);
 #pragma unroll
     for (int r = 0; r < M; ++r) {
-      vm = fma(tb.dcol[r * M + qs], R[M2 + r + qt * M], vm);
-      vm = fma(tb.dcol[r * M + qt], R[2 * M2 + qs + r * M], vm);
+      vm.add(tb.dcol[r * M + qs], R[M2 + r + qt * M]);
+      vm.add(tb.dcol[r * M + qt], R[2 * M2 + qs + r * M]);
     }
     if (F.cm >= 0 && F.cp >= 0) {
+      Acc<T> vp;
+      vp.set(-R[qf]);
 #pragma unroll
       for (int r = 0; r < M; ++r) {
-        vp = fma(tb.dcol[r * M + qs], R[3 * M2 + r + qt * M], vp);
-        vp = fma(tb.dcol[r * M + qt], R[4 * M2 + qs + r * M], vp);
+        vp.add(tb.dcol[r * M + qs], R[3 * M2 + r + qt * M]);
+        vp.add(tb.dcol[r * M + qt], R[4 * M2 + qs + r * M]);
       }
-      fres[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)] = vm;
-      fres[tr_idx<M>(F.cp, 2 * ax, 0, qf)] = vp;
+      fres[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)] = vm.get();
+      fres[tr_idx<M>(F.cp, 2 * ax, 0, qf)] = vp.get();
     } else {
       const int side = F.cm >= 0 ? 1 : 0;
-      fres[tr_idx<M>(side ? F.cm : F.cp, 2 * ax + side, 0, qf)] = vm;
+      fres[tr_idx<M>(side ? F.cm : F.cp, 2 * ax + side, 0, qf)] = vm.get();
     }
   }
 }
@@ -442,18 +468,19 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
     const int c = i / M3, q = i - c * M3;
     const int qv[3] = {q % M, (q / M) % M, q / M2};
     const T *sf = SF + c * 12 * M2;
-    T acc = S0[i];
+    Acc<T> acc;
+    acc.set(S0[i]);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const int qa = qv[ax];
       const int qf = (ax == 0) ? qv[1] + M * qv[2] : (ax == 1 ? qv[0] + M * qv[2] : qv[0] + M * qv[1]);
       const T *lo = sf + (2 * ax) * 2 * M2, *hi = sf + (2 * ax + 1) * 2 * M2;
-      acc = fma(tb.e0[qa], lo[qf], acc);
-      acc = fma(tb.d0[qa], lo[M2 + qf], acc);
-      acc = fma(tb.e1[qa], hi[qf], acc);
-      acc = fma(tb.d1[qa], hi[M2 + qf], acc);
+      acc.add(tb.e0[qa], lo[qf]);
+      acc.add(tb.d0[qa], lo[M2 + qf]);
+      acc.add(tb.e1[qa], hi[qf]);
+      acc.add(tb.d1[qa], hi[M2 + qf]);
     }
-    S1[i] = acc;
+    S1[i] = acc.get();
   }
   __syncthreads();
   // transposed interpolation, axis 0: [c][q2][q1][q0] -> [c][q2][q1][j0]
@@ -461,10 +488,11 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
     const int c = i / (M2 * P), r = i - c * (M2 * P);
     const int j0 = r % P, q12 = r / P;
     const T *src = S1 + c * M3 + q12 * M;
-    T acc = tb.interp[j0] * src[0];
+    Acc<T> acc;
+    acc.init(tb.interp[j0], src[0]);
 #pragma unroll
-    for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j0], src[q], acc);
-    S0[i] = acc;
+    for (int q = 1; q < M; ++q) acc.add(tb.interp[q * P + j0], src[q]);
+    S0[i] = acc.get();
   }
   __syncthreads();
   // axis 1: [c][q2][q1][j0] -> [c][q2][j1][j0]
@@ -472,10 +500,11 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
     const int c = i / (M * P * P), r = i - c * (M * P * P);
     const int j0 = r % P, j1 = (r / P) % P, q2 = r / (P * P);
     const T *src = S0 + c * (M2 * P) + q2 * (M * P) + j0;
-    T acc = tb.interp[j1] * src[0];
+    Acc<T> acc;
+    acc.init(tb.interp[j1], src[0]);
 #pragma unroll
-    for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j1], src[q * P], acc);
-    S1[i] = acc;
+    for (int q = 1; q < M; ++q) acc.add(tb.interp[q * P + j1], src[q * P]);
+    S1[i] = acc.get();
   }
   __syncthreads();
   // axis 2: [c][q2][j1][j0] -> y [c][j2][j1][j0]
@@ -485,10 +514,11 @@ __global__ void __launch_bounds__(256) k_back(const ScalarArgs<T> a, const T *__
       const int c = i / P3, r = i - c * P3;
       const int j01 = r % (P * P), j2 = r / (P * P);
       const T *src = S1 + c * (M * P * P) + j01;
-      T acc = tb.interp[j2] * src[0];
+      Acc<T> acc;
+      acc.init(tb.interp[j2], src[0]);
 #pragma unroll
-      for (int q = 1; q < M; ++q) acc = fma(tb.interp[q * P + j2], src[q * P * P], acc);
-      yb[i] = io_out(acc);
+      for (int q = 1; q < M; ++q) acc.add(tb.interp[q * P + j2], src[q * P * P]);
+      yb[i] = io_out(acc.get());
     }
   }
 }
