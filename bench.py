@@ -416,6 +416,24 @@ def run_solve(args):
     print(json.dumps(out), flush=True)
 
 
+def df64_entry(op, x, y64, pk, args):
+    """The benchmark operator in double-float arithmetic (DG_VARIANT_DF64): its three
+    kernels on the FP32 pipes with FP64 vectors; y64 holds the FP64 variant's A x."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    op.set_variant(dg.DG_VARIANT_DF64)
+    tuning = op.autotune(1) if args.autotune else None
+    y = torch.empty_like(y64)
+    ms, kt, _ = time_applies(op, x, y, min(args.steps, 100), 5, None, profile=True)
+    f = sum(op.stats().flops)
+    return {"variant": "double-float three-kernel (pairs of FP32, 48-bit significand)",
+            "dof_s": op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "kernel_ms": kt,
+            "fp64_equivalent_tflops": f / (ms * 1e-3) / 1e12,
+            "fp64_equivalent_frac_of_fp64_peak": f / (ms * 1e-3) / 1e12 / pk["fp64_tflops"],
+            "rel_diff_vs_fp64": float((y - y64).abs().max() / y64.abs().max()),
+            "tuning": tuning}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1812_08075_gb300 import build as libbuild, dg
@@ -480,6 +498,8 @@ def run_ours(args, rank, world, dist):
     dt = (time.perf_counter() - t) / e2e_steps
     out["e2e"] = {"value": world * op.ndofs / dt, "unit": "DOF/s", "h2d_bytes_per_step": 8 * op.ndofs,
                   "d2h_bytes_per_step": 8 * op.ndofs, "steps": e2e_steps, "api": "dg_apply_host (pinned host x, y)"}
+    if rank == 0:
+        out["df64"] = df64_entry(op, x, y, pk, args)
     del op, x, y, xh, yh
     if args.sweep and rank == 0:
         sweep = {}
@@ -500,6 +520,16 @@ def run_ours(args, rank, world, dist):
                                          "roofline_frac": t_roof / (ms_k * 1e-3),
                                          "bound": "alu" if f / (peak * 1e12) >= byt / (pk["hbm_gbs"] * 1e9) else "hbm",
                                          "kernel_ms": kt_k}
+                if prec == dg.DG_FP64:  # the same operator in double-float arithmetic, default blocking
+                    y64 = yy.clone()
+                    o.set_variant(dg.DG_VARIANT_DF64)
+                    ms_d, kt_d, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
+                    sweep[f"Q{kk}_df64"] = {"dof_s": o.ndofs / (ms_d * 1e-3), "ms": ms_d,
+                                            "fp64_equivalent_tflops": f / (ms_d * 1e-3) / 1e12,
+                                            "speedup_over_fp64": ms_k / ms_d,
+                                            "rel_diff_vs_fp64": float((yy - y64).abs().max() / y64.abs().max()),
+                                            "kernel_ms": kt_d}
+                    del y64
                 del o, xx, yy
         out["sweep"] = sweep
     if args.mixed and rank == 0:
