@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "dg_internal.h"
@@ -128,6 +129,8 @@ static ScalarArgs<T> scalar_args(const dg_operator *o, bool transpose) {
     a.face_area[d] = (T)(V / h[d]);
   }
   a.vol_m = (T)(o->c * V);
+  if constexpr (std::is_same<T, df64>::value) a.vol = df64(1.0 / ((double)o->nx * o->ny * o->nz));
+  else a.vol = T(1) / (T(o->nx) * T(o->ny) * T(o->nz));  // as the kernels computed it
   a.gvol = (const T *)o->d_gvol;
   a.gface = (const T *)o->d_gface;
   a.verts = o->d_verts;
@@ -158,9 +161,10 @@ static bool fused_ok(const dg_operator *o) {
 static bool cellwise_ok(const dg_operator *o) { return fused_ok(o) && o->p <= 3; }
 
 // double-float three-kernel apply: FP64 scalar operators with affine or stored geometry
-// and kappa = 1 (setting kappa returns the operator to the FP64 three-kernel variant)
+// and kappa = 1 (setting kappa returns the operator to the FP64 three-kernel variant),
+// and FP64 Stokes operators
 static bool df64_ok(const dg_operator *o) {
-  return o->problem == DG_SCALAR && o->precision == DG_FP64 && !o->aniso && o->kappa_vol == nullptr &&
+  return o->precision == DG_FP64 && !o->aniso && o->kappa_vol == nullptr &&
          (o->geo == GEO_AFFINE || o->geo == GEO_STORED);
 }
 
@@ -456,6 +460,15 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   cudaError_t e;
   if (op->problem == DG_STOKES) {
     const int64_t sdof = op->ndofs, srv = op->ncell * 4 * M3, str = op->ncell * 42 * M2;
+    if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
+      ScalarArgs<df64> a = scalar_args<df64>(op, transpose);
+      a.tab = (const DevTables<df64> *)op->d_tab_df;
+      e = launch_stokes_apply<df64>(op->p, a, df64(op->mu), (const double *)x, (double *)y, (df64 *)op->d_rvol,
+                                    (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s,
+                                    ev);
+      if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+      return DG_OK;
+    }
     if (op->precision == DG_FP64)
       e = launch_stokes_apply<double>(op->p, scalar_args<double>(op, transpose), op->mu, (const double *)x,
                                       (double *)y, (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_fres,

@@ -99,6 +99,12 @@ struct Acc<df64> {
   __device__ __forceinline__ df64 get() const { return df_fast_two_sum(s, c); }
 };
 
+// Store of a value computed in T to a T buffer, or of a double-float value to an FP64 one.
+template <typename T>
+__device__ __forceinline__ void store_to(T *p, const T &v) { *p = v; }
+__device__ __forceinline__ void store_to(df64 *p, const df64 &v) { *p = v; }
+__device__ __forceinline__ void store_to(double *p, const df64 &v) { *p = (double)v.hi + (double)v.lo; }
+
 // Conversions of the FP64 input and output vectors (identity for double and float).
 template <typename T>
 __device__ __forceinline__ T io_in(io_t<T> v) { return v; }

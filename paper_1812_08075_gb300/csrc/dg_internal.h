@@ -76,6 +76,7 @@ struct ScalarArgs {
   // affine fast path (axis-parallel unit-cube lattice): per-axis constants
   T vol_g[3];               // detJ * (1/h_a)^2  (times the Gauss weight in-kernel)
   T vol_m;                  // c * detJ
+  T vol;                    // detJ = 1 / (nx ny nz)
   T face_b[3];              // |F_a| / h_a : reference normal derivative weight
   T face_pw[3];             // gamma_a * |F_a|
   T face_area[3];           // |F_a| (face area element of the affine lattice)
@@ -180,7 +181,7 @@ void aniso_work_model(const int kax[3], int64_t ncell, int64_t nface, int64_t nb
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
 template <typename T>
-cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const T *x, T *y, T *rvol, T *traces,
+cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const io_t<T> *x, io_t<T> *y, T *rvol, T *traces,
                                 T *fres, int nrhs, int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
 

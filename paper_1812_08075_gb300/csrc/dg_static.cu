@@ -88,6 +88,7 @@ extern "C" dg_status dg_apply_affine_static(int nx, int ny, int nz, int degree, 
     a.face_pw[d] = penalty_alpha * degree * (degree + 1) * n[d] * V / h[d];
   }
   a.vol_m = c * V;
+  a.vol = 1.0 / ((double)nx * ny * nz);
   a.c = c;
   a.dmask = (unsigned)dirichlet_mask;
   a.sc = -1.0;

@@ -48,10 +48,11 @@ __device__ __forceinline__ void contract0(const T *in, int ics, T *out, int ocs,
     const int c = i / (O * A1 * A2), r = i - c * (O * A1 * A2);
     const int o = r % O, k12 = r / O;
     const T *src = in + c * ics + k12 * N;
-    T acc = (TR ? mat[o] : mat[o * N]) * src[0];
+    Acc<T> acc;
+    acc.init(TR ? mat[o] : mat[o * N], src[0]);
 #pragma unroll
-    for (int n = 1; n < N; ++n) acc = fma(TR ? mat[n * O + o] : mat[o * N + n], src[n], acc);
-    out[c * ocs + r] = acc;
+    for (int n = 1; n < N; ++n) acc.add(TR ? mat[n * O + o] : mat[o * N + n], src[n]);
+    out[c * ocs + r] = acc.get();
   }
 }
 
@@ -61,23 +62,26 @@ __device__ __forceinline__ void contract1(const T *in, int ics, T *out, int ocs,
     const int c = i / (A0 * O * A2), r = i - c * (A0 * O * A2);
     const int k0 = r % A0, o = (r / A0) % O, k2 = r / (A0 * O);
     const T *src = in + c * ics + k2 * (N * A0) + k0;
-    T acc = (TR ? mat[o] : mat[o * N]) * src[0];
+    Acc<T> acc;
+    acc.init(TR ? mat[o] : mat[o * N], src[0]);
 #pragma unroll
-    for (int n = 1; n < N; ++n) acc = fma(TR ? mat[n * O + o] : mat[o * N + n], src[n * A0], acc);
-    out[c * ocs + r] = acc;
+    for (int n = 1; n < N; ++n) acc.add(TR ? mat[n * O + o] : mat[o * N + n], src[n * A0]);
+    out[c * ocs + r] = acc.get();
   }
 }
 
-template <int A01, int N, int O, bool TR, typename T>
-__device__ __forceinline__ void contract2(const T *in, int ics, T *out, int ocs, const T *mat, int nc) {
+// (the output may be the FP64 result vector of a double-float apply: TO = io_t<T>)
+template <int A01, int N, int O, bool TR, typename T, typename TO>
+__device__ __forceinline__ void contract2(const T *in, int ics, TO *out, int ocs, const T *mat, int nc) {
   for (int i = threadIdx.x; i < nc * A01 * O; i += blockDim.x) {
     const int c = i / (A01 * O), r = i - c * (A01 * O);
     const int k01 = r % A01, o = r / A01;
     const T *src = in + c * ics + k01;
-    T acc = (TR ? mat[o] : mat[o * N]) * src[0];
+    Acc<T> acc;
+    acc.init(TR ? mat[o] : mat[o * N], src[0]);
 #pragma unroll
-    for (int n = 1; n < N; ++n) acc = fma(TR ? mat[n * O + o] : mat[o * N + n], src[n * A01], acc);
-    out[c * ocs + r] = acc;
+    for (int n = 1; n < N; ++n) acc.add(TR ? mat[n * O + o] : mat[o * N + n], src[n * A01]);
+    store_to(out + c * ocs + r, acc.get());
   }
 }
 
@@ -93,8 +97,8 @@ __device__ __forceinline__ void to_gauss(const T *in, int ics, T *t1, T *t2, T *
 }
 
 // transposed: Gauss-point residual [c][M^3] -> coefficients out (global, stride ocs)
-template <int NO, int M, typename T>
-__device__ __forceinline__ void from_gauss(const T *in, T *t1, T *t2, T *out, int ocs, const T *mat, int nc) {
+template <int NO, int M, typename T, typename TO>
+__device__ __forceinline__ void from_gauss(const T *in, T *t1, T *t2, TO *out, int ocs, const T *mat, int nc) {
   contract0<M, NO, M, M, true>(in, M * M * M, t1, NO * M * M, mat, nc);
   __syncthreads();
   contract1<NO, M, NO, M, true>(t1, NO * M * M, t2, NO * NO * M, mat, nc);
@@ -111,7 +115,7 @@ __host__ __device__ constexpr size_t cell_smem(int cpb) {
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, const T mu, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, const T mu, const io_t<T> *__restrict__ x,
                                                      T *__restrict__ rvol, T *__restrict__ traces, int cpb,
                                                      int64_t sx, int64_t sr, int64_t st) {
   constexpr int M = P, PP = P - 1, P3 = P * P * P, PP3 = PP * PP * PP, M2 = M * M, M3 = M * M * M;
@@ -129,11 +133,11 @@ __global__ void __launch_bounds__(256) k_stokes_cell(const ScalarArgs<T> a, cons
   const int64_t c0 = (int64_t)blockIdx.x * cpb;
   const int nc = (int)min((int64_t)cpb, a.ncell - c0);
   load_tabs(tb, a.tab);
-  for (int i = tid; i < nc * 3 * P3; i += nt) Xu[i] = x[c0 * 3 * P3 + i];
-  for (int i = tid; i < nc * PP3; i += nt) Xp[i] = x[a.ncell * 3 * P3 + c0 * PP3 + i];
+  for (int i = tid; i < nc * 3 * P3; i += nt) Xu[i] = io_in<T>(x[c0 * 3 * P3 + i]);
+  for (int i = tid; i < nc * PP3; i += nt) Xp[i] = io_in<T>(x[a.ncell * 3 * P3 + c0 * PP3 + i]);
   for (int i = tid; i < nc * M3; i += nt) DV[i] = T(0);
   const T hinv[3] = {T(a.nx), T(a.ny), T(a.nz)};
-  const T V = T(1) / (hinv[0] * hinv[1] * hinv[2]);
+  const T V = a.vol;
   __syncthreads();  // tables loaded
   for (int q = tid; q < M3; q += nt) {
     const T W = tb.w[q % M] * tb.w[(q / M) % M] * tb.w[q / M2];
@@ -309,7 +313,7 @@ __host__ __device__ constexpr size_t back_smem(int cpb) {
 
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_stokes_back(const ScalarArgs<T> a, const T *__restrict__ rvol,
-                                                     const T *__restrict__ fres, T *__restrict__ y, int cpb,
+                                                     const T *__restrict__ fres, io_t<T> *__restrict__ y, int cpb,
                                                      int64_t sy, int64_t sr, int64_t st) {
   constexpr int M = P, PP = P - 1, P3 = P * P * P, PP3 = PP * PP * PP, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -334,23 +338,24 @@ __global__ void __launch_bounds__(256) k_stokes_back(const ScalarArgs<T> a, cons
       const int c = i / M3, q = i - c * M3;
       const int qv[3] = {q % M, (q / M) % M, q / M2};
       const T *sf = SF + c * kTr * M2;
-      T acc = R[i];
+      Acc<T> acc;
+      acc.set(R[i]);
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         const int qa = qv[ax];
         const int qf = (ax == 0) ? qv[1] + M * qv[2] : (ax == 1 ? qv[0] + M * qv[2] : qv[0] + M * qv[1]);
         if (comp < 3) {
           const T *lo = sf + (comp * 12 + 4 * ax) * M2, *hi = lo + 2 * M2;
-          acc = fma(tb.e0[qa], lo[qf], acc);
-          acc = fma(tb.d0[qa], lo[M2 + qf], acc);
-          acc = fma(tb.e1[qa], hi[qf], acc);
-          acc = fma(tb.d1[qa], hi[M2 + qf], acc);
+          acc.add(tb.e0[qa], lo[qf]);
+          acc.add(tb.d0[qa], lo[M2 + qf]);
+          acc.add(tb.e1[qa], hi[qf]);
+          acc.add(tb.d1[qa], hi[M2 + qf]);
         } else {
-          acc = fma(tb.e0[qa], sf[(36 + 2 * ax) * M2 + qf], acc);
-          acc = fma(tb.e1[qa], sf[(36 + 2 * ax + 1) * M2 + qf], acc);
+          acc.add(tb.e0[qa], sf[(36 + 2 * ax) * M2 + qf]);
+          acc.add(tb.e1[qa], sf[(36 + 2 * ax + 1) * M2 + qf]);
         }
       }
-      T1[i] = acc;
+      T1[i] = acc.get();
     }
     __syncthreads();
     if (comp < 3) {
@@ -375,7 +380,7 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 }
 
 template <int P, typename T>
-cudaError_t apply_p(const ScalarArgs<T> &a, T mu, const T *x, T *y, T *rvol, T *tr, T *fres, int nrhs, int64_t sdof,
+cudaError_t apply_p(const ScalarArgs<T> &a, T mu, const io_t<T> *x, io_t<T> *y, T *rvol, T *tr, T *fres, int nrhs, int64_t sdof,
                     int64_t srv, int64_t str, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev) {
   constexpr int M = P, M2 = M * M, M3 = M * M * M;
   cudaError_t e;
@@ -410,7 +415,7 @@ cudaError_t apply_p(const ScalarArgs<T> &a, T mu, const T *x, T *y, T *rvol, T *
 }  // namespace dgs
 
 template <typename T>
-cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const T *x, T *y, T *rvol, T *traces, T *fres,
+cudaError_t launch_stokes_apply(int p, const ScalarArgs<T> &a, T mu, const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres,
                                 int nrhs, int64_t sdof, int64_t srv, int64_t str, int cpb, int fpb, cudaStream_t s,
                                 const cudaEvent_t *ev) {
   switch (p) {
@@ -428,3 +433,6 @@ template cudaError_t launch_stokes_apply<double>(int, const ScalarArgs<double> &
 template cudaError_t launch_stokes_apply<float>(int, const ScalarArgs<float> &, float, const float *, float *, float *,
                                                 float *, float *, int, int64_t, int64_t, int64_t, int, int,
                                                 cudaStream_t, const cudaEvent_t *);
+template cudaError_t launch_stokes_apply<df64>(int, const ScalarArgs<df64> &, df64, const double *, double *, df64 *,
+                                               df64 *, df64 *, int, int64_t, int64_t, int64_t, int, int, cudaStream_t,
+                                               const cudaEvent_t *);

@@ -122,9 +122,34 @@ def test_df64_cg_solve():
     assert abs(its[dg.DG_VARIANT_DF64] - its[dg.DG_VARIANT_THREE_KERNEL]) <= 2
 
 
+@pytest.mark.parametrize("k,n,mask,theta,mu,nrhs", [(2, (3, 2, 4), 0b111101, -1.0, 1.0, 1),
+                                                   (3, (4, 3, 2), 0b010110, 1.0, 0.7, 2),
+                                                   (4, (2, 3, 2), 0, -1.0, 2.5, 1), (5, (2, 2, 3), 0b111111, 0.0, 1.0, 1)])
+def test_df64_stokes_matches_oracle(k, n, mask, theta, mu, nrhs):
+    op = dg.Operator(dg.Mesh(*n), k, problem=dg.DG_STOKES, mu=mu, theta=theta, dirichlet_mask=mask, max_rhs=nrhs)
+    op.set_variant(dg.DG_VARIANT_DF64)
+    assert op.stats().variant == dg.DG_VARIANT_DF64
+    orc = oracle.Problem(*n, k, problem="stokes", mu=mu, theta=theta, dirichlet_mask=mask)
+    xs = np.stack([wl.uniform_vector(op.ndofs, 20 + r) for r in range(nrhs)])
+    y = op.apply(torch.from_numpy(xs)[0 if nrhs == 1 else slice(None)].cuda()).cpu().numpy().reshape(nrhs, -1)
+    err = max(relerr(y[r], orc.apply(xs[r])) for r in range(nrhs))
+    print(f"df64 Stokes Q{k}/Q{k - 1}: rel err vs oracle {err:.2e}")
+    assert err <= TOL64
+
+
+def test_df64_stokes_agrees_with_fp64_variant():
+    op = dg.Operator(dg.Mesh(16, 16, 16), 3, problem=dg.DG_STOKES)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    y64 = op.apply(x)
+    op.set_variant(dg.DG_VARIANT_DF64)
+    err = float((op.apply(x) - y64).abs().max() / y64.abs().max())
+    print(f"df64 vs FP64 Stokes Q3/Q2 at 16^3: {err:.2e}")
+    assert err <= TOL_DF_VS_FP64
+
+
 def test_df64_where_it_does_not_apply():
     for op in (dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32),
-               dg.Operator(dg.Mesh(3, 3, 3), 3, problem=dg.DG_STOKES),
+               dg.Operator(dg.Mesh(3, 3, 3), 3, problem=dg.DG_STOKES, precision=dg.DG_FP32),
                dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, geometry=dg.DG_GEOM_RECOMPUTE)):
         with pytest.raises(dg.DGError) as e:
             op.set_variant(dg.DG_VARIANT_DF64)
