@@ -271,9 +271,18 @@ def stokes_apply(pk, n_cells=32, k=3):
     y = torch.empty_like(x)
     ms, kt, _ = time_applies(op, x, y, 20, 3, None, profile=True)
     f = sum(op.stats().flops)
+    # the same operator in double-float arithmetic (DG_VARIANT_DF64), blockings tuned
+    y64 = y.clone()
+    op.set_variant(dg.DG_VARIANT_DF64)
+    op.autotune(1)
+    ms_d, kt_d, _ = time_applies(op, x, y, 20, 3, None, profile=True)
+    df = {"dof_s": op.ndofs / (ms_d * 1e-3), "ms": ms_d, "kernel_ms": kt_d, "speedup_over_fp64": ms / ms_d,
+          "fp64_equivalent_tflops": f / (ms_d * 1e-3) / 1e12,
+          "rel_diff_vs_fp64": float((y - y64).abs().max() / y64.abs().max())}
     return {"workload": f"DG Stokes, {n_cells}^3 affine cells, velocity Q{k} x3 + pressure Q{k - 1}, FP64",
             "ndofs": op.ndofs, "dof_s": op.ndofs / (ms * 1e-3), "ms": ms, "kernel_ms": kt,
-            "tflops_model": f / (ms * 1e-3) / 1e12, "frac_fp64_peak_model": f / (ms * 1e-3) / 1e12 / pk["fp64_tflops"]}
+            "tflops_model": f / (ms * 1e-3) / 1e12, "frac_fp64_peak_model": f / (ms * 1e-3) / 1e12 / pk["fp64_tflops"],
+            "df64": df}
 
 
 def adjoint_apply(n_cells=64, k=3):

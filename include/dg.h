@@ -171,9 +171,9 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out);
  *     bits, built from error-free FP32 transformations) on the FP32 pipes, which run at
  *     64 times the FP64 rate of this GPU. Vectors stay FP64 in memory and are converted
  *     on load and store; tables and stored geometry get double-float copies on the first
- *     use of the variant. FP64 Stokes operators, and scalar FP64 operators with affine
- *     or stored geometry and kappa = 1 (setting kappa returns the operator to
- *     DG_VARIANT_THREE_KERNEL); the
+ *     use of the variant. FP64 Stokes operators and FP64 scalar operators (any
+ *     geometry and kappa; with recomputed geometry, and for dg_apply_adjoint and
+ *     dg_apply_semilinear, the adjoint kernels run in double-float too); the
  *     result agrees with the FP64 variant to a few 1e-14 relative. Never chosen by
  *     DG_VARIANT_AUTO; dg_operator_autotune keeps it and tunes its blockings.
  *   DG_VARIANT_AUTO: cellwise for FP32 affine scalar operators of degree k <= 2, fused

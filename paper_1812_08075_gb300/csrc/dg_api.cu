@@ -136,8 +136,8 @@ static ScalarArgs<T> scalar_args(const dg_operator *o, bool transpose) {
   a.verts = o->d_verts;
   a.gamma_face = o->d_gamma;
   a.c = o->c;
-  a.kappa_vol = (const T *)o->kappa_vol;
-  a.kappa_face = (const T *)o->kappa_face;
+  a.kappa_vol = (const io_t<T> *)o->kappa_vol;
+  a.kappa_face = (const io_t<T> *)o->kappa_face;
   a.dmask = o->dmask;
   a.sc = (T)(transpose ? o->theta : -1.0);
   a.ss = (T)(transpose ? -1.0 : o->theta);
@@ -160,12 +160,19 @@ static bool fused_ok(const dg_operator *o) {
 
 static bool cellwise_ok(const dg_operator *o) { return fused_ok(o) && o->p <= 3; }
 
-// double-float three-kernel apply: FP64 scalar operators with affine or stored geometry
-// and kappa = 1 (setting kappa returns the operator to the FP64 three-kernel variant),
-// and FP64 Stokes operators
+// double-float kernels: FP64 scalar operators (any geometry, kappa; recomputed geometry
+// and the adjoint run through the double-float adjoint kernels) and FP64 Stokes operators
 static bool df64_ok(const dg_operator *o) {
-  return o->precision == DG_FP64 && !o->aniso && o->kappa_vol == nullptr &&
-         (o->geo == GEO_AFFINE || o->geo == GEO_STORED);
+  return o->precision == DG_FP64 && !o->aniso && (o->problem == DG_SCALAR || o->geo == GEO_AFFINE);
+}
+
+// Kernel arguments of the double-float variant: its tables and stored geometry.
+static ScalarArgs<df64> df64_args(const dg_operator *op, bool transpose) {
+  ScalarArgs<df64> a = scalar_args<df64>(op, transpose);
+  a.tab = (const DevTables<df64> *)op->d_tab_df;
+  a.gvol = (const df64 *)op->d_gvol_df;
+  a.gface = (const df64 *)op->d_gface_df;
+  return a;
 }
 
 // Tables and stored geometry of the operator as double-float (DG_VARIANT_DF64), converted
@@ -461,9 +468,7 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   if (op->problem == DG_STOKES) {
     const int64_t sdof = op->ndofs, srv = op->ncell * 4 * M3, str = op->ncell * 42 * M2;
     if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
-      ScalarArgs<df64> a = scalar_args<df64>(op, transpose);
-      a.tab = (const DevTables<df64> *)op->d_tab_df;
-      e = launch_stokes_apply<df64>(op->p, a, df64(op->mu), (const double *)x, (double *)y, (df64 *)op->d_rvol,
+      e = launch_stokes_apply<df64>(op->p, df64_args(op, transpose), df64(op->mu), (const double *)x, (double *)y, (df64 *)op->d_rvol,
                                     (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s,
                                     ev);
       if (e != cudaSuccess) return fail(DG_ERR_CUDA);
@@ -496,8 +501,18 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   const int64_t sdof = op->ndofs, srv = op->ncell * M3, str = op->ncell * 12 * M2;
   const bool kap = op->kappa_vol != nullptr;
   if (op->geo == GEO_RECOMPUTE) {  // geometry from the vertices, in the adjoint kernels with forward coefficients
+    if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
+      for (int r = 0; r < nrhs; ++r) {
+        e = launch_scalar_adjoint<df64>(op->p, GEO_RECOMPUTE, kap, df64_args(op, transpose), op->theta,
+                                        (const double *)x + r * sdof, nullptr, (double *)y + r * sdof, nullptr,
+                                        nullptr, (df64 *)op->d_rvol, (df64 *)op->d_tr, nullptr, (df64 *)op->d_fres,
+                                        op->cpb, op->fpb, s, r == 0 ? ev : nullptr);
+        if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+      }
+      return DG_OK;
+    }
     for (int r = 0; r < nrhs; ++r) {
-      e = launch_scalar_adjoint(op->p, GEO_RECOMPUTE, kap, scalar_args<double>(op, transpose), op->theta,
+      e = launch_scalar_adjoint<double>(op->p, GEO_RECOMPUTE, kap, scalar_args<double>(op, transpose), op->theta,
                                 (const double *)x + r * sdof, nullptr, (double *)y + r * sdof, nullptr, nullptr,
                                 (double *)op->d_rvol, (double *)op->d_tr, nullptr, (double *)op->d_fres, op->cpb,
                                 op->fpb, s, r == 0 ? ev : nullptr);
@@ -506,11 +521,8 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
     return DG_OK;
   }
   if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
-    ScalarArgs<df64> a = scalar_args<df64>(op, transpose);
-    a.tab = (const DevTables<df64> *)op->d_tab_df;
-    a.gvol = (const df64 *)op->d_gvol_df;
-    a.gface = (const df64 *)op->d_gface_df;
-    e = launch_scalar_apply<df64>(op->p, op->m, op->geo, false, a, (const double *)x, (double *)y, (df64 *)op->d_rvol,
+    e = launch_scalar_apply<df64>(op->p, op->m, op->geo, kap, df64_args(op, transpose), (const double *)x, (double *)y,
+                                  (df64 *)op->d_rvol,
                                   (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s, ev);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;
@@ -610,7 +622,15 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   }
   const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
   const cudaEvent_t *ev = next_events(op);
-  cudaError_t e = launch_scalar_adjoint(op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, true), op->theta,
+  if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
+    const cudaError_t e = launch_scalar_adjoint<df64>(
+        op->p, geo, op->kappa_vol != nullptr, df64_args(op, true), op->theta, (const double *)r,
+        dkappa_vol ? (const double *)x : nullptr, (double *)y, (double *)dkappa_vol, (double *)dkappa_face,
+        (df64 *)op->d_rvol, (df64 *)op->d_tr, (df64 *)op->d_tr2, (df64 *)op->d_fres, op->cpb, op->fpb,
+        (cudaStream_t)stream, ev);
+    return e == cudaSuccess ? DG_OK : fail(DG_ERR_CUDA);
+  }
+  cudaError_t e = launch_scalar_adjoint<double>(op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, true), op->theta,
                                         (const double *)r, dkappa_vol ? (const double *)x : nullptr, (double *)y,
                                         (double *)dkappa_vol, (double *)dkappa_face, (double *)op->d_rvol,
                                         (double *)op->d_tr, (double *)op->d_tr2, (double *)op->d_fres, op->cpb,
@@ -630,7 +650,15 @@ dg_status dg_apply_semilinear(const dg_operator *op_c, int mode, double beta, co
   if (op->problem != DG_SCALAR || op->precision != DG_FP64 || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
   const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
   const cudaEvent_t *ev = next_events(op);
-  cudaError_t e = launch_scalar_adjoint(
+  if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
+    const cudaError_t e = launch_scalar_adjoint<df64>(
+        op->p, geo, op->kappa_vol != nullptr, df64_args(op, false), op->theta, (const double *)w,
+        mode == DG_SEMILINEAR_JACOBIAN ? (const double *)u0 : nullptr, (double *)y, nullptr, nullptr,
+        (df64 *)op->d_rvol, (df64 *)op->d_tr, nullptr, (df64 *)op->d_fres, op->cpb, op->fpb, (cudaStream_t)stream,
+        ev, mode == DG_SEMILINEAR_JACOBIAN ? 2 : 1, beta);
+    return e == cudaSuccess ? DG_OK : fail(DG_ERR_CUDA);
+  }
+  cudaError_t e = launch_scalar_adjoint<double>(
       op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, false), op->theta, (const double *)w,
       mode == DG_SEMILINEAR_JACOBIAN ? (const double *)u0 : nullptr, (double *)y, nullptr, nullptr,
       (double *)op->d_rvol, (double *)op->d_tr, nullptr, (double *)op->d_fres, op->cpb, op->fpb, (cudaStream_t)stream,

@@ -61,6 +61,23 @@ __device__ __forceinline__ df64 fma(const df64 &a, const df64 &b, const df64 &c)
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
+// a / b: the FP32 quotient of the high parts, corrected once by the quotient of the
+// double-float remainder a - q b (Dekker 1971, Sec. 8), about 2^-46 relative.
+__device__ __forceinline__ df64 operator/(const df64 &a, const df64 &b) {
+  const float q = __fdiv_rn(a.hi, b.hi);
+  const df64 r = a - b * df64(q, 0.f);
+  return df_fast_two_sum(q, __fdiv_rn(r.hi, b.hi));
+}
+
+// sqrt(a) for a >= 0: the FP32 root s of the high part and one Newton correction
+// (a - s^2) / (2 s) with the exact square (Karp and Markstein, ACM TOMS 23 (1997)).
+__device__ __forceinline__ df64 sqrt(const df64 &a) {
+  if (!(a.hi > 0.f)) return df64(0.f, 0.f);
+  const float s = __fsqrt_rn(a.hi);
+  const df64 r = a - df64(s, 0.f) * df64(s, 0.f);
+  return df_fast_two_sum(s, __fdiv_rn(r.hi, __fadd_rn(s, s)));
+}
+
 // Accumulator of a contraction sum_j a_j b_j. For double and float it is the plain FMA
 // chain (the same instructions as writing the chain out). For df64 it keeps a running
 // FP32 high sum s, updated by TwoSum with each exact high product, and one FP32 sum c of

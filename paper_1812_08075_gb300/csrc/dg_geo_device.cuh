@@ -41,7 +41,8 @@ __device__ __forceinline__ void trilinear_jacobian(const double V[8][3], double 
 }
 
 // Adjugate (transpose of the cofactor matrix) and determinant: J^-1 = adj / det.
-__device__ __forceinline__ double adjugate(const double J[3][3], double A[3][3]) {
+template <typename T>
+__device__ __forceinline__ T adjugate(const T J[3][3], T A[3][3]) {
   A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
   A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
   A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
@@ -56,12 +57,13 @@ __device__ __forceinline__ double adjugate(const double J[3][3], double A[3][3])
 
 // Area vector of the face xi_a = const of a cell at its point with Jacobian J: the cross
 // product of the tangential columns (t1 < t2), oriented along +xi_a (dir = +1) or -xi_a.
-__device__ __forceinline__ void area_vector(const double J[3][3], int a, int dir, double n[3]) {
+template <typename T>
+__device__ __forceinline__ void area_vector(const T J[3][3], int a, int dir, T n[3]) {
   const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-  const double u0 = J[0][t1], u1 = J[1][t1], u2 = J[2][t1];
-  const double v0 = J[0][t2], v1 = J[1][t2], v2 = J[2][t2];
-  // (a, t1, t2) is an even permutation of (0,1,2) for a = 0, 2 and odd for a = 1
-  const double sg = (a == 1 ? -1.0 : 1.0) * dir;
+  const T u0 = J[0][t1], u1 = J[1][t1], u2 = J[2][t1];
+  const T v0 = J[0][t2], v1 = J[1][t2], v2 = J[2][t2];
+  // (a, t1, t2) is an even permutation of (0,1,2) for a = 0, 2 and odd for a = 1; dir = +-1
+  const T sg = ((a == 1) != (dir < 0)) ? T(-1) : T(1);
   n[0] = sg * (u1 * v2 - u2 * v1);
   n[1] = sg * (u2 * v0 - u0 * v2);
   n[2] = sg * (u0 * v1 - u1 * v0);

@@ -89,8 +89,8 @@ struct ScalarArgs {
   const double *verts;
   const double *gamma_face; // [nface]
   double c;
-  const T *kappa_vol;       // [ncell][m^3] or NULL
-  const T *kappa_face;      // [ncell][6][m^2] or NULL
+  const io_t<T> *kappa_vol;   // [ncell][m^3] or NULL (FP64 for a double-float apply)
+  const io_t<T> *kappa_face;  // [ncell][6][m^2] or NULL
   unsigned dmask;
   T sc, ss;                 // face flux / symmetry coefficients (forward: -1, theta)
 };
@@ -119,11 +119,12 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
 // a.verts (geo = GEO_AFFINE or GEO_RECOMPUTE).
 // nlmode 1 / 2 (with forward coefficients): the semilinear reaction's residual term
 // beta (r^3, v) / Jacobian term 3 beta (x^2 r, v) added to the volume integral.
-cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<double> &a, double theta,
-                                  const double *r, const double *x, double *y, double *dk_vol,
-                                  double *dk_face, double *rvol, double *tr_r, double *tr_x,
-                                  double *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
-                                  int nlmode = 0, double beta = 0.0);
+// T = double, or df64 (double-float arithmetic with FP64 vectors, kappa and dkappa).
+template <typename T>
+cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<T> &a, double theta,
+                                  const io_t<T> *r, const io_t<T> *x, io_t<T> *y, io_t<T> *dk_vol,
+                                  io_t<T> *dk_face, T *rvol, T *tr_r, T *tr_x, T *fres, int cpb, int fpb,
+                                  cudaStream_t s, const cudaEvent_t *ev, int nlmode = 0, double beta = 0.0);
 
 // Persistent single-pass apply for affine meshes (dg_fused.cu): one launch of one wave of
 // blocks that loop over (right-hand side, row of cells) work items; each cell gathers its

@@ -154,14 +154,14 @@ __global__ void __launch_bounds__(256) k_cell(const ScalarArgs<T> a, const io_t<
     T f0, f1, f2;
     if (GEO == GEO_AFFINE) {
       T W = tb.w[q0] * tb.w[q1] * tb.w[q2];
-      if (KAPPA) W *= a.kappa_vol[(c0 + c) * M3 + q];
+      if (KAPPA) W *= io_in<T>(a.kappa_vol[(c0 + c) * M3 + q]);
       f0 = (W * a.vol_g[0]) * g0;
       f1 = (W * a.vol_g[1]) * g1;
       f2 = (W * a.vol_g[2]) * g2;
     } else {
       const T *G = a.gvol + (c0 + c) * (7 * M3) + q;
       if (KAPPA) {
-        const T kq = a.kappa_vol[(c0 + c) * M3 + q];
+        const T kq = io_in<T>(a.kappa_vol[(c0 + c) * M3 + q]);
         g0 *= kq; g1 *= kq; g2 *= kq;
       }
       const T G00 = G[0], G01 = G[M3], G02 = G[2 * M3], G11 = G[3 * M3], G12 = G[4 * M3], G22 = G[5 * M3];
@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
         const T dp = traces[tr_idx<M>(F.cp, 2 * ax, 1, qf)];
         T km = T(1), kp = T(1);
         if (KAPPA) {
-          km = a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf];
-          kp = a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf];
+          km = io_in<T>(a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf]);
+          kp = io_in<T>(a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf]);
         }
         const T J = um - up;
         const T flux = half * bW * fma(km, dm, kp * dp);
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
         if ((a.dmask >> lf) & 1u) {
           const T u = traces[tr_idx<M>(cb, lf, 0, qf)];
           const T d = traces[tr_idx<M>(cb, lf, 1, qf)];
-          const T kb = KAPPA ? a.kappa_face[(cb * 6 + lf) * M2 + qf] : T(1);
+          const T kb = KAPPA ? io_in<T>(a.kappa_face[(cb * 6 + lf) * M2 + qf]) : T(1);
           const T b = side ? bW : -bW;  // outward normal
           Rv = fma(sc * kb, b * d, pw * u);
           Rn = ss * kb * u * b;
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
       const T gp = pacc.get();
       T km = T(1), kp = T(1);
       if (KAPPA) {
-        km = a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf];
-        kp = a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf];
+        km = io_in<T>(a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf]);
+        kp = io_in<T>(a.kappa_face[(F.cp * 6 + 2 * ax) * M2 + qf]);
       }
       const T J = u0[qf] - u1[qf];
       const T flux = half * fma(km, gm, kp * gp);
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
       const int lf = 2 * ax + side;
       T Rv = T(0), s1 = T(0), s2 = T(0), sn = T(0);
       if ((a.dmask >> lf) & 1u) {
-        const T kb = KAPPA ? a.kappa_face[(cb * 6 + lf) * M2 + qf] : T(1);
+        const T kb = KAPPA ? io_in<T>(a.kappa_face[(cb * 6 + lf) * M2 + qf]) : T(1);
         const T u = u0[qf];
         Rv = fma(sc * kb, gm, pw * u);
         const T su = ss * kb * u;

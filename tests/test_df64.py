@@ -147,16 +147,90 @@ def test_df64_stokes_agrees_with_fp64_variant():
     assert err <= TOL_DF_VS_FP64
 
 
+def kappa_setup(n, k, geom, theta=-1.0, mask=0b111111, geometry=None):
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    kw = {} if geometry is None else {"geometry": geometry}
+    op = dg.Operator(dg.Mesh(*n, verts), k, theta=theta, dirichlet_mask=mask, **kw)
+    orc = oracle.Problem(*n, k, vertices=verts, theta=theta, dirichlet_mask=mask)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    orc.kappa_vol, orc.kappa_face = kv, kf
+    op._kappa = (torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    op.set_kappa(*op._kappa)
+    op.set_variant(dg.DG_VARIANT_DF64)
+    assert op.stats().variant == dg.DG_VARIANT_DF64
+    return op, orc, kv, kf
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+@pytest.mark.parametrize("geometry", [dg.DG_GEOM_STORED, dg.DG_GEOM_RECOMPUTE])
+def test_df64_kappa_and_recomputed_geometry_match_oracle(k, geometry):
+    n = (4, 3, 5)
+    op, orc, _, _ = kappa_setup(n, k, "trilinear", geometry=geometry)
+    x = wl.uniform_vector(op.ndofs, 5)
+    err = relerr(op.apply(torch.from_numpy(x).cuda()).cpu().numpy(), orc.apply(x))
+    print(f"df64 Q{k} trilinear, kappa, geometry {geometry}: rel err {err:.2e}")
+    assert err <= TOL64
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+@pytest.mark.parametrize("theta", [-1.0, 1.0])
+def test_df64_adjoint_and_dkappa_match_oracle(k, geom, theta):
+    # y = A^T r and r^T dA/dkappa_q x at every volume and face point, double-float kernels
+    n = (4, 3, 5)
+    op, orc, kv, kf = kappa_setup(n, k, geom, theta=theta, mask=0b101111)
+    x, r = wl.uniform_vector(op.ndofs, 3), wl.uniform_vector(op.ndofs, 4)
+    xd, rd = torch.from_numpy(x).cuda(), torch.from_numpy(r).cuda()
+    y = torch.empty_like(xd)
+    dkv = torch.empty(kv.size, dtype=torch.float64, device="cuda")
+    dkf = torch.empty(kf.size, dtype=torch.float64, device="cuda")
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+    torch.cuda.synchronize()
+    rv, rf = orc.dkappa(x, r)
+    errs = (relerr(y.cpu().numpy(), orc.apply(r, transpose=True)), relerr(dkv.cpu().numpy(), rv),
+            relerr(dkf.cpu().numpy(), rf))
+    print(f"df64 adjoint Q{k} {geom} theta {theta}: A^T r {errs[0]:.2e}, dkappa vol {errs[1]:.2e}, face {errs[2]:.2e}")
+    assert max(errs) <= TOL64
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_df64_semilinear_matches_oracle(k):
+    n = (4, 3, 5)
+    op, orc, _, _ = kappa_setup(n, k, "trilinear")
+    w, u0 = wl.uniform_vector(op.ndofs, 0), wl.uniform_vector(op.ndofs, 1)
+    wd, ud = torch.from_numpy(w).cuda(), torch.from_numpy(u0).cuda()
+    er = relerr(op.semilinear(wd, 2.5).cpu().numpy(), orc.semilinear(w, 2.5))
+    ej = relerr(op.semilinear(wd, 2.5, u0=ud).cpu().numpy(), orc.semilinear(w, 2.5, u0=u0))
+    print(f"df64 semilinear Q{k}: residual {er:.2e}, Jacobian {ej:.2e}")
+    assert er <= TOL64 and ej <= TOL64
+
+
+def test_df64_adjoint_agrees_with_fp64_at_config5_scale():
+    # 32^3 trilinear Q3 with log-normal kappa: A^T r and dkappa of both variants
+    n, k = (32, 32, 32), 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    tk = (torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    op.set_kappa(*tk)
+    x = torch.from_numpy(wl.uniform_vector(op.ndofs, 3)).cuda()
+    r = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
+    out = {}
+    for v in (dg.DG_VARIANT_THREE_KERNEL, dg.DG_VARIANT_DF64):
+        op.set_variant(v)
+        y = torch.empty_like(x)
+        dkv, dkf = torch.empty_like(tk[0]), torch.empty_like(tk[1])
+        dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+        out[v] = (y, dkv, dkf)
+    a, b = out[dg.DG_VARIANT_THREE_KERNEL], out[dg.DG_VARIANT_DF64]
+    errs = [float((q - p).abs().max() / p.abs().max()) for p, q in zip(a, b)]
+    print(f"df64 vs FP64 adjoint at 32^3 Q3: y {errs[0]:.2e}, dkappa vol {errs[1]:.2e}, face {errs[2]:.2e}")
+    assert max(errs) <= TOL_DF_VS_FP64
+
+
 def test_df64_where_it_does_not_apply():
     for op in (dg.Operator(dg.Mesh(3, 3, 3), 2, precision=dg.DG_FP32),
-               dg.Operator(dg.Mesh(3, 3, 3), 3, problem=dg.DG_STOKES, precision=dg.DG_FP32),
-               dg.Operator(dg.Mesh(3, 3, 3, wl.perturbed_vertices(3, 3, 3)), 2, geometry=dg.DG_GEOM_RECOMPUTE)):
+               dg.Operator(dg.Mesh(3, 3, 3), 3, problem=dg.DG_STOKES, precision=dg.DG_FP32)):
         with pytest.raises(dg.DGError) as e:
             op.set_variant(dg.DG_VARIANT_DF64)
         assert e.value.status == dg.DG_ERR_UNSUPPORTED
-    # kappa returns the operator to the FP64 three-kernel variant
-    op, _ = df_operator((4, 4, 4), 2, "trilinear")
-    kv, kf = wl.lognormal_kappa(op.mesh.ncell, 3, seed=2)
-    op._kappa = (torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
-    op.set_kappa(*op._kappa)
-    assert op.stats().variant == dg.DG_VARIANT_THREE_KERNEL
