@@ -312,9 +312,19 @@ def adjoint_apply(n_cells=64, k=3):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_adj = e0.elapsed_time(e1) / 20
+    # the same adjoint in double-float arithmetic (DG_VARIANT_DF64)
+    ref = (y.clone(), gv.clone(), gf.clone())
+    op.set_variant(dg.DG_VARIANT_DF64)
+    adj = lambda: dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(),  # noqa: E731
+                                      gf.data_ptr(), stream.cuda_stream)
+    ms_adj_df = event_ms(adj)
+    diffs = [float((q - p).abs().max() / p.abs().max()) for p, q in zip(ref, (y, gv, gf))]
+    ms_fwd_df, _, _ = time_applies(op, x, y, 20, 3, None, profile=False)
     return {"workload": f"{n_cells}^3 trilinear cells, Q{k}, log-normal kappa at every point, FP64",
             "ndofs": op.ndofs, "forward_ms": ms_fwd, "adjoint_ms": ms_adj,
-            "adjoint_dof_s": op.ndofs / (ms_adj * 1e-3), "geometry": "recomputed in the adjoint kernels"}
+            "adjoint_dof_s": op.ndofs / (ms_adj * 1e-3), "geometry": "recomputed in the adjoint kernels",
+            "df64": {"forward_ms": ms_fwd_df, "adjoint_ms": ms_adj_df, "speedup_adjoint": ms_adj / ms_adj_df,
+                     "rel_diff_vs_fp64": {"y": diffs[0], "dkappa_vol": diffs[1], "dkappa_face": diffs[2]}}}
 
 
 def event_ms(fn, reps=20, warm=3):
