@@ -35,6 +35,17 @@ def test_library_exports_every_declared_symbol():
     assert sorted(dg.EXPORTED) == names
 
 
+def test_binding_constants_match_the_header_enums():
+    # every DG_* enumerator of include/dg.h has the same value in the Python binding
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dg.h")).read(), flags=re.S)
+    found = 0
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for name, val in re.findall(r"\b(DG_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            assert getattr(dg, name) == int(val), name
+            found += 1
+    assert found >= 20 and dg.DG_VARIANT_DF64 == 4
+
+
 def test_status_strings_and_argument_errors_without_gpu():
     assert dg.status_string(dg.DG_OK) == "DG_OK"
     assert dg.status_string(dg.DG_ERR_UNSUPPORTED) == "DG_ERR_UNSUPPORTED"
