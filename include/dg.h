@@ -252,7 +252,11 @@ dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void
 
 /* Same operator applied through host buffers: copies x (host [nrhs][ndofs]) to the
  * device, applies, copies y back and synchronises the stream. Page-locked host memory
- * gives the full link bandwidth; pageable memory also works. */
+ * gives the full link bandwidth; pageable memory also works. For the three-kernel scalar
+ * apply (FP64, FP32 or double-float; affine or stored geometry) the call pipelines over
+ * eight chunks of cells: each chunk's x is copied ahead of its cell kernel and its y
+ * behind its back-projection kernel, on an internal copy stream ordered by events, so
+ * the copies overlap the kernels. The result is the same as dg_apply's. */
 dg_status dg_apply_host(const dg_operator *op, const void *x_host, void *y_host, int nrhs,
                         void *stream);
 

@@ -87,6 +87,8 @@ static void free_op(dg_operator *o) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : o->hs_ev) cudaEventDestroy(e);
+  if (o->hs_copy) cudaStreamDestroy(o->hs_copy);
   dg_solver_release(o);
   delete o;
 }
@@ -576,6 +578,91 @@ dg_status dg_apply(const dg_operator *op, const void *x, void *y, int nrhs, void
   return apply_impl(op, x, y, nrhs, (cudaStream_t)stream, false);
 }
 
+}  // extern "C"
+
+// dg_apply_host pipelined over chunks of cells for the three-kernel scalar apply: the cell
+// kernel of a chunk needs only that chunk's x, and the back-projection kernel of a chunk
+// produces that chunk's y, so host-to-device copies run ahead of the cell kernels and
+// device-to-host copies behind the back-projection kernels, on a copy stream ordered by
+// events; the face kernel runs between the two loops.
+static bool host_pipeline_ok(const dg_operator *o) {
+  return o->problem == DG_SCALAR && !o->aniso && (o->geo == GEO_AFFINE || o->geo == GEO_STORED) &&
+         (o->variant == DG_VARIANT_THREE_KERNEL || (o->variant == DG_VARIANT_DF64 && df64_ok(o)));
+}
+
+static constexpr int kHostChunks = 8;
+
+static dg_status apply_host_pipelined(dg_operator *op, const void *x_host, void *y_host, int nrhs, cudaStream_t s) {
+  const size_t es = op->precision == DG_FP64 ? sizeof(double) : sizeof(float);
+  if (!op->hs_copy) {
+    if (cudaStreamCreateWithFlags(&op->hs_copy, cudaStreamNonBlocking) != cudaSuccess) {
+      op->hs_copy = nullptr;
+      return fail(DG_ERR_CUDA);
+    }
+    while (op->hs_ev.size() < 2 * kHostChunks + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(DG_ERR_CUDA);
+      op->hs_ev.push_back(e);
+    }
+  }
+  const int M = op->m, M2 = M * M, M3 = M2 * M;
+  const int64_t P3 = (int64_t)op->p * op->p * op->p, ncell = op->ncell, sdof = op->ndofs;
+  const int64_t srv = ncell * M3, str = ncell * 12 * M2;
+  const int nch = (int)std::min<int64_t>(kHostChunks, ncell);
+  const size_t pitch = (size_t)sdof * es;
+  cudaStream_t cs = op->hs_copy;
+  cudaEvent_t *ev = op->hs_ev.data();
+  const bool kap = op->kappa_vol != nullptr;
+  auto phase = [&](int ph, int64_t cb, int64_t cn) -> cudaError_t {
+    if (op->variant == DG_VARIANT_DF64)
+      return launch_scalar_apply<df64>(op->p, M, op->geo, kap, df64_args(op, false), (const double *)op->d_xh,
+                                       (double *)op->d_yh, (df64 *)op->d_rvol, (df64 *)op->d_tr, (df64 *)op->d_fres,
+                                       nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn);
+    if (op->precision == DG_FP64)
+      return launch_scalar_apply<double>(op->p, M, op->geo, kap, scalar_args<double>(op, false),
+                                         (const double *)op->d_xh, (double *)op->d_yh, (double *)op->d_rvol,
+                                         (double *)op->d_tr, (double *)op->d_fres, nrhs, sdof, srv, str, op->cpb,
+                                         op->fpb, s, nullptr, nullptr, ph, cb, cn);
+    return launch_scalar_apply<float>(op->p, M, op->geo, kap, scalar_args<float>(op, false), (const float *)op->d_xh,
+                                      (float *)op->d_yh, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres,
+                                      nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn);
+  };
+  auto chunk = [&](int k, int64_t *cb, int64_t *cn) {
+    *cb = ncell * k / nch;
+    *cn = ncell * (k + 1) / nch - *cb;
+  };
+  // the copies into the staging buffers wait for earlier work on s that may still use them
+  CK(cudaEventRecord(ev[2 * kHostChunks], s));
+  CK(cudaStreamWaitEvent(cs, ev[2 * kHostChunks], 0));
+  for (int k = 0; k < nch; ++k) {
+    int64_t cb, cn;
+    chunk(k, &cb, &cn);
+    const size_t off = (size_t)(cb * P3) * es;
+    CK(cudaMemcpy2DAsync((char *)op->d_xh + off, pitch, (const char *)x_host + off, pitch, (size_t)(cn * P3) * es,
+                         nrhs, cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(ev[k], cs));
+    CK(cudaStreamWaitEvent(s, ev[k], 0));
+    CK(phase(1, cb, cn));
+  }
+  CK(phase(2, 0, ncell));
+  for (int k = 0; k < nch; ++k) {
+    int64_t cb, cn;
+    chunk(k, &cb, &cn);
+    CK(phase(4, cb, cn));
+    CK(cudaEventRecord(ev[kHostChunks + k], s));
+    CK(cudaStreamWaitEvent(cs, ev[kHostChunks + k], 0));
+    const size_t off = (size_t)(cb * P3) * es;
+    CK(cudaMemcpy2DAsync((char *)y_host + off, pitch, (const char *)op->d_yh + off, pitch, (size_t)(cn * P3) * es,
+                         nrhs, cudaMemcpyDeviceToHost, cs));
+  }
+  CK(cudaEventRecord(ev[2 * kHostChunks + 1], cs));
+  CK(cudaStreamWaitEvent(s, ev[2 * kHostChunks + 1], 0));
+  CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+extern "C" {
+
 dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_host, int nrhs, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (!op || !x_host || !y_host) return fail(DG_ERR_INVALID_ARG);
@@ -590,6 +677,7 @@ dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_hos
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (host_pipeline_ok(op)) return apply_host_pipelined(op, x_host, y_host, nrhs, s);
   CK(cudaMemcpyAsync(op->d_xh, x_host, bytes, cudaMemcpyHostToDevice, s));
   dg_status st = apply_impl(op, op->d_xh, op->d_yh, nrhs, s, false);
   if (st != DG_OK) return st;

@@ -111,7 +111,8 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
                                 const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres, int nrhs,
                                 int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
-                                LaunchInfo *query = nullptr);
+                                LaunchInfo *query = nullptr, int phases = 7, int64_t cell_begin = 0,
+                                int64_t cell_count = -1);
 
 // Adjoint of the scalar operator (dg_adjoint.cu, FP64): y = A^T r with a.sc/a.ss set for
 // the transpose, and, when x is non-NULL, dkappa at every volume and face point for the
@@ -239,6 +240,8 @@ struct dg_operator {
   void *d_gvol = nullptr, *d_gface = nullptr;
   void *d_rvol = nullptr, *d_tr = nullptr, *d_fres = nullptr;
   void *d_xh = nullptr, *d_yh = nullptr;  // staging for dg_apply_host
+  cudaStream_t hs_copy = nullptr;         // dg_apply_host: copy stream and its events (first use)
+  std::vector<cudaEvent_t> hs_ev;
   void *d_tr2 = nullptr;                  // traces of x in the adjoint (allocated on first use)
   const void *kappa_vol = nullptr, *kappa_face = nullptr;
   int cpb = 1, fpb = 1;

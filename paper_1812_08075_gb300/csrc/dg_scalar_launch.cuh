@@ -28,12 +28,28 @@ static cudaError_t query_launch(Kern k, dim3 grid, int threads, size_t sm, Launc
   return cudaSuccess;
 }
 
+// Cells [cb, cb + cn) of the cell-side kernels as a launch of their own: the arguments with
+// every per-cell array offset to cb and ncell = cn.
+template <int P, int M, typename T>
+static ScalarArgs<T> cell_range(const ScalarArgs<T> &a, int64_t cb, int64_t cn) {
+  ScalarArgs<T> r = a;
+  r.ncell = cn;
+  if (r.gvol) r.gvol += cb * 7 * M * M * M;
+  if (r.kappa_vol) r.kappa_vol += cb * M * M * M;
+  return r;
+}
+
+// phases: bit 0 the cell kernel, bit 1 the face kernel, bit 2 the back-projection kernel;
+// the cell-side kernels take cells [cb, cb + cn) (cn < 0: all cells).
 template <int P, int M, typename T, int GEO, bool KAPPA>
 static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres,
                              int nrhs, int64_t sdof, int64_t srv, int64_t str, int cpb, int fpb,
-                             cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q) {
-  constexpr int M2 = M * M, M3 = M * M * M;
+                             cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q, int phases = 7, int64_t cb = 0,
+                             int64_t cn = -1) {
+  constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   cudaError_t e;
+  if (cn < 0) { cb = 0; cn = a.ncell; }
+  const ScalarArgs<T> ac = cell_range<P, M, T>(a, cb, cn);
   if (q) {
     const dim3 gc((unsigned)((a.ncell + cpb - 1) / cpb), nrhs), gf((unsigned)((a.nface + fpb - 1) / fpb), nrhs);
     const size_t s0 = cell_smem_bytes<P, M, T>(cpb), s2 = back_smem_bytes<P, M, T>(cpb);
@@ -45,16 +61,17 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *
     if ((e = query_launch(k_face<M, T, GEO, KAPPA>, gf, threads_for(fpb * M2), s1, q + 1)) != cudaSuccess) return e;
     return query_launch(k_back<P, M, T>, gc, threads_for(cpb * M3), s2, q + 2);
   }
-  {
+  if ((phases & 1) && cn > 0) {
     size_t sm = cell_smem_bytes<P, M, T>(cpb);
     auto k = k_cell<P, M, T, GEO, KAPPA>;
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-    dim3 grid((unsigned)((a.ncell + cpb - 1) / cpb), nrhs);
+    dim3 grid((unsigned)((cn + cpb - 1) / cpb), nrhs);
     if (ev) cudaEventRecord(ev[0], s);
-    k<<<grid, threads_for(cpb * M3), sm, s>>>(a, x, rvol, traces, cpb, sdof, srv, str);
+    k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, x + cb * P3, rvol + cb * M3, traces + cb * 12 * M2, cpb, sdof, srv,
+                                              str);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  {
+  if (phases & 2) {
     size_t sm = face_smem_bytes<M, T>(fpb, GEO == GEO_AFFINE ? GEO_AFFINE : GEO_STORED);
     auto k = k_face<M, T, GEO, KAPPA>;
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
@@ -63,13 +80,14 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *
     k<<<grid, threads_for(fpb * M2), sm, s>>>(a, traces, fres, fpb, str);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  {
+  if ((phases & 4) && cn > 0) {
     size_t sm = back_smem_bytes<P, M, T>(cpb);
     auto k = k_back<P, M, T>;
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-    dim3 grid((unsigned)((a.ncell + cpb - 1) / cpb), nrhs);
+    dim3 grid((unsigned)((cn + cpb - 1) / cpb), nrhs);
     if (ev) cudaEventRecord(ev[2], s);
-    k<<<grid, threads_for(cpb * M3), sm, s>>>(a, rvol, fres, y, cpb, sdof, srv, str);
+    k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, rvol + cb * M3, fres + cb * 12 * M2, y + cb * P3, cpb, sdof, srv,
+                                              str);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], s);
   }
@@ -79,15 +97,19 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *
 template <int P, int M, typename T>
 static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol,
                            T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
-                           int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q) {
+                           int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q, int ph,
+                           int64_t cb, int64_t cn) {
+#define DGK_PMK(G, K) \
+  return apply_pmk<P, M, T, G, K>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q, ph, cb, cn)
   if (geo == GEO_AFFINE) {
-    if (kappa) return apply_pmk<P, M, T, GEO_AFFINE, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q);
-    return apply_pmk<P, M, T, GEO_AFFINE, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q);
+    if (kappa) DGK_PMK(GEO_AFFINE, true);
+    DGK_PMK(GEO_AFFINE, false);
   }
   if (geo == GEO_STORED) {
-    if (kappa) return apply_pmk<P, M, T, GEO_STORED, true>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q);
-    return apply_pmk<P, M, T, GEO_STORED, false>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q);
+    if (kappa) DGK_PMK(GEO_STORED, true);
+    DGK_PMK(GEO_STORED, false);
   }
+#undef DGK_PMK
   return cudaErrorInvalidValue;
 }
 
@@ -97,11 +119,12 @@ template <typename T>
 cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y,
                                 T *rvol, T *traces, T *fres, int nrhs, int64_t stride_dofs,
                                 int64_t stride_rvol, int64_t stride_tr, int cpb, int fpb, cudaStream_t s,
-                                const cudaEvent_t *ev, LaunchInfo *query) {
+                                const cudaEvent_t *ev, LaunchInfo *query, int phases, int64_t cell_begin,
+                                int64_t cell_count) {
 #define DGK_CASE(PP, MM)                                                                                      \
   if (p == PP && m == MM)                                                                                     \
     return dgk::apply_p<PP, MM, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, \
-                                   stride_tr, cpb, fpb, s, ev, query);
+                                   stride_tr, cpb, fpb, s, ev, query, phases, cell_begin, cell_count);
   DGK_CASE(2, 2) DGK_CASE(3, 3) DGK_CASE(4, 4) DGK_CASE(5, 5) DGK_CASE(6, 6)
   DGK_CASE(2, 3) DGK_CASE(3, 4) DGK_CASE(4, 5) DGK_CASE(5, 6) DGK_CASE(6, 7)
 #undef DGK_CASE

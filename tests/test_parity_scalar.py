@@ -95,15 +95,32 @@ def test_fp32_against_fp64_oracle(k, geom):
     assert err <= TOL32
 
 
-def test_apply_host_matches_device():
-    n, k = (4, 4, 3), 3
-    verts = wl.perturbed_vertices(*n, seed=1)
-    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=2)
-    x = np.stack([wl.uniform_vector(op.ndofs, s) for s in (0, 1)])
-    yh = np.zeros_like(x)
-    op.apply_host(x, yh)
-    yd = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert np.array_equal(yh, yd)
+@pytest.mark.parametrize("case", ["fp64_q3_2rhs", "fp64_4cells", "fp64_kappa_3rhs", "fp32_three_kernel",
+                                  "df64_q3", "fp32_fused_unpipelined"])
+def test_apply_host_matches_device(case):
+    # dg_apply_host runs the three-kernel apply in chunks of cells with the copies overlapped
+    # (one chunk per cell when there are fewer cells than chunks); other variants copy, apply
+    # and copy back. Either way the result is the device apply's, bit for bit.
+    cfg = {"fp64_q3_2rhs": ((4, 4, 3), 3, dg.DG_FP64, 2, True, False, None),
+           "fp64_4cells": ((2, 2, 1), 2, dg.DG_FP64, 1, True, False, None),
+           "fp64_kappa_3rhs": ((9, 7, 5), 2, dg.DG_FP64, 3, True, True, None),
+           "fp32_three_kernel": ((7, 6, 5), 2, dg.DG_FP32, 3, True, False, None),
+           "df64_q3": ((6, 5, 4), 3, dg.DG_FP64, 2, True, False, dg.DG_VARIANT_DF64),
+           "fp32_fused_unpipelined": ((6, 5, 4), 3, dg.DG_FP32, 2, False, False, dg.DG_VARIANT_FUSED)}[case]
+    n, k, prec, nrhs, curved, kappa, variant = cfg
+    verts = wl.perturbed_vertices(*n, seed=1) if curved else None
+    op = dg.Operator(dg.Mesh(*n, verts), k, precision=prec, max_rhs=nrhs)
+    if kappa:
+        kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+        op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    if variant is not None:
+        op.set_variant(variant)
+    dt = np.float64 if prec == dg.DG_FP64 else np.float32
+    x = np.stack([wl.uniform_vector(op.ndofs, s) for s in range(nrhs)]).astype(dt)
+    xh, yh = torch.from_numpy(x).pin_memory(), torch.zeros(x.shape, dtype=torch.from_numpy(x).dtype).pin_memory()
+    op.apply_host(xh if nrhs > 1 else xh[0], yh if nrhs > 1 else yh[0])
+    yd = op.apply(torch.from_numpy(x).cuda() if nrhs > 1 else torch.from_numpy(x[0]).cuda()).cpu().numpy()
+    assert np.array_equal(yh.numpy().reshape(yd.shape), yd)
 
 
 def test_apply_is_deterministic():
