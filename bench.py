@@ -525,6 +525,8 @@ def run_ours(args, rank, world, dist):
         for kk in (1, 2, 3, 4, 5):
             for prec, tag, es in ((dg.DG_FP64, "fp64", 8), (dg.DG_FP32, "fp32", 4)):
                 o = dg.Operator(mesh, kk, precision=prec)
+                if args.autotune:  # the framework's own tuner, as for the headline operator
+                    o.autotune(1)
                 xx = torch.from_numpy(wl.uniform_vector(o.ndofs, 0)).to("cuda", o.dtype)
                 yy = torch.empty_like(xx)
                 ms_k, kt_k, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
@@ -538,10 +540,13 @@ def run_ours(args, rank, world, dist):
                                          "hbm_gbs_model": byt / (ms_k * 1e-3) / 1e9,
                                          "roofline_frac": t_roof / (ms_k * 1e-3),
                                          "bound": "alu" if f / (peak * 1e12) >= byt / (pk["hbm_gbs"] * 1e9) else "hbm",
-                                         "kernel_ms": kt_k}
-                if prec == dg.DG_FP64:  # the same operator in double-float arithmetic, default blocking
+                                         "kernel_ms": kt_k,
+                                         "blocking": [st_k.variant, st_k.cells_per_block, st_k.faces_per_block]}
+                if prec == dg.DG_FP64:  # the same operator in double-float arithmetic, blockings tuned
                     y64 = yy.clone()
                     o.set_variant(dg.DG_VARIANT_DF64)
+                    if args.autotune:
+                        o.autotune(1)
                     ms_d, kt_d, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
                     sweep[f"Q{kk}_df64"] = {"dof_s": o.ndofs / (ms_d * 1e-3), "ms": ms_d,
                                             "fp64_equivalent_tflops": f / (ms_d * 1e-3) / 1e12,
