@@ -525,7 +525,8 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
     e = launch_scalar_apply<df64>(op->p, op->m, op->geo, kap, df64_args(op, transpose), (const double *)x, (double *)y,
                                   (df64 *)op->d_rvol,
-                                  (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s, ev);
+                                  (df64 *)op->d_tr, (df64 *)op->d_fres, nrhs, sdof, srv, str, op->cpb, op->fpb, s, ev,
+                                  nullptr, 7, 0, -1, &op->ht);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;
   }
@@ -556,7 +557,7 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
   else
     e = launch_scalar_apply<float>(op->p, op->m, op->geo, kap, scalar_args<float>(op, transpose), (const float *)x,
                                    (float *)y, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres, nrhs, sdof,
-                                   srv, str, op->cpb, op->fpb, s, ev);
+                                   srv, str, op->cpb, op->fpb, s, ev, nullptr, 7, 0, -1, &op->ht);
   if (e != cudaSuccess) return fail(DG_ERR_CUDA);
   return DG_OK;
 }
@@ -617,7 +618,8 @@ static dg_status apply_host_pipelined(dg_operator *op, const void *x_host, void 
     if (op->variant == DG_VARIANT_DF64)
       return launch_scalar_apply<df64>(op->p, M, op->geo, kap, df64_args(op, false), (const double *)op->d_xh,
                                        (double *)op->d_yh, (df64 *)op->d_rvol, (df64 *)op->d_tr, (df64 *)op->d_fres,
-                                       nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn);
+                                       nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn,
+                                       &op->ht);
     if (op->precision == DG_FP64)
       return launch_scalar_apply<double>(op->p, M, op->geo, kap, scalar_args<double>(op, false),
                                          (const double *)op->d_xh, (double *)op->d_yh, (double *)op->d_rvol,
@@ -625,7 +627,7 @@ static dg_status apply_host_pipelined(dg_operator *op, const void *x_host, void 
                                          op->fpb, s, nullptr, nullptr, ph, cb, cn);
     return launch_scalar_apply<float>(op->p, M, op->geo, kap, scalar_args<float>(op, false), (const float *)op->d_xh,
                                       (float *)op->d_yh, (float *)op->d_rvol, (float *)op->d_tr, (float *)op->d_fres,
-                                      nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn);
+                                      nrhs, sdof, srv, str, op->cpb, op->fpb, s, nullptr, nullptr, ph, cb, cn, &op->ht);
   };
   auto chunk = [&](int k, int64_t *cb, int64_t *cn) {
     *cb = ncell * k / nch;

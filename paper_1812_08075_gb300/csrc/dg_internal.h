@@ -112,7 +112,7 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
                                 int64_t stride_dofs, int64_t stride_rvol, int64_t stride_tr,
                                 int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
                                 LaunchInfo *query = nullptr, int phases = 7, int64_t cell_begin = 0,
-                                int64_t cell_count = -1);
+                                int64_t cell_count = -1, const HostTables *ht = nullptr);
 
 // Adjoint of the scalar operator (dg_adjoint.cu, FP64): y = A^T r with a.sc/a.ss set for
 // the transpose, and, when x is non-NULL, dkappa at every volume and face point for the

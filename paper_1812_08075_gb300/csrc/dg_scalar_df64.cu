@@ -4,7 +4,8 @@
 
 template cudaError_t launch_scalar_apply<df64>(int, int, int, bool, const ScalarArgs<df64> &, const double *, double *,
                                                df64 *, df64 *, df64 *, int, int64_t, int64_t, int64_t, int, int,
-                                               cudaStream_t, const cudaEvent_t *, LaunchInfo *, int, int64_t, int64_t);
+                                               cudaStream_t, const cudaEvent_t *, LaunchInfo *, int, int64_t, int64_t,
+                                               const HostTables *);
 
 namespace {
 __global__ void k_to_df64(const double *__restrict__ in, df64 *__restrict__ out, int64_t n) {

@@ -4,4 +4,5 @@
 template cudaError_t launch_scalar_apply<float>(int, int, int, bool, const ScalarArgs<float> &, const float *,
                                                 float *, float *, float *, float *, int, int64_t, int64_t,
                                                 int64_t, int, int, cudaStream_t,
-                                                 const cudaEvent_t *, LaunchInfo *, int, int64_t, int64_t);
+                                                 const cudaEvent_t *, LaunchInfo *, int, int64_t, int64_t,
+                                               const HostTables *);

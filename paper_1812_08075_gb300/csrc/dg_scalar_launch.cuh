@@ -1,6 +1,8 @@
 // Launchers of the scalar apply kernels; included by one translation unit per precision.
 #pragma once
-#include "dg_scalar_kernels.cuh"
+#include <type_traits>
+
+#include "dg_scalar_lines.cuh"
 
 namespace dgk {
 
@@ -45,7 +47,12 @@ template <int P, int M, typename T, int GEO, bool KAPPA>
 static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol, T *traces, T *fres,
                              int nrhs, int64_t sdof, int64_t srv, int64_t str, int cpb, int fpb,
                              cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q, int phases = 7, int64_t cb = 0,
-                             int64_t cn = -1) {
+                             int64_t cn = -1, const HostTables *ht = nullptr) {
+  // line-per-thread cell and back kernels for FP32 and double-float (same grid, block and
+  // shared memory as the thread-per-point ones); FP64 keeps the thread-per-point kernels
+  const bool lines = ht != nullptr && !std::is_same<T, double>::value;
+  LineTab<P, M, T> lt;
+  if (lines) lt = line_tables<P, M, T>(*ht);
   constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   cudaError_t e;
   if (cn < 0) { cb = 0; cn = a.ncell; }
@@ -67,8 +74,15 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((unsigned)((cn + cpb - 1) / cpb), nrhs);
     if (ev) cudaEventRecord(ev[0], s);
-    k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, x + cb * P3, rvol + cb * M3, traces + cb * 12 * M2, cpb, sdof, srv,
-                                              str);
+    if (lines) {
+      auto kl = k_cell_lines<P, M, T, GEO, KAPPA>;
+      if ((e = set_smem(kl, sm)) != cudaSuccess) return e;
+      kl<<<grid, threads_for(cpb * M3), sm, s>>>(ac, lt, x + cb * P3, rvol + cb * M3, traces + cb * 12 * M2, cpb, sdof,
+                                                 srv, str);
+    } else {
+      k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, x + cb * P3, rvol + cb * M3, traces + cb * 12 * M2, cpb, sdof, srv,
+                                                str);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (phases & 2) {
@@ -86,8 +100,15 @@ static cudaError_t apply_pmk(const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((unsigned)((cn + cpb - 1) / cpb), nrhs);
     if (ev) cudaEventRecord(ev[2], s);
-    k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, rvol + cb * M3, fres + cb * 12 * M2, y + cb * P3, cpb, sdof, srv,
-                                              str);
+    if (lines) {
+      auto kl = k_back_lines<P, M, T>;
+      if ((e = set_smem(kl, sm)) != cudaSuccess) return e;
+      kl<<<grid, threads_for(cpb * M3), sm, s>>>(ac, lt, rvol + cb * M3, fres + cb * 12 * M2, y + cb * P3, cpb, sdof,
+                                                 srv, str);
+    } else {
+      k<<<grid, threads_for(cpb * M3), sm, s>>>(ac, rvol + cb * M3, fres + cb * 12 * M2, y + cb * P3, cpb, sdof, srv,
+                                                str);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], s);
   }
@@ -98,9 +119,9 @@ template <int P, int M, typename T>
 static cudaError_t apply_p(int geo, bool kappa, const ScalarArgs<T> &a, const io_t<T> *x, io_t<T> *y, T *rvol,
                            T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
                            int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, LaunchInfo *q, int ph,
-                           int64_t cb, int64_t cn) {
+                           int64_t cb, int64_t cn, const HostTables *ht) {
 #define DGK_PMK(G, K) \
-  return apply_pmk<P, M, T, G, K>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q, ph, cb, cn)
+  return apply_pmk<P, M, T, G, K>(a, x, y, rvol, traces, fres, nrhs, sdof, srv, str, cpb, fpb, s, ev, q, ph, cb, cn, ht)
   if (geo == GEO_AFFINE) {
     if (kappa) DGK_PMK(GEO_AFFINE, true);
     DGK_PMK(GEO_AFFINE, false);
@@ -120,11 +141,11 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
                                 T *rvol, T *traces, T *fres, int nrhs, int64_t stride_dofs,
                                 int64_t stride_rvol, int64_t stride_tr, int cpb, int fpb, cudaStream_t s,
                                 const cudaEvent_t *ev, LaunchInfo *query, int phases, int64_t cell_begin,
-                                int64_t cell_count) {
+                                int64_t cell_count, const HostTables *ht) {
 #define DGK_CASE(PP, MM)                                                                                      \
   if (p == PP && m == MM)                                                                                     \
     return dgk::apply_p<PP, MM, T>(geo, kappa, a, x, y, rvol, traces, fres, nrhs, stride_dofs, stride_rvol, \
-                                   stride_tr, cpb, fpb, s, ev, query, phases, cell_begin, cell_count);
+                                   stride_tr, cpb, fpb, s, ev, query, phases, cell_begin, cell_count, ht);
   DGK_CASE(2, 2) DGK_CASE(3, 3) DGK_CASE(4, 4) DGK_CASE(5, 5) DGK_CASE(6, 6)
   DGK_CASE(2, 3) DGK_CASE(3, 4) DGK_CASE(4, 5) DGK_CASE(5, 6) DGK_CASE(6, 7)
 #undef DGK_CASE
