@@ -18,7 +18,6 @@ struct LineTab {
   T interp[M * P];  // [q][j]
   T dcol[M * M];    // [q][r]
   T e0[M], e1[M], d0[M], d1[M];
-  T w[M];
 };
 
 template <int P, int M, typename T>
@@ -29,7 +28,6 @@ LineTab<P, M, T> line_tables(const HostTables &h) {
   for (int i = 0; i < M; ++i) {
     t.e0[i] = T(h.e0[i]); t.e1[i] = T(h.e1[i]);
     t.d0[i] = T(h.d0[i]); t.d1[i] = T(h.d1[i]);
-    t.w[i] = T(h.gauss_w[i]);
   }
   return t;
 }
