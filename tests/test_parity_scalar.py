@@ -306,18 +306,24 @@ def test_autotune_keeps_parity(precision, geom):
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5])
 @pytest.mark.parametrize("geom", ["affine", "trilinear"])
-def test_overintegration_k_plus_2_points(k, geom):
+@pytest.mark.parametrize("arith", ["fp64", "fp32", "df64"])
+def test_overintegration_k_plus_2_points(k, geom, arith):
+    # m = k + 2 Gauss points: the point kernels (FP64) and the line kernels (FP32,
+    # double-float) with M = P + 1
     n = (4, 3, 5)
     verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
     m = k + 2
-    op = dg.Operator(dg.Mesh(*n, verts), k, quad_points=m)
+    op = dg.Operator(dg.Mesh(*n, verts), k, quad_points=m,
+                     precision=dg.DG_FP32 if arith == "fp32" else dg.DG_FP64)
     orc = oracle.Problem(*n, k, m=m, vertices=verts)
     kv, kf = wl.lognormal_kappa(op.mesh.ncell, m, seed=2)
-    op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    op.set_kappa(torch.from_numpy(kv).to("cuda", op.dtype), torch.from_numpy(kf).to("cuda", op.dtype))
+    if arith == "df64":
+        op.set_variant(dg.DG_VARIANT_DF64)
     orc.kappa_vol, orc.kappa_face = kv, kf
     x = wl.uniform_vector(op.ndofs, 0)
-    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert relerr(y, orc.apply(x)) <= TOL64
+    y = op.apply(torch.from_numpy(x).to("cuda", op.dtype)).double().cpu().numpy()
+    assert relerr(y, orc.apply(x)) <= (TOL32 if arith == "fp32" else TOL64)
     with pytest.raises(dg.DGError):
         op.set_variant(dg.DG_VARIANT_FUSED)
 
