@@ -8,6 +8,14 @@ DOFs), x ~ U[-1,1] (seed 0): the volume kernel, the interior and boundary face k
 and the back-projection kernel. Every input (x 134 MB, geometry 1.6 GB) is larger than
 the 129 MB L2, so no flush is needed between steps.
 
+Besides the headline the line carries (rank 0, one GPU): the Q1-Q5 sweep in FP64,
+double-float and FP32 (each FP32 result's error against the FP64 apply of the same x),
+config 4's FP32 apply of 16 right-hand sides, Stokes, the adjoint, and config 4's solve
+to 1e-10 (128^3, Q2, 16 right-hand sides): mixed CG with reliable updates and FP64
+refinement around FP32 CG against the all-FP64 CG with and without block Jacobi. Every
+roofline fraction is max(F / peak, B_alg / HBM) over the measured time, F the executed
+flops and B_alg the algorithm's own bytes (x, y, vertex coordinates).
+
 Prints one JSON line (rank 0). With --gpus N > 1 (torchrun) every rank applies its own
 replica of the workload (no collective on the data path) and value = total DOF/s.
 ``--impl reference`` times the CPU oracle instead (the only baseline that exists for
@@ -34,29 +42,62 @@ from paper_1812_08075_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "dg_apply DOF/s (FP64 and mixed) at Q2-Q5; % of FP64-peak / HBM roofline"
 N_CELLS = 64
-SM_COUNT = 152
-VARIANT_NAMES = {1: "three-kernel", 2: "fused persistent", 3: "cellwise persistent"}
+VARIANT_NAMES = {1: "three-kernel", 2: "fused persistent", 3: "cellwise persistent", 4: "double-float three-kernel"}
 PRECOND_NAMES = {0: "none", 1: "point Jacobi (diagonal set up outside the timed solves)",
                  2: "cell-block Jacobi by fast diagonalisation (set up outside the timed solves)"}
 FP64_FLOPS_PER_SM_CLK = 4.0   # 2 DFMA per SM per clock: 1.25 TFLOP/s nominal at 2.07 GHz
 FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FFMA per SM per clock
-# DRAM bytes (read + write) of one k_cell launch from the ncu capture of the 40^3 Q3 case
-# (profiles/scalar_apply_q3_fp64.md: 262.4 MB + 103.9 MB for 64000 cells); the kernel's
-# traffic is proportional to the number of cells, so it scales to a full launch by cells.
+# DRAM bytes (read + write) per cell of one k_cell launch, from an ncu capture of the
+# 40^3 Q3 case (262.4 MB + 103.9 MB for 64000 cells); the kernel's traffic is
+# proportional to the number of cells, so it scales to a full launch by cells.
 KCELL_Q3_DRAM_BYTES_PER_CELL = (262.393344e6 + 103.932928e6) / 40 ** 3
 
 
-def peaks():
+def sm_count() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def peaks(probe: bool = False):
+    """Roofline denominators: HBM from the driver's measured copy bandwidth; FP64 and FP32
+    derived from the pipes' per-clock rates, the device's SM count and the maximum SM
+    clock; with probe, also the FMA throughput this run measures (dg_measure_fma_peak)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     mp = json.load(open(path)) if os.path.exists(path) else {}
     clk = float(mp.get("sm_max_mhz", 2070.0)) * 1e6
-    return {
+    sms = sm_count()
+    out = {
         "hbm_gbs": float(mp.get("hbm_gbs", 6800.0)),
         "hbm_src": "measured" if "hbm_gbs" in mp else "fallback",
-        "fp64_tflops": SM_COUNT * FP64_FLOPS_PER_SM_CLK * clk / 1e12,
-        "fp32_tflops": SM_COUNT * FP32_FLOPS_PER_SM_CLK * clk / 1e12,
+        "fp64_tflops": sms * FP64_FLOPS_PER_SM_CLK * clk / 1e12,
+        "fp32_tflops": sms * FP32_FLOPS_PER_SM_CLK * clk / 1e12,
         "clk_mhz": clk / 1e6,
+        "sms": sms,
     }
+    if probe:
+        from paper_1812_08075_gb300 import dg
+        out["fp64_probe_tflops"] = dg.dg_measure_fma_peak(dg.DG_FP64)
+        out["fp32_probe_tflops"] = dg.dg_measure_fma_peak(dg.DG_FP32)
+    return out
+
+
+def roofline_entry(flops, alg_bytes, ms, pk, fp32, impl_bytes=None):
+    """Fraction of the roofline time max(F / peak, B_alg / HBM) over the measured time:
+    F = the executed kernels' exact flop count (equal to ncu's FP instruction count and
+    below the analytic model of the algorithm), B_alg = x read + y written (+ vertex
+    coordinates, + kappa), the algorithm's own bytes; stored geometry and scratch are
+    implementation bytes, reported apart."""
+    peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
+    t_alu = flops / (peak * 1e12)
+    t_mem = alg_bytes / (pk["hbm_gbs"] * 1e9)
+    t = ms * 1e-3
+    out = {"bound": "alu" if t_alu >= t_mem else "hbm", "roofline_frac": max(t_alu, t_mem) / t,
+           "tflops": flops / t / 1e12, "frac_alu_peak": flops / t / 1e12 / peak,
+           "alg_bytes": alg_bytes, "alg_gbs": alg_bytes / t / 1e9, "frac_hbm_alg": alg_bytes / t / 1e9 / pk["hbm_gbs"],
+           "flops": flops}
+    if impl_bytes is not None:
+        out["impl_bytes_model"] = impl_bytes
+    return out
 
 
 def workload_config(k: int):
@@ -231,34 +272,61 @@ def time_applies(op, x, y, steps, warmup, dist, profile=False):
     return ms, kt, (t0, t1)
 
 
+def config4_rhs(op64, n, k, nrhs):
+    """Config 4's right-hand sides b_s = l / max|l| + eta_s (seeds 0..nrhs-1) on the device:
+    l_i = (sin pi x sin pi y sin pi z, phi_i), the source evaluated at the library's own
+    Gauss points and integrated by its data-term kernel (dg_rhs)."""
+    import torch
+    from paper_1812_08075_gb300 import dg
+    nodes = dg.dg_reference_tables(k)["gauss_nodes"]
+    f = torch.from_numpy(wl.sin_product_source(n, n, n, nodes)).cuda()
+    l = op64.rhs(f)
+    del f
+    l = l / l.abs().max()
+    b = torch.empty(nrhs, op64.ndofs, dtype=torch.float64, device="cuda")
+    for s in range(nrhs):
+        b[s] = l + torch.from_numpy(wl.uniform_vector(op64.ndofs, s)).cuda()
+    torch.cuda.synchronize()
+    return b
+
+
 def mixed_apply(pk, n_cells=128, k=2, nrhs=16):
     """Config 4's operator (affine 128^3, Q2): the FP32 apply of 16 right-hand sides in one
-    persistent launch, next to the FP64 apply of the same 16 vectors."""
+    persistent launch, next to the FP64 apply of the same 16 vectors, with the FP32
+    result's error against the FP64 one."""
     import torch
     from paper_1812_08075_gb300 import dg
     mesh = dg.Mesh(n_cells, n_cells, n_cells)
     res = {"workload": f"scalar SIPG, {n_cells}^3 affine cells, Q{k}, {nrhs} right-hand sides "
-                       f"(sin-product source + U[-1,1] noise, seeds 0-{nrhs - 1})"}
-    b = torch.from_numpy(wl.refinement_rhs(n_cells, n_cells, n_cells, (k + 1) ** 3, range(nrhs))).cuda()
-    for prec, tag in ((dg.DG_FP32, "fp32"), (dg.DG_FP64, "fp64")):
+                       f"(Gauss-projected sin-product load vector + U[-1,1] noise, seeds 0-{nrhs - 1})"}
+    ys = {}
+    b = None
+    for prec, tag in ((dg.DG_FP64, "fp64"), (dg.DG_FP32, "fp32")):
         op = dg.Operator(mesh, k, precision=prec, max_rhs=nrhs)
+        if b is None:
+            b = config4_rhs(op, n_cells, k, nrhs)
         res.setdefault("tuning", {})[tag] = op.autotune(nrhs)
         xx = b.to(op.dtype)
         yy = torch.empty_like(xx)
         ms, kt, _ = time_applies(op, xx, yy, 10, 3, None, profile=True)
         st = op.stats()
         f = sum(st.flops) * nrhs
-        peak = pk["fp32_tflops"] if prec == dg.DG_FP32 else pk["fp64_tflops"]
-        byt = st.dofs_bytes * nrhs
-        t_roof = max(f / (peak * 1e12), sum(st.bytes) * nrhs / (pk["hbm_gbs"] * 1e9))
-        res[tag] = {"dof_s": nrhs * op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "variant":
-                    VARIANT_NAMES[st.variant],
-                    "persistent_grid": st.persistent_grid, "tflops": f / (ms * 1e-3) / 1e12,
-                    "frac_alu_peak": f / (ms * 1e-3) / 1e12 / peak,
-                    "hbm_gbs_algorithmic": byt / (ms * 1e-3) / 1e9,
-                    "frac_hbm": byt / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                    "roofline_frac": t_roof / (ms * 1e-3), "kernel_ms": kt}
-        del op, xx, yy
+        alg = st.dofs_bytes * nrhs  # x read + y written, affine mesh (no vertices)
+        ent = {"dof_s": nrhs * op.ndofs / (ms * 1e-3), "ms_per_apply": ms, "variant": VARIANT_NAMES[st.variant],
+               "persistent_grid": st.persistent_grid, "kernel_ms": kt}
+        ent.update(roofline_entry(f, alg, ms, pk, prec == dg.DG_FP32, impl_bytes=sum(st.bytes) * nrhs))
+        if prec == dg.DG_FP64:
+            ys["fp64"] = yy
+        else:
+            y64 = ys["fp64"]
+            err = [float((yy[s].double() - y64[s]).abs().max() / y64[s].abs().max()) for s in range(nrhs)]
+            ent["err_vs_fp64"] = max(err)
+            ent["err_note"] = "max over right-hand sides of max|y32 - y64| / max|y64| (y64: the FP64 apply above)"
+        res[tag] = ent
+        del op, xx
+        if prec == dg.DG_FP32:
+            del yy
+    del ys, b
     return res
 
 
@@ -303,12 +371,12 @@ def adjoint_apply(n_cells=64, k=3):
     stream = torch.cuda.current_stream()
     for _ in range(3):
         dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(), gf.data_ptr(),
-                            stream.cuda_stream)
+                            stream.cuda_stream, nrhs=1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(20):
         dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(), gf.data_ptr(),
-                            stream.cuda_stream)
+                            stream.cuda_stream, nrhs=1)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_adj = e0.elapsed_time(e1) / 20
@@ -316,7 +384,7 @@ def adjoint_apply(n_cells=64, k=3):
     ref = (y.clone(), gv.clone(), gf.clone())
     op.set_variant(dg.DG_VARIANT_DF64)
     adj = lambda: dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), gv.data_ptr(),  # noqa: E731
-                                      gf.data_ptr(), stream.cuda_stream)
+                                      gf.data_ptr(), stream.cuda_stream, nrhs=1)
     ms_adj_df = event_ms(adj)
     diffs = [float((q - p).abs().max() / p.abs().max()) for p, q in zip(ref, (y, gv, gf))]
     ms_fwd_df, _, _ = time_applies(op, x, y, 20, 3, None, profile=False)
@@ -373,65 +441,82 @@ def next_rows_apply(n_cells=64, k=3):
             "note": "semilinear and rhs recompute the geometry in the kernels; the forward apply reads stored geometry"}
 
 
-def run_solve(args):
-    """Config 4: 16 right-hand sides, FP64 CG against FP64 refinement around FP32 CG."""
+def solve_entry(n, k, nrhs, rtol, inner_rtol=1e-3, delta=0.1, fp64_max_iters=20000, precond=2,
+                fp64_preconds=(0, 2)):
+    """Config 4's solve to rtol, all right-hand sides advanced together: mixed CG with
+    reliable updates (FP32 iterations, FP64 residual replacements), FP64 iterative
+    refinement around FP32 CG, and the all-FP64 CG with each preconditioner of
+    fp64_preconds, on the same right-hand sides. Wall seconds of each solve call
+    (synchronous), its iterations, and the FP64 residual recomputed afterwards."""
     import torch
-    from paper_1812_08075_gb300 import build as libbuild, dg
-    libbuild.build()
-    n, k, nrhs = args.solve_cells, args.solve_degree, args.solve_rhs
+    from paper_1812_08075_gb300 import dg
     mesh = dg.Mesh(n, n, n)
     op64 = dg.Operator(mesh, k, max_rhs=nrhs)
     op32 = dg.Operator(mesh, k, precision=dg.DG_FP32, max_rhs=nrhs)
-    b = torch.from_numpy(wl.refinement_rhs(n, n, n, (k + 1) ** 3, range(nrhs))).cuda()
+    b = config4_rhs(op64, n, k, nrhs)
     stream = torch.cuda.current_stream().cuda_stream
-    out = {"mode": "solve", "workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides",
-           "ndofs": op64.ndofs, "rtol": args.solve_rtol,
-           "preconditioner": PRECOND_NAMES[args.precond]}
-    p64 = args.precond if args.precond_fp64 is None else args.precond_fp64
-    if p64 != args.precond:
-        out["preconditioner_fp64_cg"] = PRECOND_NAMES[p64]
-    # set up the preconditioners before timing (the operators keep them)
-    for op, pc, bb in ((op64, p64, b), (op32, args.precond, b.float())):
-        if pc:
-            xz = torch.zeros_like(bb)
-            dg.dg_cg_solve(op.handle, bb.data_ptr(), xz.data_ptr(), nrhs, dg.dg_cg_options(1e-1, 50, 50, 0, pc), stream)
-            del xz
+    out = {"workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides (Gauss-projected "
+                       f"sin-product load vector + U[-1,1] noise), x0 = 0",
+           "ndofs": op64.ndofs, "nrhs": nrhs, "rtol": rtol,
+           "fp32_operator": None, "mixed_preconditioner": PRECOND_NAMES[precond]}
+    # set up the preconditioners and the FP32 operator's variant before timing
+    for op, pcs, bb in ((op64, fp64_preconds, b), (op32, (precond,), b.float())):
+        for pc in pcs:
+            if pc:
+                xz = torch.zeros_like(bb)
+                dg.dg_cg_solve(op.handle, bb.data_ptr(), xz.data_ptr(), nrhs, dg.dg_cg_options(1e-1, 50, 50, 0, pc),
+                               stream)
+                del xz
+    out["fp32_operator"] = VARIANT_NAMES[op32.stats().variant]
 
-    def check(x):
+    def relres(x):
         r = b - op64.apply(x)
-        return [float(torch.linalg.norm(r[i]) / torch.linalg.norm(b[i])) for i in range(nrhs)]
+        return max(float(torch.linalg.norm(r[i]) / torch.linalg.norm(b[i])) for i in range(nrhs))
 
-    x = torch.zeros_like(b)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    ok, info = dg.dg_refine_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, args.solve_rtol, 30,
-                                  dg.dg_cg_options(args.inner_rtol, 100000, 50, 1, args.precond), stream)
-    torch.cuda.synchronize()
-    t_mixed = time.perf_counter() - t
-    out["mixed"] = {"seconds": t_mixed, "converged": ok, "outer": max(i["outer"] for i in info),
-                    "inner_iters_max": max(i["iters"] for i in info), "relres_max": max(check(x)),
-                    "inner_rtol": args.inner_rtol}
-    x = torch.zeros_like(b)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    ok, info = dg.dg_mixed_cg_solve(op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, args.delta,
-                                    dg.dg_cg_options(args.solve_rtol, 100000, 50, 1, args.precond), stream)
-    torch.cuda.synchronize()
-    t_rel = time.perf_counter() - t
-    out["mixed_reliable"] = {"seconds": t_rel, "converged": ok, "fp32_iters_max": max(i["iters"] for i in info),
-                             "updates_max": max(i["outer"] for i in info), "relres_max": max(check(x)),
-                             "delta": args.delta}
-    x = torch.zeros_like(b)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    ok, info = dg.dg_cg_solve(op64.handle, b.data_ptr(), x.data_ptr(), nrhs,
-                              dg.dg_cg_options(args.solve_rtol, args.fp64_max_iters, 50, 1, p64), stream)
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t
-    out["fp64_cg"] = {"seconds": t64, "converged": ok, "iters_max": max(i["iters"] for i in info),
-                      "relres_max": max(check(x))}
-    out["speedup_mixed_over_fp64"] = t64 / t_mixed
-    out["speedup_reliable_over_fp64"] = t64 / t_rel
+    def timed(fn):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ok, info = fn(x)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, ok, info, relres(x)
+
+    sec, ok, info, rr = timed(lambda x: dg.dg_mixed_cg_solve(
+        op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, delta,
+        dg.dg_cg_options(rtol, 100000, 50, 1, precond), stream))
+    out["mixed_reliable"] = {"seconds": sec, "converged": ok, "fp32_iters_max": max(i["iters"] for i in info),
+                             "fp64_updates_max": max(i["outer"] for i in info), "relres_fp64_max": rr, "delta": delta}
+    sec, ok, info, rr = timed(lambda x: dg.dg_refine_solve(
+        op64.handle, op32.handle, b.data_ptr(), x.data_ptr(), nrhs, rtol, 30,
+        dg.dg_cg_options(inner_rtol, 100000, 50, 1, precond), stream))
+    out["refinement"] = {"seconds": sec, "converged": ok, "outer_max": max(i["outer"] for i in info),
+                         "inner_iters_max": max(i["iters"] for i in info), "relres_fp64_max": rr,
+                         "inner_rtol": inner_rtol}
+    best = None
+    for pc in fp64_preconds:
+        sec, ok, info, rr = timed(lambda x: dg.dg_cg_solve(
+            op64.handle, b.data_ptr(), x.data_ptr(), nrhs, dg.dg_cg_options(rtol, fp64_max_iters, 50, 1, pc), stream))
+        out[f"fp64_cg_{['none', 'jacobi', 'block_jacobi'][pc]}"] = {
+            "seconds": sec, "converged": ok, "iters_max": max(i["iters"] for i in info), "relres_fp64_max": rr,
+            "preconditioner": PRECOND_NAMES[pc]}
+        if ok and (best is None or sec < best[0]):
+            best = (sec, pc)
+    if best:
+        out["fp64_cg_best_seconds"] = best[0]
+        out["fp64_cg_best_preconditioner"] = PRECOND_NAMES[best[1]]
+        out["speedup_mixed_reliable_over_best_fp64"] = best[0] / out["mixed_reliable"]["seconds"]
+        out["speedup_refinement_over_best_fp64"] = best[0] / out["refinement"]["seconds"]
+    return out
+
+
+def run_solve(args):
+    """Config 4's solve comparison alone (sizes from the command line)."""
+    from paper_1812_08075_gb300 import build as libbuild
+    libbuild.build()
+    pcs = (args.precond_fp64,) if args.precond_fp64 is not None else (0, 2)
+    out = solve_entry(args.solve_cells, args.solve_degree, args.solve_rhs, args.solve_rtol, args.inner_rtol,
+                      args.delta, args.fp64_max_iters, args.precond, pcs)
+    out["mode"] = "solve"
     print(json.dumps(out), flush=True)
 
 
@@ -470,7 +555,7 @@ def run_ours(args, rank, world, dist):
     tuning = op.autotune(1) if args.autotune else None
     x = torch.from_numpy(wl.uniform_vector(op.ndofs, 0)).cuda()
     y = torch.empty_like(x)
-    pk = peaks()
+    pk = peaks(probe=rank == 0)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -490,8 +575,11 @@ def run_ours(args, rank, world, dist):
                                   "scaled by cells to this launch" if traffic else None,
                 "algorithmic_bytes_per_launch": st.bytes[dom],
                 "kernel": names[dom], "kernel_ms": kt[dom],
-                "peak_source": f"FP64 CUDA-core peak derived: {SM_COUNT} SMs x 2 DFMA/clk x 2 flop x "
-                               f"{pk['clk_mhz']:.0f} MHz (1.25 TFLOP/s nominal)",
+                "peak_source": f"FP64 CUDA-core peak derived: {pk['sms']} SMs x 2 DFMA/clk x 2 flop x "
+                               f"{pk['clk_mhz']:.0f} MHz (1.25 TFLOP/s nominal); this run's FMA-chain probe "
+                               f"(dg_measure_fma_peak) measured {pk.get('fp64_probe_tflops', float('nan')):.3f}",
+                "probe_tflops": pk.get("fp64_probe_tflops"),
+                "frac_of_probe": achieved / pk["fp64_probe_tflops"] if pk.get("fp64_probe_tflops") else None,
                 "algorithmic_flops_per_launch": flops[dom]}
     tot_flops = sum(flops)
     whole = {"flops_per_apply": tot_flops, "tflops": tot_flops / (ms * 1e-3) / 1e12,
@@ -522,7 +610,9 @@ def run_ours(args, rank, world, dist):
     del op, x, y, xh, yh
     if args.sweep and rank == 0:
         sweep = {}
+        vert_bytes = 8 * 3 * (N_CELLS + 1) ** 3  # vertex coordinates, read by the geometry
         for kk in (1, 2, 3, 4, 5):
+            y64 = None
             for prec, tag, es in ((dg.DG_FP64, "fp64", 8), (dg.DG_FP32, "fp32", 4)):
                 o = dg.Operator(mesh, kk, precision=prec)
                 if args.autotune:  # the framework's own tuner, as for the headline operator
@@ -531,30 +621,32 @@ def run_ours(args, rank, world, dist):
                 yy = torch.empty_like(xx)
                 ms_k, kt_k, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
                 st_k = o.stats()
-                f, byt = sum(st_k.flops), sum(st_k.bytes)
-                peak = pk["fp64_tflops"] if prec == dg.DG_FP64 else pk["fp32_tflops"]
-                t_roof = max(f / (peak * 1e12), byt / (pk["hbm_gbs"] * 1e9))
-                sweep[f"Q{kk}_{tag}"] = {"dof_s": o.ndofs / (ms_k * 1e-3), "ms": ms_k,
-                                         "tflops": f / (ms_k * 1e-3) / 1e12,
-                                         "frac_alu_peak": f / (ms_k * 1e-3) / 1e12 / peak,
-                                         "hbm_gbs_model": byt / (ms_k * 1e-3) / 1e9,
-                                         "roofline_frac": t_roof / (ms_k * 1e-3),
-                                         "bound": "alu" if f / (peak * 1e12) >= byt / (pk["hbm_gbs"] * 1e9) else "hbm",
-                                         "kernel_ms": kt_k,
-                                         "blocking": [st_k.variant, st_k.cells_per_block, st_k.faces_per_block]}
+                ent = {"dof_s": o.ndofs / (ms_k * 1e-3), "ms": ms_k, "kernel_ms": kt_k,
+                       "blocking": [st_k.variant, st_k.cells_per_block, st_k.faces_per_block]}
+                ent.update(roofline_entry(sum(st_k.flops), 2 * es * o.ndofs + vert_bytes, ms_k, pk,
+                                          prec == dg.DG_FP32, impl_bytes=sum(st_k.bytes)))
+                if prec == dg.DG_FP32:  # error of the FP32 result against the FP64 apply of the same x
+                    ent["err_vs_fp64"] = float((yy.double() - y64).abs().max() / y64.abs().max())
+                sweep[f"Q{kk}_{tag}"] = ent
                 if prec == dg.DG_FP64:  # the same operator in double-float arithmetic, blockings tuned
                     y64 = yy.clone()
+                    f = sum(st_k.flops)
                     o.set_variant(dg.DG_VARIANT_DF64)
                     if args.autotune:
                         o.autotune(1)
                     ms_d, kt_d, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
-                    sweep[f"Q{kk}_df64"] = {"dof_s": o.ndofs / (ms_d * 1e-3), "ms": ms_d,
-                                            "fp64_equivalent_tflops": f / (ms_d * 1e-3) / 1e12,
-                                            "speedup_over_fp64": ms_k / ms_d,
-                                            "rel_diff_vs_fp64": float((yy - y64).abs().max() / y64.abs().max()),
-                                            "kernel_ms": kt_d}
-                    del y64
+                    ent_d = {"dof_s": o.ndofs / (ms_d * 1e-3), "ms": ms_d,
+                             "fp64_equivalent_tflops": f / (ms_d * 1e-3) / 1e12,
+                             "speedup_over_fp64": ms_k / ms_d,
+                             "err_vs_fp64": float((yy - y64).abs().max() / y64.abs().max()),
+                             "kernel_ms": kt_d}
+                    # double-float runs on the FP32 pipes with about ten FP32 operations per FP64
+                    # one, so its rate is quoted as FP64-equivalent work, beside its HBM fraction
+                    ent_d["alg_bytes"] = 16 * o.ndofs + vert_bytes
+                    ent_d["frac_hbm_alg"] = ent_d["alg_bytes"] / (ms_d * 1e-3) / 1e9 / pk["hbm_gbs"]
+                    sweep[f"Q{kk}_df64"] = ent_d
                 del o, xx, yy
+            del y64
         out["sweep"] = sweep
     if args.mixed and rank == 0:
         out["mixed_apply"] = mixed_apply(pk, n_cells=args.mixed_cells)
@@ -569,6 +661,11 @@ def run_ours(args, rank, world, dist):
         out["cpu_baseline"] = {"value": rate, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                                "sample": f"{ncells} random cells of the {N_CELLS}^3 Q{k} workload, cell-gather "
                                          f"form, {dt:.1f} s wall on {cores} threads"}
+    if args.solve and rank == 0 and world == 1:
+        torch.cuda.empty_cache()
+        out["solve"] = solve_entry(args.solve_cells, args.solve_degree, args.solve_rhs, args.solve_rtol,
+                                   args.inner_rtol, args.delta, args.fp64_max_iters, args.precond,
+                                   (0, 2) if args.precond_fp64 is None else (args.precond_fp64,))
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -594,14 +691,16 @@ def main():
     ap.add_argument("--solve-degree", type=int, default=2)
     ap.add_argument("--solve-rhs", type=int, default=16)
     ap.add_argument("--solve-rtol", type=float, default=1e-10)
-    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--fp64-max-iters", type=int, default=20000)
-    ap.add_argument("--precond", type=int, default=0, choices=(0, 1, 2),
-                    help="0: none, 1: point Jacobi, 2: cell-block Jacobi (both solvers)")
+    ap.add_argument("--precond", type=int, default=2, choices=(0, 1, 2),
+                    help="preconditioner of the mixed solvers: 0 none, 1 point Jacobi, 2 cell-block Jacobi")
     ap.add_argument("--delta", type=float, default=0.1,
                     help="reliable-update threshold of the mixed CG (FP32 residual reduction per update)")
     ap.add_argument("--precond-fp64", type=int, default=None, choices=(0, 1, 2),
-                    help="preconditioner of the FP64 CG if it differs from --precond")
+                    help="one preconditioner for the FP64 CG (default: time it with none and with block Jacobi)")
+    ap.add_argument("--no-solve", dest="solve", action="store_false", default=True,
+                    help="skip config 4's solve comparison (mixed vs FP64 CG) of the default run")
     args = ap.parse_args()
     global N_CELLS
     N_CELLS = args.cells

@@ -286,18 +286,22 @@ dg_status dg_apply_semilinear(const dg_operator *op, int mode, double beta, cons
  * DG_ERR_CUDA. */
 dg_status dg_rhs(const dg_operator *op, const void *f_vol, const void *g_face, void *F, void *stream);
 
-/* Adjoint of the scalar operator for the loss L = 0.5 ||A(kappa) x - b||^2:
- *   y = A^T r (the transposed apply, r = A x - b supplied by the caller), and, when
- *   x and the output arrays are non-NULL, dkappa_vol[c][q] = r^T dA/dkappa_vol[c][q] x
- *   and dkappa_face[c][lf][q] likewise (layouts as dg_operator_set_kappa).
+/* Adjoint of the scalar operator for the loss L = 0.5 sum_s ||A(kappa) x_s - b_s||^2 over
+ * nrhs right-hand sides (Sec. 2.1: the transposed Jacobian action of the linear problem):
+ *   y_s = A^T r_s for s = 0..nrhs-1 (the transposed apply, r_s = A x_s - b_s supplied by the
+ *   caller), and, when x and the output arrays are non-NULL,
+ *   dkappa_vol[c][q] = sum_s r_s^T dA/dkappa_vol[c][q] x_s and dkappa_face[c][lf][q] likewise
+ *   (layouts as dg_operator_set_kappa; one array shared by all right-hand sides, holding
+ *   the gradient of the summed loss).
+ * r, x, y: device [nrhs][ndofs], nrhs in 1..max_rhs; y distinct from r and x.
  * Geometry is recomputed from the vertex coordinates inside the kernels (nothing
  * stored is required). Stokes and FP32 operators give y = A^T r only (their forward
  * kernels with the flux and symmetry coefficients exchanged; the Stokes coupling is its
- * own transpose), and require dkappa NULL. One right-hand side. Errors:
- * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED (dkappa on Stokes or FP32, anisotropic degrees,
- * over-integration), DG_ERR_CUDA. */
+ * own transpose), and require dkappa NULL. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED
+ * (dkappa on Stokes or FP32, anisotropic degrees, over-integration), DG_ERR_OOM (the
+ * first call with dkappa allocates a second trace buffer), DG_ERR_CUDA. */
 dg_status dg_apply_adjoint(const dg_operator *op, const void *r, const void *x, void *y,
-                           void *dkappa_vol, void *dkappa_face, void *stream);
+                           void *dkappa_vol, void *dkappa_face, int nrhs, void *stream);
 
 /* Options of the conjugate-gradient solves (the paper has no solver; these are the
  * solves the matrix-free apply serves).
@@ -393,15 +397,21 @@ dg_status dg_mixed_cg_solve(const dg_operator *op64, const dg_operator *op32, co
  * implicit device synchronisation that cudaMalloc/cudaFree can cause. Instead of
  * operator-owned buffers it uses one file-scope device array of 32 MiB (reserved on
  * every GPU that loads libdg until the process exits) for the reference tables and the
- * apply's scratch; the caller passes x and y (device, 16-byte aligned, not aliased).
- * Limit: ncell * ((k+1)^3 + 24 (k+1)^2) * 8 bytes must fit in 32 MiB - 4 KiB (e.g.
- * 9362 cells at Q3); larger problems return DG_ERR_UNSUPPORTED without launching.
- * The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture. All calls share the array:
- * calls that overlap on the GPU (different streams, or concurrent host threads) race on
- * it and must be ordered by the caller. Within one call every scratch entry is written
- * before it is read, so leftovers of earlier calls do no harm. Errors:
- * DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_CUDA. */
+ * apply's scratch; the caller passes x and y (device, 16-byte aligned, [ncell][(k+1)^3],
+ * non-overlapping).
+ * Limit: ncell * ((k+1)^3 + 24 (k+1)^2) * 8 bytes must fit in 32 MiB - 20 KiB (e.g.
+ * 9356 cells at Q3); larger problems return DG_ERR_UNSUPPORTED without launching.
+ * Set-up: the first call on a device, with that device current, looks up the array's
+ * device address and uploads the reference tables of degrees 1..5 into it with one
+ * synchronous copy; make that first call before any stream capture. Later calls on the
+ * device only launch the apply's three kernels on `stream`. A cudaDeviceReset discards
+ * the array and its tables, so the entry point must not be used on that device again
+ * in the same process after a reset.
+ * All calls share the array: calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race on it and must be ordered by the caller. Within one call
+ * every scratch entry is written before it is read, so leftovers of earlier calls do no
+ * harm. Errors: DG_ERR_INVALID_ARG (bad size, NULL, misaligned or overlapping x and y),
+ * DG_ERR_UNSUPPORTED (degree > 5 or over the limit), DG_ERR_CUDA. */
 dg_status dg_apply_affine_static(int nx, int ny, int nz, int degree, double c, double theta,
                                  double penalty_alpha, int dirichlet_mask, const double *x,
                                  double *y, void *stream);
@@ -414,6 +424,15 @@ dg_status dg_apply_affine_static(int nx, int ny, int nz, int degree, double c, d
  * DG_ERR_CUDA. */
 dg_status dg_operator_profile(dg_operator *op, int enable);
 dg_status dg_operator_kernel_times(dg_operator *op, double ms[3], int64_t *napplies);
+
+/* Measured FMA throughput of this GPU for measurement harnesses (the paper reports its
+ * operator throughput as a fraction of the machine's peak, Sec. 5): a kernel in which
+ * every thread runs eight independent FMA chains in the given precision (DG_FP64 or
+ * DG_FP32), one wave of blocks filling every SM, calibrated to about 50 ms per launch and
+ * timed with CUDA events on `stream`; *tflops receives the best of three launches in
+ * TFLOP/s (FMA = 2 flops). Allocates and frees a small output buffer; synchronises the
+ * stream. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_measure_fma_peak(int precision, void *stream, double *tflops);
 
 /* Reference-element tables the CUDA path uses (host, double), for inspection:
  * gauss_nodes/weights [m] on [0,1], gll_nodes [k+1], interp [m][k+1] (GLL Lagrange

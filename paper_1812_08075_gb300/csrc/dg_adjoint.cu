@@ -4,4 +4,4 @@
 template cudaError_t launch_scalar_adjoint<double>(int, int, bool, const ScalarArgs<double> &, double, const double *,
                                                    const double *, double *, double *, double *, double *, double *,
                                                    double *, double *, int, int, cudaStream_t, const cudaEvent_t *,
-                                                   int, double);
+                                                   int, double, bool);

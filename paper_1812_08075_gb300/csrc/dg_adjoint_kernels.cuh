@@ -19,6 +19,19 @@ namespace dga {
 
 using namespace dgk;
 
+// dkappa entry: overwritten, or (acc) added to, for the sum over right-hand sides. Each
+// entry is written by exactly one thread of a launch, so no atomics are needed.
+template <typename T>
+__device__ __forceinline__ void put_dk(io_t<T> *p, const T &v, bool acc) {
+  if (acc) {
+    io_t<T> t;
+    store_to(&t, v);
+    *p += t;
+  } else {
+    store_to(p, v);
+  }
+}
+
 template <int P, int M, typename T>
 struct Tab {
   T interp[M * P];
@@ -114,7 +127,8 @@ template <int P, int GEO, bool KAPPA, bool DK, typename T>
 __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<T> a, const io_t<T> *__restrict__ r,
                                                   const io_t<T> *__restrict__ x, T *__restrict__ rvol,
                                                   T *__restrict__ tr_r, T *__restrict__ tr_x,
-                                                  io_t<T> *__restrict__ dk_vol, int cpb, int nlmode, double beta) {
+                                                  io_t<T> *__restrict__ dk_vol, int cpb, int nlmode, double beta,
+                                                  bool dk_acc) {
   constexpr int M = P, P3 = P * P * P, M2 = M * M, M3 = M * M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &tb = *reinterpret_cast<Tab<P, M, T> *>(smem_raw);
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(256) k_cell_adj(const ScalarArgs<T> a, const i
         b2.add(tb.dcol[q2 * M + k], v[q0 + q1 * M + k * M2]);
       }
       const T h0 = b0.get(), h1 = b1.get(), h2 = b2.get();
-      store_to(dk_vol + (c0 + c) * M3 + q, fma(Gr0, h0, fma(Gr1, h1, Gr2 * h2)));
+      put_dk<T>(dk_vol + (c0 + c) * M3 + q, fma(Gr0, h0, fma(Gr1, h1, Gr2 * h2)), dk_acc);
     }
     F0[i] = kq * Gr0;
     F1[i] = kq * Gr1;
@@ -243,7 +257,8 @@ __device__ __forceinline__ void tangential(const T *u, const T *dcol, int qs, in
 template <int M, int GEO, bool KAPPA, bool DK, typename T>
 __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const double theta,
                                                   const T *__restrict__ tr_r, const T *__restrict__ tr_x,
-                                                  T *__restrict__ fres, io_t<T> *__restrict__ dk_face, int fpb) {
+                                                  T *__restrict__ fres, io_t<T> *__restrict__ dk_face, int fpb,
+                                                  bool dk_acc) {
   constexpr int M2 = M * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto &tb = *reinterpret_cast<Tab<1, M, T> *>(smem_raw);
@@ -369,8 +384,8 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
       }
       if (DK) {
         const T Jx = S[4 * M2 + qf] - S[6 * M2 + qf];
-        store_to(dk_face + (F.cm * 6 + 2 * ax + 1) * M2 + qf, half * fma(-gxm, Jr, thetaT * Jx * grm));
-        store_to(dk_face + (F.cp * 6 + 2 * ax) * M2 + qf, half * fma(-gxp, Jr, thetaT * Jx * grp));
+        put_dk<T>(dk_face + (F.cm * 6 + 2 * ax + 1) * M2 + qf, half * fma(-gxm, Jr, thetaT * Jx * grm), dk_acc);
+        put_dk<T>(dk_face + (F.cp * 6 + 2 * ax) * M2 + qf, half * fma(-gxp, Jr, thetaT * Jx * grp), dk_acc);
       }
     } else {
       const int64_t cb = side1 ? F.cm : F.cp;
@@ -394,7 +409,7 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
         R[M2 + qf] = s1;
         R[2 * M2 + qf] = s2;
       }
-      if (DK) store_to(dk_face + (cb * 6 + lf) * M2 + qf, dk);
+      if (DK) put_dk<T>(dk_face + (cb * 6 + lf) * M2 + qf, dk, dk_acc);
     }
   }
   if (GEO == GEO_AFFINE) return;
@@ -443,7 +458,7 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 template <int P, int GEO, bool KAPPA, bool DK, typename T>
 cudaError_t run(const ScalarArgs<T> &a, double theta, const io_t<T> *r, const io_t<T> *x, io_t<T> *y,
                 io_t<T> *dk_vol, io_t<T> *dk_face, T *rvol, T *tr_r, T *tr_x, T *fres, int cpb, int fpb,
-                cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta) {
+                cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta, bool dk_acc) {
   constexpr int M = P, M2 = M * M, M3 = M * M * M;
   cudaError_t e;
   {
@@ -452,7 +467,7 @@ cudaError_t run(const ScalarArgs<T> &a, double theta, const io_t<T> *r, const io
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], s);
     k<<<(unsigned)((a.ncell + cpb - 1) / cpb), threads_for(cpb * M3), sm, s>>>(a, r, x, rvol, tr_r, tr_x, dk_vol, cpb,
-                                                                              nlmode, beta);
+                                                                              nlmode, beta, dk_acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -460,7 +475,7 @@ cudaError_t run(const ScalarArgs<T> &a, double theta, const io_t<T> *r, const io
     auto k = k_face_adj<M, GEO, KAPPA, DK, T>;
     if ((e = set_smem(k, sm)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    k<<<(unsigned)((a.nface + fpb - 1) / fpb), threads_for(fpb * M2), sm, s>>>(a, theta, tr_r, tr_x, fres, dk_face, fpb);
+    k<<<(unsigned)((a.nface + fpb - 1) / fpb), threads_for(fpb * M2), sm, s>>>(a, theta, tr_r, tr_x, fres, dk_face, fpb, dk_acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -478,9 +493,9 @@ cudaError_t run(const ScalarArgs<T> &a, double theta, const io_t<T> *r, const io
 template <int P, typename T>
 cudaError_t run_p(int geo, bool kappa, bool dk, const ScalarArgs<T> &a, double theta, const io_t<T> *r,
                   const io_t<T> *x, io_t<T> *y, io_t<T> *dkv, io_t<T> *dkf, T *rvol, T *trr, T *trx, T *fres, int cpb,
-                  int fpb, cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta) {
+                  int fpb, cudaStream_t s, const cudaEvent_t *ev, int nlmode, double beta, bool dk_acc) {
 #define DGA_RUN(G, K, D) \
-  return run<P, G, K, D, T>(a, theta, r, x, y, dkv, dkf, rvol, trr, trx, fres, cpb, fpb, s, ev, nlmode, beta)
+  return run<P, G, K, D, T>(a, theta, r, x, y, dkv, dkf, rvol, trr, trx, fres, cpb, fpb, s, ev, nlmode, beta, dk_acc)
   if (geo == GEO_AFFINE) {
     if (kappa) { if (dk) DGA_RUN(GEO_AFFINE, true, true); DGA_RUN(GEO_AFFINE, true, false); }
     if (dk) DGA_RUN(GEO_AFFINE, false, true);
@@ -498,14 +513,14 @@ template <typename T>
 cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<T> &a, double theta, const io_t<T> *r,
                                   const io_t<T> *x, io_t<T> *y, io_t<T> *dk_vol, io_t<T> *dk_face, T *rvol, T *tr_r,
                                   T *tr_x, T *fres, int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev,
-                                  int nlmode, double beta) {
+                                  int nlmode, double beta, bool dk_acc) {
   const bool dk = x != nullptr && dk_vol != nullptr && dk_face != nullptr;
   if ((nlmode == 2 && !x) || (nlmode && dk)) return cudaErrorInvalidValue;
   switch (p) {
 #define DGA_P(PP)                                                                                                \
   case PP:                                                                                                       \
     return dga::run_p<PP, T>(geo, kappa, dk, a, theta, r, x, y, dk_vol, dk_face, rvol, tr_r, tr_x, fres, cpb, fpb, s, \
-                             ev, nlmode, beta);
+                             ev, nlmode, beta, dk_acc);
     DGA_P(2) DGA_P(3) DGA_P(4) DGA_P(5) DGA_P(6)
 #undef DGA_P
     default: return cudaErrorInvalidValue;

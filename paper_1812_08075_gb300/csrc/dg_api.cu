@@ -30,6 +30,16 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
+int dg_device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return sms;
+}
+
 extern "C" {
 
 const char *dg_status_string(dg_status s) {
@@ -689,10 +699,11 @@ dg_status dg_apply_host(const dg_operator *op_c, const void *x_host, void *y_hos
 }
 
 dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x, void *y, void *dkappa_vol,
-                           void *dkappa_face, void *stream) {
+                           void *dkappa_face, int nrhs, void *stream) {
   dg_operator *op = const_cast<dg_operator *>(op_c);
   if (op && op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if (!op || !r || !y || r == y || (x && x == y)) return fail(DG_ERR_INVALID_ARG);
+  if (nrhs < 1 || nrhs > op->max_rhs) return fail(DG_ERR_INVALID_ARG);
   if (!aligned16(r) || !aligned16(y) || (x && !aligned16(x))) return fail(DG_ERR_INVALID_ARG);
   if ((dkappa_vol == nullptr) != (dkappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (dkappa_vol && (!x || !aligned16(dkappa_vol) || !aligned16(dkappa_face))) return fail(DG_ERR_INVALID_ARG);
@@ -700,7 +711,7 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
     // no kappa to differentiate: y = A^T r is the forward operator with the flux and
     // symmetry coefficients exchanged (the Stokes coupling [[., B^T], [B, 0]] is symmetric)
     if (dkappa_vol) return fail(DG_ERR_UNSUPPORTED);
-    return apply_impl(op, r, y, 1, (cudaStream_t)stream, true);
+    return apply_impl(op, r, y, nrhs, (cudaStream_t)stream, true);
   }
   if (op->problem != DG_SCALAR || op->precision != DG_FP64 || op->m != op->p) return fail(DG_ERR_UNSUPPORTED);
   const int M2 = op->m * op->m;
@@ -712,20 +723,29 @@ dg_status dg_apply_adjoint(const dg_operator *op_c, const void *r, const void *x
   }
   const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
   const cudaEvent_t *ev = next_events(op);
-  if (op->variant == DG_VARIANT_DF64 && df64_ok(op)) {
-    const cudaError_t e = launch_scalar_adjoint<df64>(
-        op->p, geo, op->kappa_vol != nullptr, df64_args(op, true), op->theta, (const double *)r,
-        dkappa_vol ? (const double *)x : nullptr, (double *)y, (double *)dkappa_vol, (double *)dkappa_face,
-        (df64 *)op->d_rvol, (df64 *)op->d_tr, (df64 *)op->d_tr2, (df64 *)op->d_fres, op->cpb, op->fpb,
-        (cudaStream_t)stream, ev);
-    return e == cudaSuccess ? DG_OK : fail(DG_ERR_CUDA);
+  const int64_t sd = op->ndofs;
+  const bool df = op->variant == DG_VARIANT_DF64 && df64_ok(op);
+  // one pass of the three adjoint kernels per right-hand side (scratch of the first slot
+  // reused in stream order); dkappa of the second and later right-hand sides is added to
+  // the first one's, which gives the gradient of the summed loss
+  for (int s = 0; s < nrhs; ++s) {
+    const double *rs = (const double *)r + s * sd;
+    const double *xs = dkappa_vol ? (const double *)x + s * sd : nullptr;
+    double *ys = (double *)y + s * sd;
+    cudaError_t e;
+    if (df)
+      e = launch_scalar_adjoint<df64>(op->p, geo, op->kappa_vol != nullptr, df64_args(op, true), op->theta, rs, xs,
+                                      ys, (double *)dkappa_vol, (double *)dkappa_face, (df64 *)op->d_rvol,
+                                      (df64 *)op->d_tr, (df64 *)op->d_tr2, (df64 *)op->d_fres, op->cpb, op->fpb,
+                                      (cudaStream_t)stream, s == 0 ? ev : nullptr, 0, 0.0, s > 0);
+    else
+      e = launch_scalar_adjoint<double>(op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, true),
+                                        op->theta, rs, xs, ys, (double *)dkappa_vol, (double *)dkappa_face,
+                                        (double *)op->d_rvol, (double *)op->d_tr, (double *)op->d_tr2,
+                                        (double *)op->d_fres, op->cpb, op->fpb, (cudaStream_t)stream,
+                                        s == 0 ? ev : nullptr, 0, 0.0, s > 0);
+    if (e != cudaSuccess) return fail(DG_ERR_CUDA);
   }
-  cudaError_t e = launch_scalar_adjoint<double>(op->p, geo, op->kappa_vol != nullptr, scalar_args<double>(op, true), op->theta,
-                                        (const double *)r, dkappa_vol ? (const double *)x : nullptr, (double *)y,
-                                        (double *)dkappa_vol, (double *)dkappa_face, (double *)op->d_rvol,
-                                        (double *)op->d_tr, (double *)op->d_tr2, (double *)op->d_fres, op->cpb,
-                                        op->fpb, (cudaStream_t)stream, ev);
-  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
   return DG_OK;
 }
 
@@ -978,13 +998,15 @@ struct Candidate {
   int variant, cpb, fpb;  // cpb: cells per block, row tile (fused) or brick (cellwise)
 };
 
-constexpr double kPeakFP64 = 152 * 2 * 2 * 2.07e9;    // 2 DFMA per SM per clock at 2070 MHz
-constexpr double kPeakFP32 = 152 * 128 * 2 * 2.07e9;  // 128 FFMA per SM per clock
-constexpr double kHBM = 6.6785e12;                     // copy bandwidth measured on this part
+constexpr double kClock = 2.07e9;   // maximum SM clock of this part
+constexpr double kHBM = 6.6785e12;  // copy bandwidth measured on this part
 
 double kernel_cost_ms(double flops, double bytes, const LaunchInfo &q, bool fp64, int p) {
   if (q.blocks_per_sm <= 0 || q.blocks <= 0) return 1e30;
-  const double t = fmax(flops / (fp64 ? kPeakFP64 : kPeakFP32), bytes / kHBM);
+  const double sms = (double)dg_device_sms();
+  // 2 DFMA or 128 FFMA per SM per clock
+  const double peak = sms * (fp64 ? 2.0 * 2.0 : 128.0 * 2.0) * kClock;
+  const double t = fmax(flops / peak, bytes / kHBM);
   const double warps = (double)q.blocks_per_sm * ((q.threads + 31) / 32);
   const double ilp = 1.0 + 0.5 * log2(fmax(1.0, 16.0 / warps));
   const double loads = 1.0 + 0.25 * log2((double)p);
@@ -993,10 +1015,10 @@ double kernel_cost_ms(double flops, double bytes, const LaunchInfo &q, bool fp64
     const double r = (double)q.items / (double)q.blocks;
     tail = ceil(r) / r;
   } else {
-    const double w = (double)q.blocks / ((double)q.blocks_per_sm * 152.0);
+    const double w = (double)q.blocks / ((double)q.blocks_per_sm * sms);
     tail = ceil(w) / w;
   }
-  const double per_block = 50e-9 * (double)(q.items > q.blocks ? q.items : q.blocks) / 152.0;
+  const double per_block = 50e-9 * (double)(q.items > q.blocks ? q.items : q.blocks) / sms;
   return (t * ilp * loads * tail + per_block) * 1e3;
 }
 

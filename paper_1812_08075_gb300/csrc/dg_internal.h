@@ -121,11 +121,13 @@ cudaError_t launch_scalar_apply(int p, int m, int geo, bool kappa, const ScalarA
 // nlmode 1 / 2 (with forward coefficients): the semilinear reaction's residual term
 // beta (r^3, v) / Jacobian term 3 beta (x^2 r, v) added to the volume integral.
 // T = double, or df64 (double-float arithmetic with FP64 vectors, kappa and dkappa).
+// dk_acc: add dkappa to the arrays instead of overwriting them (sum over right-hand sides).
 template <typename T>
 cudaError_t launch_scalar_adjoint(int p, int geo, bool kappa, const ScalarArgs<T> &a, double theta,
                                   const io_t<T> *r, const io_t<T> *x, io_t<T> *y, io_t<T> *dk_vol,
                                   io_t<T> *dk_face, T *rvol, T *tr_r, T *tr_x, T *fres, int cpb, int fpb,
-                                  cudaStream_t s, const cudaEvent_t *ev, int nlmode = 0, double beta = 0.0);
+                                  cudaStream_t s, const cudaEvent_t *ev, int nlmode = 0, double beta = 0.0,
+                                  bool dk_acc = false);
 
 // Persistent single-pass apply for affine meshes (dg_fused.cu): one launch of one wave of
 // blocks that loop over (right-hand side, row of cells) work items; each cell gathers its
@@ -275,6 +277,9 @@ struct dg_operator {
   void *sv_graph_key = nullptr;
 };
 
+
+// Multiprocessors of the current device (1 if the query fails); sizes grids and waves.
+int dg_device_sms();
 
 // Shared by the API and the solver (dg_api.cu).
 dg_status dg_record_error(dg_status s);

@@ -395,7 +395,8 @@ BJTab<P, T> device_tab(const double *tab) {
 // blocks per right-hand side when partials are written
 inline int64_t cell_blocks(int64_t ncell, int nrhs, bool partial, int stride) {
   const int64_t nchunks = (ncell + 127) / 128;
-  int64_t nb = (16 * 152) / nrhs > 0 ? (16 * 152) / nrhs : 1;
+  const int64_t wave = 16 * (int64_t)dg_device_sms();
+  int64_t nb = wave / nrhs > 0 ? wave / nrhs : 1;
   if (partial && nb > stride) nb = stride;
   return nb > nchunks ? nchunks : nb;
 }
@@ -428,7 +429,8 @@ cudaError_t run_bj(const double *tab, const T *dinv, int nx, int ny, int nz, int
   const size_t sm = 2 * (size_t)cpb * P * P * P * sizeof(T);
   // one wave of 8 blocks per SM over the right-hand sides, at most `stride` per rhs
   const int64_t ngroups = (ncell + cpb - 1) / cpb;
-  int64_t nb = (8 * 152) / nrhs > 0 ? (8 * 152) / nrhs : 1;
+  const int64_t wave = 8 * (int64_t)dg_device_sms();
+  int64_t nb = wave / nrhs > 0 ? wave / nrhs : 1;
   if (partial && nb > stride) nb = stride;
   if (nb > ngroups) nb = ngroups;
   if (blocks) *blocks = (int)nb;

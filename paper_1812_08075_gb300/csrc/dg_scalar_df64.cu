@@ -17,6 +17,7 @@ __global__ void k_to_df64(const double *__restrict__ in, df64 *__restrict__ out,
 cudaError_t convert_to_df64(const double *in, df64 *out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t want = (n + 255) / 256;
-  k_to_df64<<<(unsigned)(want < 152 * 32 ? want : 152 * 32), 256, 0, s>>>(in, out, n);
+  const int64_t cap = 32 * (int64_t)dg_device_sms();
+  k_to_df64<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }

@@ -13,6 +13,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "dg_internal.h"
 
 namespace {
@@ -23,7 +25,10 @@ struct Scalars {  // device, one entry per right-hand side
 };
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = 152 * 16;  // grid of the vector kernels (fixed per size: fixed reduction order)
+// Row stride of the per-block partial sums: room for the largest grid of the vector
+// kernels (16 blocks per SM, up to 256 SMs). The grid is fixed per vector size and device,
+// so the reduction order is too.
+constexpr int kMaxBlocks = 4096;
 
 // Scalars followed by per-block partial sums [16 rhs][kMaxBlocks] of the reductions.
 struct Workspace {
@@ -332,7 +337,8 @@ __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, 
 
 unsigned grid_for(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
-  return (unsigned)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
+  const int64_t cap = std::min<int64_t>(16 * (int64_t)dg_device_sms(), kMaxBlocks);
+  return (unsigned)(g > cap ? cap : (g < 1 ? 1 : g));
 }
 
 // Blocks per right-hand side of the reducing vector kernels: one wave of 8 blocks per SM
@@ -340,7 +346,7 @@ unsigned grid_for(int64_t n) {
 // FP64 reduction tree (FP64 add throughput is scarce on this part; a reduction per few
 // elements would cost more than the vector traffic itself).
 unsigned grid_vec(int64_t n, int nrhs) {
-  const int64_t wave = 8 * 152;
+  const int64_t wave = std::min<int64_t>(8 * (int64_t)dg_device_sms(), kMaxBlocks);
   int64_t g = (n + kThreads - 1) / kThreads;
   const int64_t cap = wave / nrhs > 1 ? wave / nrhs : 1;
   return (unsigned)(g > cap ? cap : (g < 1 ? 1 : g));

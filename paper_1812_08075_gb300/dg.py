@@ -33,7 +33,7 @@ EXPORTED = [
     "dg_apply_affine_static", "dg_cg_solve", "dg_refine_solve", "dg_operator_set_variant",
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
     "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
-    "dg_operator_create_aniso", "dg_mixed_cg_solve",
+    "dg_operator_create_aniso", "dg_mixed_cg_solve", "dg_measure_fma_peak",
 ]
 
 
@@ -101,7 +101,7 @@ def lib():
         L.dg_operator_set_kappa.argtypes = [vp, vp, vp]
         L.dg_apply.argtypes = [vp, vp, vp, i32, vp]
         L.dg_apply_host.argtypes = [vp, vp, vp, i32, vp]
-        L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.dg_apply_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
         L.dg_reference_tables.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.dg_operator_profile.argtypes = [vp, i32]
         L.dg_operator_set_variant.argtypes = [vp, i32, i32, i32]
@@ -122,6 +122,7 @@ def lib():
                                       ctypes.POINTER(dg_solve_info), vp]
         L.dg_apply_affine_static.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              i32, vp, vp, vp]
+        L.dg_measure_fma_peak.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
         for name in EXPORTED:
             if name not in ("dg_status_string",):
@@ -201,8 +202,10 @@ def dg_apply_host(op: int, x_ptr: int, y_ptr: int, nrhs: int, stream: Optional[i
 
 
 def dg_apply_adjoint(op: int, r_ptr: int, x_ptr: Optional[int], y_ptr: int, dk_vol_ptr: Optional[int],
-                     dk_face_ptr: Optional[int], stream: Optional[int]):
-    _check(lib().dg_apply_adjoint(op, r_ptr, x_ptr, y_ptr, dk_vol_ptr, dk_face_ptr, stream), "dg_apply_adjoint")
+                     dk_face_ptr: Optional[int], stream: Optional[int], nrhs: int = 1):
+    """y_s = A^T r_s for nrhs vectors; dkappa summed over the right-hand sides."""
+    _check(lib().dg_apply_adjoint(op, r_ptr, x_ptr, y_ptr, dk_vol_ptr, dk_face_ptr, nrhs, stream),
+           "dg_apply_adjoint")
 
 
 def dg_apply_affine_static(nx: int, ny: int, nz: int, degree: int, c: float, theta: float, penalty_alpha: float,
@@ -297,6 +300,13 @@ def dg_operator_kernel_times(op: int):
     n = ctypes.c_int64()
     _check(lib().dg_operator_kernel_times(op, ctypes.byref(ms), ctypes.byref(n)), "dg_operator_kernel_times")
     return list(ms), n.value
+
+
+def dg_measure_fma_peak(precision: int, stream: Optional[int] = None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU in FP64 or FP32."""
+    t = ctypes.c_double()
+    _check(lib().dg_measure_fma_peak(precision, stream, ctypes.byref(t)), "dg_measure_fma_peak")
+    return t.value
 
 
 def dg_reference_tables(degree: int, m: int = 0):

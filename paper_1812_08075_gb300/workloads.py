@@ -66,10 +66,35 @@ def lognormal_kappa(ncell: int, m: int, seed: int = 2, sigma: float = 0.5):
     return k[:nv].copy(), k[nv:].copy()
 
 
+def sin_product_source(nx: int, ny: int, nz: int, nodes) -> np.ndarray:
+    """The smooth source f = sin(pi x) sin(pi y) sin(pi z) of the mixed-precision solve,
+    evaluated at the volume points of the uniform unit-cube lattice: cell c's point q is
+    ((cx + s_q0)/nx, (cy + s_q1)/ny, (cz + s_q2)/nz) for the caller's 1D points s on [0,1]
+    (its own quadrature nodes). Layout [ncell][m^3], q = q0 + m (q1 + m q2)."""
+    s = np.asarray(nodes, dtype=np.float64)
+    m = s.size
+    gx = np.sin(np.pi * (np.arange(nx)[:, None] + s[None, :]) / nx)
+    gy = np.sin(np.pi * (np.arange(ny)[:, None] + s[None, :]) / ny)
+    gz = np.sin(np.pi * (np.arange(nz)[:, None] + s[None, :]) / nz)
+    f = (gz.reshape(nz, 1, 1, m, 1, 1) * gy.reshape(1, ny, 1, 1, m, 1)) * gx.reshape(1, 1, nx, 1, 1, m)
+    return np.ascontiguousarray(f).reshape(-1)
+
+
+def projected_rhs(load, seeds, dtype=np.float64) -> np.ndarray:
+    """Right-hand sides b_s = l / max|l| + eta_s of the mixed-precision solve, with l the
+    load vector (f, phi_i) of ``sin_product_source`` (integrated by the caller's own
+    quadrature) and eta_s ~ U[-1,1] from seed s. Shape [len(seeds), l.size]."""
+    l = np.asarray(load, dtype=np.float64)
+    l = l / np.abs(l).max()
+    out = np.empty((len(seeds), l.size), dtype=dtype)
+    for i, sd in enumerate(seeds):
+        out[i] = l + uniform_vector(l.size, sd)
+    return out
+
+
 def cell_centre_sin_source(nx: int, ny: int, nz: int, ndof_per_cell: int) -> np.ndarray:
-    """Smooth part of the mixed-precision solve's right-hand sides: the product
-    sin(pi x) sin(pi y) sin(pi z) at each cell's centre, repeated over the cell's DOFs
-    (the unit-cube lattice, no basis or quadrature involved)."""
+    """A smooth test vector: sin(pi x) sin(pi y) sin(pi z) at each cell's centre, repeated
+    over the cell's DOFs (the unit-cube lattice, no basis or quadrature involved)."""
     cx = (np.arange(nx) + 0.5) / nx
     cy = (np.arange(ny) + 0.5) / ny
     cz = (np.arange(nz) + 0.5) / nz
@@ -79,14 +104,10 @@ def cell_centre_sin_source(nx: int, ny: int, nz: int, ndof_per_cell: int) -> np.
 
 
 def refinement_rhs(nx: int, ny: int, nz: int, ndof_per_cell: int, seeds, dtype=np.float64) -> np.ndarray:
-    """Right-hand sides b_s = l / max|l| + eta_s, eta_s ~ U[-1,1] from seed s.
-    Shape [len(seeds), ncell*ndof_per_cell]."""
-    l = cell_centre_sin_source(nx, ny, nz, ndof_per_cell)
-    l = l / np.abs(l).max()
-    out = np.empty((len(seeds), l.size), dtype=dtype)
-    for i, s in enumerate(seeds):
-        out[i] = l + uniform_vector(l.size, s)
-    return out
+    """Smooth-plus-noise test vectors b_s = v / max|v| + eta_s with v the cell-centre
+    sin-product above and eta_s ~ U[-1,1] from seed s (generic solver inputs that need
+    no quadrature). Shape [len(seeds), ncell*ndof_per_cell]."""
+    return projected_rhs(cell_centre_sin_source(nx, ny, nz, ndof_per_cell), seeds, dtype)
 
 
 def sample_cells(ncell: int, count: int, seed: int = 7) -> np.ndarray:

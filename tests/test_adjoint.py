@@ -49,7 +49,7 @@ def test_transpose_and_dkappa_vs_oracle(k, geom, theta):
     y = torch.empty_like(xd)
     dkv = torch.empty(kv.size, dtype=torch.float64, device="cuda")
     dkf = torch.empty(kf.size, dtype=torch.float64, device="cuda")
-    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None, nrhs=1)
     torch.cuda.synchronize()
     assert relerr(y.cpu().numpy(), orc.apply(r, transpose=True)) <= TOL64
     rv, rf = orc.dkappa(x, r)
@@ -57,7 +57,7 @@ def test_transpose_and_dkappa_vs_oracle(k, geom, theta):
     assert relerr(dkf.cpu().numpy(), rf) <= TOL64
     # transpose only (no x): same y
     y2 = torch.empty_like(xd)
-    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y2.data_ptr(), None, None, None)
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y2.data_ptr(), None, None, None, nrhs=1)
     assert torch.equal(y, y2)
 
 
@@ -65,7 +65,7 @@ def test_adjoint_without_kappa_equals_forward_for_sipg():
     op, orc, _, _ = setup((3, 4, 3), 3, "trilinear", kappa=False)
     r = torch.from_numpy(wl.uniform_vector(op.ndofs, 4)).cuda()
     y = torch.empty_like(r)
-    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, y.data_ptr(), None, None, None)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, y.data_ptr(), None, None, None, nrhs=1)
     fwd = op.apply(r)
     assert relerr(y.cpu().numpy(), fwd.cpu().numpy()) <= TOL64
 
@@ -105,7 +105,7 @@ def test_finite_differences_full_config5():
     gx = torch.empty_like(x)
     gkv = torch.empty_like(tkv)
     gkf = torch.empty_like(tkf)
-    dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), gx.data_ptr(), gkv.data_ptr(), gkf.data_ptr(), None)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), gx.data_ptr(), gkv.data_ptr(), gkf.data_ptr(), None, nrhs=1)
     h = 1e-6
     rng = np.random.default_rng(9)
 
@@ -147,7 +147,7 @@ def fd_gradient_check(op, x, b, idxs, h=1e-6):
     differences of L = 0.5 ||A x - b||^2 (formed from y+ - y- so that nothing cancels)."""
     r = op.apply(x) - b
     g = torch.empty_like(x)
-    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g.data_ptr(), None, None, None)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g.data_ptr(), None, None, None, nrhs=1)
     worst = 0.0
     for idx in idxs:
         xp, xm = x.clone(), x.clone()
@@ -184,7 +184,7 @@ def test_stokes_adjoint_matches_oracle_transpose():
         r = wl.uniform_vector(op.ndofs, 2)
         y = torch.empty(op.ndofs, dtype=torch.float64, device="cuda")
         rd = torch.from_numpy(r).cuda()
-        dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y.data_ptr(), None, None, None)
+        dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y.data_ptr(), None, None, None, nrhs=1)
         assert relerr(y.cpu().numpy(), orc.apply(r, transpose=True)) <= TOL64
 
 
@@ -210,8 +210,103 @@ def test_finite_differences_config4_and_fp32_transpose():
     op32 = dg.Operator(dg.Mesh(*n), 2, precision=dg.DG_FP32)
     r = b
     g64 = torch.empty_like(r)
-    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g64.data_ptr(), None, None, None)
+    dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, g64.data_ptr(), None, None, None, nrhs=1)
     r32 = r.float()
     g32 = torch.empty_like(r32)
-    dg.dg_apply_adjoint(op32.handle, r32.data_ptr(), None, g32.data_ptr(), None, None, None)
+    dg.dg_apply_adjoint(op32.handle, r32.data_ptr(), None, g32.data_ptr(), None, None, None, nrhs=1)
     assert float((g32.double() - g64).abs().max() / g64.abs().max()) <= 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [3, 16])
+@pytest.mark.parametrize("geom", ["affine", "trilinear"])
+def test_multi_rhs_adjoint_vs_oracle(nrhs, geom):
+    """nrhs right-hand sides in one call: y_s = A^T r_s per right-hand side against the
+    oracle's transposed apply, and dkappa against the oracle's derivative summed over s
+    (the gradient of the summed loss)."""
+    n, k = (4, 3, 5), 3
+    verts = wl.perturbed_vertices(*n, seed=1) if geom == "trilinear" else None
+    op = dg.Operator(dg.Mesh(*n, verts), k, theta=1.0, dirichlet_mask=0b101111, max_rhs=nrhs)
+    orc = oracle.Problem(*n, k, vertices=verts, theta=1.0, dirichlet_mask=0b101111)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    orc.kappa_vol, orc.kappa_face = kv, kf
+    op.set_kappa(torch.from_numpy(kv).cuda(), torch.from_numpy(kf).cuda())
+    X = np.stack([wl.uniform_vector(op.ndofs, 30 + s) for s in range(nrhs)])
+    R = np.stack([wl.uniform_vector(op.ndofs, 60 + s) for s in range(nrhs)])
+    xd, rd = torch.from_numpy(X).cuda(), torch.from_numpy(R).cuda()
+    y = torch.full_like(xd, float("nan"))
+    dkv = torch.full((kv.size,), float("nan"), dtype=torch.float64, device="cuda")
+    dkf = torch.full((kf.size,), float("nan"), dtype=torch.float64, device="cuda")
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None,
+                        nrhs=nrhs)
+    torch.cuda.synchronize()
+    yh = y.cpu().numpy()
+    sv, sf = np.zeros(kv.size), np.zeros(kf.size)
+    for s in range(nrhs):
+        assert relerr(yh[s], orc.apply(R[s], transpose=True)) <= TOL64, s
+        rv, rf = orc.dkappa(X[s], R[s])
+        sv += rv
+        sf += rf
+    assert relerr(dkv.cpu().numpy(), sv) <= TOL64
+    assert relerr(dkf.cpu().numpy(), sf) <= TOL64
+
+
+def test_multi_rhs_adjoint_rejects_more_than_max_rhs():
+    op = dg.Operator(dg.Mesh(2, 2, 2), 2, max_rhs=2)
+    r = torch.zeros(3 * op.ndofs, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(r)
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_apply_adjoint(op.handle, r.data_ptr(), None, y.data_ptr(), None, None, None, nrhs=3)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("problem", ["stokes", "fp32"])
+def test_multi_rhs_transpose_without_kappa(problem):
+    """Stokes and FP32 operators: y_s = A^T r_s for 3 right-hand sides in one call, each
+    against the single-vector call (Stokes: and the oracle's transpose)."""
+    nrhs = 3
+    if problem == "stokes":
+        n, k = (3, 2, 3), 3
+        op = dg.Operator(dg.Mesh(*n), k, problem=dg.DG_STOKES, dirichlet_mask=0b111101, theta=1.0, max_rhs=nrhs)
+        orc = oracle.Problem(*n, k, problem="stokes", dirichlet_mask=0b111101, theta=1.0)
+    else:
+        n, k = (4, 3, 5), 2
+        op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, theta=1.0, max_rhs=nrhs)
+        orc = None
+    R = np.stack([wl.uniform_vector(op.ndofs, 90 + s) for s in range(nrhs)])
+    rd = torch.from_numpy(R).to("cuda", op.dtype)
+    y = torch.empty_like(rd)
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), None, y.data_ptr(), None, None, None, nrhs=nrhs)
+    for s in range(nrhs):
+        ys = torch.empty_like(rd[s])
+        dg.dg_apply_adjoint(op.handle, rd[s].data_ptr(), None, ys.data_ptr(), None, None, None, nrhs=1)
+        assert torch.equal(ys, y[s]), s
+        if orc is not None:
+            assert relerr(y[s].cpu().numpy(), orc.apply(R[s], transpose=True)) <= TOL64
+
+
+def test_autograd_batched_x_sums_dkappa():
+    """DGApply with x of shape [nrhs, ndofs]: dL/dx per right-hand side and dL/dkappa summed,
+    against the oracle's transposed apply and pointwise derivative."""
+    n, k, nrhs = (3, 4, 3), 2, 4
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, max_rhs=nrhs)
+    orc = oracle.Problem(*n, k, vertices=verts)
+    kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+    orc.kappa_vol, orc.kappa_face = kv, kf
+    X = np.stack([wl.uniform_vector(op.ndofs, 5 + s) for s in range(nrhs)])
+    B = np.stack([wl.uniform_vector(op.ndofs, 50 + s) for s in range(nrhs)])
+    x = torch.from_numpy(X).cuda().requires_grad_(True)
+    tkv = torch.from_numpy(kv).cuda().requires_grad_(True)
+    tkf = torch.from_numpy(kf).cuda().requires_grad_(True)
+    y = dg_apply_ad(op, x, tkv, tkf)
+    loss = 0.5 * ((y - torch.from_numpy(B).cuda()) ** 2).sum()
+    loss.backward()
+    sv, sf = np.zeros(kv.size), np.zeros(kf.size)
+    for s in range(nrhs):
+        r = orc.apply(X[s]) - B[s]
+        assert relerr(x.grad[s].cpu().numpy(), orc.apply(r, transpose=True)) <= TOL64
+        rv, rf = orc.dkappa(X[s], r)
+        sv += rv
+        sf += rf
+    assert relerr(tkv.grad.cpu().numpy(), sv) <= TOL64
+    assert relerr(tkf.grad.cpu().numpy(), sf) <= TOL64

@@ -184,7 +184,7 @@ def test_df64_adjoint_and_dkappa_match_oracle(k, geom, theta):
     y = torch.empty_like(xd)
     dkv = torch.empty(kv.size, dtype=torch.float64, device="cuda")
     dkf = torch.empty(kf.size, dtype=torch.float64, device="cuda")
-    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+    dg.dg_apply_adjoint(op.handle, rd.data_ptr(), xd.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None, nrhs=1)
     torch.cuda.synchronize()
     rv, rf = orc.dkappa(x, r)
     errs = (relerr(y.cpu().numpy(), orc.apply(r, transpose=True)), relerr(dkv.cpu().numpy(), rv),
@@ -220,7 +220,7 @@ def test_df64_adjoint_agrees_with_fp64_at_config5_scale():
         op.set_variant(v)
         y = torch.empty_like(x)
         dkv, dkf = torch.empty_like(tk[0]), torch.empty_like(tk[1])
-        dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None)
+        dg.dg_apply_adjoint(op.handle, r.data_ptr(), x.data_ptr(), y.data_ptr(), dkv.data_ptr(), dkf.data_ptr(), None, nrhs=1)
         out[v] = (y, dkv, dkf)
     a, b = out[dg.DG_VARIANT_THREE_KERNEL], out[dg.DG_VARIANT_DF64]
     errs = [float((q - p).abs().max() / p.abs().max()) for p, q in zip(a, b)]
