@@ -134,18 +134,24 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
                              dg_operator **out);
 dg_status dg_operator_destroy(dg_operator *op);
 
-/* Scalar operator with anisotropic degrees (Sec. 2.1's vector k): degrees[a] = k_a in 1..5
- * per direction, k_a + 1 GLL basis points and k_a + 1 Gauss points per direction, cell DOFs
- * j0 + p0 (j1 + p1 j2), the face penalty taking the degree along the face normal
- * (DG_PEN_CONFIG: alpha k_a (k_a + 1) / h_a; DG_PEN_PAPER: alpha k_a (k_a + 2) / h_a on the
- * uniform lattice). Affine meshes (vertices NULL) and the scalar problem only; the apply runs
- * the three-kernel structure with run-time extents. dg_apply, dg_apply_host, dg_operator_stats
- * and unpreconditioned dg_cg_solve / dg_refine_solve accept it; kappa, the adjoint, dg_rhs,
- * dg_apply_semilinear, the preconditioners, variants and the tuners return
- * DG_ERR_UNSUPPORTED. Errors: DG_ERR_INVALID_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
+/* Scalar operator with anisotropic degrees and quadrature (Sec. 2.1: a degree k_a and a
+ * Gauss rule of m_a points per direction; Sec. 4 raises m on purpose): degrees[a] = k_a in
+ * 1..5, quad_points[a] = m_a with k_a + 1 <= m_a <= 7 (NULL or 0 entries: m_a = k_a + 1);
+ * k_a + 1 GLL basis points per direction, cell DOFs j0 + p0 (j1 + p1 j2). The face penalty
+ * takes the degree along the face normal (DG_PEN_CONFIG: alpha k_a (k_a + 1) / h_a;
+ * DG_PEN_PAPER: alpha k_a (k_a + 2) / h_a, affine meshes only). Affine meshes and trilinear
+ * meshes (geometry recomputed from the vertex coordinates at every point inside the
+ * kernels; nothing stored), the scalar problem, FP64 or FP32. kappa (dg_operator_set_kappa)
+ * then uses the per-direction layouts kappa_vol [ncell][m0 m1 m2] (q0 + m0 (q1 + m1 q2))
+ * and kappa_face [ncell][sum over lf = 0..5 of m_t1 m_t2] (faces in order, points qs + m_t1 qt
+ * over the tangential axes t1 < t2). The apply runs the three-kernel structure with run-time
+ * extents. dg_apply, dg_apply_host, dg_operator_stats and unpreconditioned dg_cg_solve /
+ * dg_refine_solve accept it; the adjoint, dg_rhs, dg_apply_semilinear, the preconditioners,
+ * variants and the tuners return DG_ERR_UNSUPPORTED. Errors: DG_ERR_INVALID_ARG (k_a or m_a
+ * out of range), DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3],
-                                   const dg_penalty *penalty, const dg_coefficients *coef,
-                                   dg_operator **out);
+                                   const int32_t quad_points[3], const dg_penalty *penalty,
+                                   const dg_coefficients *coef, dg_operator **out);
 
 /* Number of DOFs of one vector of this operator. */
 dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n);
@@ -237,7 +243,8 @@ dg_status dg_operator_time(const dg_operator *op, int nrhs, int variant, int cel
 dg_status dg_operator_autotune_prior(dg_operator *op, int nrhs, int measure, void *stream,
                                      dg_tune_result *out);
 
-/* Per-quadrature-point diffusion coefficient kappa (scalar problem): device arrays of
+/* Per-quadrature-point diffusion coefficient kappa (scalar problem; anisotropic operators:
+ * the per-direction layouts of dg_operator_create_aniso): device arrays of
  * the operator's precision, kappa_vol [ncell][m^3] (points q0 + m(q1 + m q2)) and
  * kappa_face [ncell][6][m^2] (each cell's own side of faces -x,+x,-y,+y,-z,+z, points
  * qs + m*qt over the two tangential axes in increasing order). NULL = 1. The arrays
@@ -433,6 +440,14 @@ dg_status dg_operator_kernel_times(dg_operator *op, double ms[3], int64_t *nappl
  * TFLOP/s (FMA = 2 flops). Allocates and frees a small output buffer; synchronises the
  * stream. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_measure_fma_peak(int precision, void *stream, double *tflops);
+
+/* Measured tensor-core throughput for measurement harnesses, with the same protocol as
+ * dg_measure_fma_peak: kind 0 = FP64 mma.sync m8n8k4 (DMMA), kind 1 = TF32 mma.sync
+ * m16n8k8 with FP32 accumulation; every warp keeps four independent accumulations in
+ * flight. *tflops in TFLOP/s (one multiply-add = 2 flops). These decide whether the
+ * batched 1D contractions of the sum factorisation (Sec. 2.2) could gain from the tensor
+ * cores of this part. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_measure_mma_peak(int kind, void *stream, double *tflops);
 
 /* Reference-element tables the CUDA path uses (host, double), for inspection:
  * gauss_nodes/weights [m] on [0,1], gll_nodes [k+1], interp [m][k+1] (GLL Lagrange

@@ -45,7 +45,7 @@ class _Problem(ctypes.Structure):
         ("c", ctypes.c_double), ("mu", ctypes.c_double), ("theta", ctypes.c_double),
         ("pen_alpha", ctypes.c_double),
         ("vertices", ctypes.c_void_p), ("kappa_vol", ctypes.c_void_p), ("kappa_face", ctypes.c_void_p),
-        ("kaxis", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
+        ("kaxis", ctypes.c_int32 * 3), ("maxis", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -112,7 +112,8 @@ class Problem:
     vertices: Optional[np.ndarray] = None
     kappa_vol: Optional[np.ndarray] = None
     kappa_face: Optional[np.ndarray] = None
-    degrees: Optional[tuple] = None  # anisotropic (k_0, k_1, k_2): scalar, k_a + 1 points, kappa = 1
+    degrees: Optional[tuple] = None  # anisotropic (k_0, k_1, k_2): scalar problem
+    quad: Optional[tuple] = None     # with degrees: Gauss points (m_0, m_1, m_2), None = k_a + 1
 
     def __post_init__(self):
         if self.m is None:
@@ -141,7 +142,8 @@ class Problem:
         s = _Problem(self.nx, self.ny, self.nz, self.k, self.m, self.pen_mode, self.dirichlet_mask,
                      0 if self.problem == "scalar" else 1, self.c, self.mu, self.theta, self.pen_alpha,
                      arr(self.vertices), arr(self.kappa_vol), arr(self.kappa_face),
-                     (ctypes.c_int32 * 3)(*(self.degrees or (0, 0, 0))), 0)
+                     (ctypes.c_int32 * 3)(*(self.degrees or (0, 0, 0))),
+                     (ctypes.c_int32 * 3)(*(self.quad or (0, 0, 0))), 0)
         return s, keep
 
     def ndofs(self) -> int:

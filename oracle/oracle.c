@@ -118,7 +118,11 @@ typedef struct {
   int aniso;
   int ka[3], pa[3], ma[3];
   double sa[3][OMAXM], wa[3][OMAXM], za[3][OMAXP];
+  /* kappa layouts: volume points per cell; face points per cell and face offsets */
+  int nqv, nqf, fo[7];
 } octx;
+
+static void tangential_axes(int a, int *t1, int *t2);
 
 static int ctx_init(octx *o, const oracle_problem *pb) {
   memset(o, 0, sizeof(*o));
@@ -138,10 +142,11 @@ static int ctx_init(octx *o, const oracle_problem *pb) {
   for (int d = 0; d < 3; ++d) {
     if (o->aniso) {
       const int kd = pb->kaxis[d];
-      if (kd < 1 || kd + 1 > OMAXP || kd + 1 > OMAXM || pb->problem != 0 || pb->kappa_vol || pb->kappa_face) return 1;
+      const int md = pb->maxis[d] ? pb->maxis[d] : kd + 1;
+      if (kd < 1 || kd + 1 > OMAXP || md < 1 || md > OMAXM || pb->problem != 0) return 1;
       o->ka[d] = kd;
       o->pa[d] = kd + 1;
-      o->ma[d] = kd + 1;
+      o->ma[d] = md;
       if (oracle_gauss_rule(o->ma[d], o->sa[d], o->wa[d])) return 1;
       if (oracle_gll_nodes(kd, o->za[d])) return 1;
     } else {
@@ -154,6 +159,14 @@ static int ctx_init(octx *o, const oracle_problem *pb) {
     }
   }
   if (o->aniso) o->P3 = o->pa[0] * o->pa[1] * o->pa[2];
+  o->nqv = o->ma[0] * o->ma[1] * o->ma[2];
+  o->fo[0] = 0;
+  for (int lf = 0; lf < 6; ++lf) {
+    int t1, t2;
+    tangential_axes(lf >> 1, &t1, &t2);
+    o->fo[lf + 1] = o->fo[lf] + o->ma[t1] * o->ma[t2];
+  }
+  o->nqf = o->fo[6];
   if (pb->problem == 1) {
     o->pp = pb->k; /* pressure degree k-1 */
     if (oracle_gll_nodes(pb->k - 1, o->zp)) return 1;
@@ -337,7 +350,7 @@ static double penalty(const octx *o, int a, int64_t cm, int sidem, int64_t cp) {
 static void vol_scalar(const octx *o, int64_t c, const double *xe, double *ye) {
   double V[8][3], J[3][3], Ji[3][3], xi[3];
   static __thread double phi[OMAXP3], g[OMAXP3][3];
-  const int P3 = o->P3, m = o->m;
+  const int P3 = o->P3;
   cell_vertices(o, c, V);
   for (int q2 = 0; q2 < o->ma[2]; ++q2)
     for (int q1 = 0; q1 < o->ma[1]; ++q1)
@@ -353,8 +366,8 @@ static void vol_scalar(const octx *o, int64_t c, const double *xe, double *ye) {
           u += xe[j] * phi[j];
           for (int i = 0; i < 3; ++i) gu[i] += xe[j] * g[j][i];
         }
-        int q = q0 + m * (q1 + m * q2);
-        double kap = o->pb->kappa_vol ? o->pb->kappa_vol[c * m * m * m + q] : 1.0;
+        int q = q0 + o->ma[0] * (q1 + o->ma[1] * q2);
+        double kap = o->pb->kappa_vol ? o->pb->kappa_vol[c * o->nqv + q] : 1.0;
         double cr = o->pb->c;
         for (int i = 0; i < P3; ++i)
           ye[i] += W * dJ * (kap * (gu[0] * g[i][0] + gu[1] * g[i][1] + gu[2] * g[i][2]) + cr * u * phi[i]);
@@ -397,7 +410,9 @@ static void side_eval(const octx *o, int64_t c, int a, int side, int qs, int qt,
 
 static double kappa_face_at(const octx *o, int64_t c, int lf, int qs, int qt) {
   if (!o->pb->kappa_face) return 1.0;
-  return o->pb->kappa_face[(c * 6 + lf) * o->m * o->m + qs + o->m * qt];
+  int t1, t2;
+  tangential_axes(lf >> 1, &t1, &t2);
+  return o->pb->kappa_face[c * o->nqf + o->fo[lf] + qs + o->ma[t1] * qt];
 }
 
 /* Face terms of Eq. (diffreac_weak) on one face. cp < 0: boundary face of cm at

@@ -56,8 +56,13 @@ typedef struct {
   const double *kappa_vol;  /* [ncell][m^3] or NULL (kappa = 1) */
   const double *kappa_face; /* [ncell][6][m^2] or NULL (kappa = 1) */
   int32_t kaxis[3];       /* anisotropic degrees (k_0, k_1, k_2), all >= 1, or all 0 for k in
-                             every direction; anisotropic: scalar problem, k_a + 1 Gauss points
-                             per direction, kappa = 1, cell DOFs j0 + p0 (j1 + p1 j2) */
+                             every direction; anisotropic: scalar problem, cell DOFs
+                             j0 + p0 (j1 + p1 j2) */
+  int32_t maxis[3];       /* with kaxis: Gauss points per direction (m_0, m_1, m_2), 0 = k_a + 1.
+                             kappa layouts then follow the per-direction counts:
+                             kappa_vol [ncell][m0 m1 m2] (q0 + m0 (q1 + m1 q2)),
+                             kappa_face [ncell][sum over lf of m_t1 m_t2], faces lf = 0..5 in
+                             order, face points qs + m_t1 qt (t1 < t2 the tangential axes) */
   int32_t reserved;
 } oracle_problem;
 

@@ -235,8 +235,18 @@ static int resolve_variant(const dg_operator *o, int v) {
 
 extern "C" {
 
+// any_recompute: also FP32 with recomputed trilinear geometry (the anisotropic operator,
+// whose kernels recompute it themselves, uses the isotropic one only for its bookkeeping).
+static dg_status create_impl(const dg_mesh *mesh, int degree, int quad_points_1d, const dg_penalty *pen,
+                             const dg_coefficients *co, dg_operator **out, bool any_recompute);
+
 dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d, const dg_penalty *pen,
                              const dg_coefficients *co, dg_operator **out) {
+  return create_impl(mesh, degree, quad_points_1d, pen, co, out, false);
+}
+
+static dg_status create_impl(const dg_mesh *mesh, int degree, int quad_points_1d, const dg_penalty *pen,
+                             const dg_coefficients *co, dg_operator **out, bool any_recompute) {
   if (!mesh || !pen || !co || !out) return fail(DG_ERR_INVALID_ARG);
   *out = nullptr;
   if (degree < 1) return fail(DG_ERR_INVALID_ARG);
@@ -251,7 +261,7 @@ dg_status dg_operator_create(const dg_mesh *mesh, int degree, int quad_points_1d
   if (pen->mode != DG_PEN_CONFIG && pen->mode != DG_PEN_PAPER) return fail(DG_ERR_INVALID_ARG);
   if (co->dirichlet_mask < 0 || co->dirichlet_mask > 63) return fail(DG_ERR_INVALID_ARG);
   if (co->geometry < DG_GEOM_AUTO || co->geometry > DG_GEOM_RECOMPUTE) return fail(DG_ERR_INVALID_ARG);
-  if (co->geometry == DG_GEOM_RECOMPUTE && !mesh->affine &&
+  if (co->geometry == DG_GEOM_RECOMPUTE && !mesh->affine && !any_recompute &&
       (co->precision != DG_FP64 || co->problem != DG_SCALAR || m != degree + 1))
     return fail(DG_ERR_UNSUPPORTED);
 
@@ -349,37 +359,65 @@ dg_status dg_operator_destroy(dg_operator *op) {
   return DG_OK;
 }
 
-dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3], const dg_penalty *pen,
-                                   const dg_coefficients *co, dg_operator **out) {
+dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3], const int32_t quad_points[3],
+                                   const dg_penalty *pen, const dg_coefficients *co, dg_operator **out) {
   if (!mesh || !degrees || !pen || !co || !out) return fail(DG_ERR_INVALID_ARG);
-  int kmax = 0;
+  int kmax = 0, mq[3];
   for (int a = 0; a < 3; ++a) {
     if (degrees[a] < 1 || degrees[a] + 1 > DG_MAXP) return fail(DG_ERR_INVALID_ARG);
     kmax = degrees[a] > kmax ? degrees[a] : kmax;
+    mq[a] = (quad_points && quad_points[a]) ? quad_points[a] : degrees[a] + 1;
+    if (mq[a] < degrees[a] + 1) return fail(DG_ERR_INVALID_ARG);
+    if (mq[a] > DG_MAXM) return fail(DG_ERR_UNSUPPORTED);
   }
-  if (!mesh->affine || co->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
-  // an isotropic operator of the largest degree supplies the mesh bookkeeping and scratch
-  // large enough for every per-direction size (p0 p1 p2 <= (k_max+1)^3, likewise the traces)
-  dg_status st = dg_operator_create(mesh, kmax, 0, pen, co, out);
+  if (co->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
+  // the paper's penalty needs face and cell measures by the anisotropic rule: affine only
+  if (!mesh->affine && pen->mode != DG_PEN_CONFIG) return fail(DG_ERR_UNSUPPORTED);
+  // an isotropic operator of the largest degree supplies the mesh bookkeeping (vertices,
+  // face numbering); trilinear geometry is recomputed by the anisotropic kernels, so none
+  // is stored, and the scratch is reallocated below for the per-direction sizes
+  dg_coefficients co2 = *co;
+  co2.geometry = DG_GEOM_RECOMPUTE;
+  dg_status st = create_impl(mesh, kmax, 0, pen, &co2, out, true);
   if (st != DG_OK) return st;
   dg_operator *o = *out;
   HostTables ht[3];
   const int n[3] = {o->nx, o->ny, o->nz};
-  int npts = 1;
+  int npts = 1, nq = 1;
   for (int a = 0; a < 3; ++a) {
     const int k = degrees[a];
-    if (dg_build_tables(k, k + 1, false, &ht[a])) { free_op(o); *out = nullptr; return fail(DG_ERR_UNSUPPORTED); }
+    if (dg_build_tables(k, mq[a], false, &ht[a])) { free_op(o); *out = nullptr; return fail(DG_ERR_UNSUPPORTED); }
     o->kax[a] = k;
+    o->max_q[a] = mq[a];
     // the penalty of a face takes the degree along its normal
     o->gamma_axis[a] = pen->mode == DG_PEN_CONFIG ? pen->alpha * k * (k + 1) * n[a] : pen->alpha * k * (k + 2) * n[a];
     npts *= k + 1;
+    nq *= mq[a];
   }
   const bool f64 = o->precision == DG_FP64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
   std::vector<unsigned char> host(f64 ? aniso_tab_bytes<double>() : aniso_tab_bytes<float>());
   int ts = 0;
-  if ((f64 ? aniso_tables<double>(ht, host.data(), &ts) : aniso_tables<float>(ht, host.data(), &ts)) != 0 ||
-      cudaMalloc(&o->d_antab, host.size()) != cudaSuccess ||
-      cudaMemcpy(o->d_antab, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  bool ok = (f64 ? aniso_tables<double>(ht, host.data(), &ts) : aniso_tables<float>(ht, host.data(), &ts)) == 0;
+  if (ok) {
+    cudaFree(o->d_rvol);
+    cudaFree(o->d_tr);
+    cudaFree(o->d_fres);
+    o->d_rvol = o->d_tr = o->d_fres = nullptr;
+    const size_t R = (size_t)o->max_rhs;
+    ok = cudaMalloc(&o->d_antab, host.size()) == cudaSuccess &&
+         cudaMemcpy(o->d_antab, host.data(), host.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&o->d_rvol, R * o->ncell * nq * es) == cudaSuccess &&
+         cudaMalloc(&o->d_tr, R * o->ncell * ts * es) == cudaSuccess &&
+         cudaMalloc(&o->d_fres, R * o->ncell * ts * es) == cudaSuccess;
+  }
+  if (ok && !mesh->affine) {  // per-face penalty alpha k_a (k_a + 1) n_a for the recomputed-geometry kernels
+    std::vector<double> g((size_t)o->nface);
+    for (int a = 0; a < 3; ++a)
+      for (int64_t f = o->face_off[a]; f < o->face_off[a + 1]; ++f) g[(size_t)f] = o->gamma_axis[a];
+    ok = cudaMemcpy(o->d_gamma, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
     cudaGetLastError();
     free_op(o);
     *out = nullptr;
@@ -387,10 +425,11 @@ dg_status dg_operator_create_aniso(const dg_mesh *mesh, const int32_t degrees[3]
   }
   o->aniso = 1;
   o->an_npts = npts;
+  o->an_nq = nq;
   o->an_ts = ts;
   o->ndofs = o->ncell * npts;
   o->variant = DG_VARIANT_THREE_KERNEL;
-  o->cpb = 256 / npts > 0 ? 256 / npts : 1;
+  o->cpb = 256 / nq > 0 ? 256 / nq : 1;
   o->fpb = 256 / (DG_MAXM * DG_MAXM) > 0 ? 256 / (DG_MAXM * DG_MAXM) : 1;
   return DG_OK;
 }
@@ -403,7 +442,6 @@ dg_status dg_operator_ndofs(const dg_operator *op, int64_t *n) {
 
 dg_status dg_operator_set_kappa(dg_operator *op, const void *kappa_vol, const void *kappa_face) {
   if (!op) return fail(DG_ERR_INVALID_ARG);
-  if (op->aniso) return fail(DG_ERR_UNSUPPORTED);
   if ((kappa_vol && !aligned16(kappa_vol)) || (kappa_face && !aligned16(kappa_face))) return fail(DG_ERR_INVALID_ARG);
   if ((kappa_vol == nullptr) != (kappa_face == nullptr)) return fail(DG_ERR_INVALID_ARG);
   if (op->problem != DG_SCALAR) return fail(DG_ERR_UNSUPPORTED);
@@ -425,7 +463,8 @@ dg_status dg_operator_stats(const dg_operator *op, dg_stats *out) {
   out->nface = op->nface;
   const int es = op->precision == DG_FP64 ? 8 : 4;
   if (op->aniso)
-    aniso_work_model(op->kax, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
+    aniso_work_model(op->kax, op->max_q, op->geo, op->kappa_vol != nullptr, op->ncell, op->nface, op->nbface,
+                     out->flops, out->bytes, es);
   else if (op->problem == DG_STOKES)
     stokes_work_model(op->p, op->ncell, op->nface, op->nbface, out->flops, out->bytes, es);
   else if (op->variant == DG_VARIANT_FUSED)
@@ -498,15 +537,19 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
     return DG_OK;
   }
   if (op->aniso) {
-    const int64_t sv = op->ncell * op->an_npts, st = op->ncell * op->an_ts;
+    const int64_t sv = op->ncell * op->an_nq, st = op->ncell * op->an_ts;
+    const int geo = op->geo == GEO_AFFINE ? GEO_AFFINE : GEO_RECOMPUTE;
+    const bool kap = op->kappa_vol != nullptr;
     if (op->precision == DG_FP64)
       e = launch_aniso_apply<double>(scalar_args<double>(op, transpose), op->d_antab, op->an_npts, op->an_ts,
                                      (const double *)x, (double *)y, (double *)op->d_rvol, (double *)op->d_tr,
-                                     (double *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev);
+                                     (double *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev, geo, kap,
+                                     op->an_nq);
     else
       e = launch_aniso_apply<float>(scalar_args<float>(op, transpose), op->d_antab, op->an_npts, op->an_ts,
                                     (const float *)x, (float *)y, (float *)op->d_rvol, (float *)op->d_tr,
-                                    (float *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev);
+                                    (float *)op->d_fres, nrhs, op->ndofs, sv, st, op->cpb, op->fpb, s, ev, geo, kap,
+                                    op->an_nq);
     if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     return DG_OK;
   }
@@ -1331,10 +1374,12 @@ void cellwise_work_model(int P, int nx, int ny, int nz, int brick, int64_t nbfac
   const double halo = 2.0 * ((double)((nx - 1) / bx) * ny * nz + (double)((ny - 1) / by) * nx * nz +
                              (double)((nz - 1) / bz) * nx * ny);
   const double per_halo = P2 * cP + 2.0 * (M * P + M2) * cP;
-  double cell = 2.0 * (P2 * M + P * M2 + M3) * cP + M3;
-  cell += 3.0 * (M3 * cM + M3 + 2.0 * M * M3 + 4.0 * M2 * cM);
-  const double own_sides = 6.0 * ncell - (double)nbface;  // interior own sides
-  const double face = own_sides * M2 * (7.0 + 4.0 * M) + (double)nbface * M2 * (5.0 + 4.0 * M);
+  // interpolation to u~ and back; per axis four weighted traces per line and the line
+  // operator (axis 0 starts the residual, axes 1 and 2 accumulate)
+  double cell = 2.0 * (P2 * M + P * M2 + M3) * cP;
+  cell += 3.0 * 4.0 * M2 * cM + M3 * cM + 2.0 * M3 * 2.0 * M;
+  const double own_sides = 6.0 * ncell - (double)nbface;  // interior own sides: neighbour coupling
+  const double face = own_sides * M2 * 4.0 * M + (double)nbface * M3 * 2.0 * M;  // boundary: correction
   flops[0] = cell * ncell + face + halo * per_halo;
   flops[1] = flops[2] = 0.0;
   bytes[0] = es * ncell * 2.0 * P3;

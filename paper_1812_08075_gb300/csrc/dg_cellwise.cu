@@ -1,37 +1,46 @@
 // One-thread-per-cell persistent apply for affine (axis-parallel) meshes and low degree
-// (k <= 3), used for FP32.
+// (k <= 2), used for FP32.
 //
 // A block owns a brick of bx x by x bz cells, one thread per cell, and loops over work
-// items (right-hand side, brick) in one wave of blocks. Each thread runs the whole of
-// Algorithm 1 for its cell in registers: interpolation to the Gauss points, the three
-// derivative contractions with the (diagonal) affine metric, the transposed contractions
-// and the transposed interpolation, every contraction fully unrolled so that the
-// reference-table entries, identical across the block, are read as constant-bank operands
-// of the FMAs. The face terms (Sec. 2.2) are evaluated per axis from each side: a cell
-// publishes the trace (u and the reference normal derivative at the face Gauss points) of
-// its two faces normal to the axis in shared memory, and reads its neighbours' traces
-// there; neighbours across the brick boundary were turned into traces at the start of the
-// item from their GLL coefficients (the face layer of nodes and the end row of the GLL
-// derivative along the normal, then facet sum factorisation to the face Gauss points), one
-// brick-boundary face per thread. The apply reads x and writes y once, both staged through
+// items (right-hand side, brick) in one wave of blocks. Each thread runs Algorithm 1 for
+// its cell in registers, every contraction fully unrolled so that the table entries,
+// identical across the block, are constant-bank operands of the FMAs.
+//
+// The cell works on weighted Gauss-point values u~ = W u (W_q = w_q0 w_q1 w_q2, folded
+// into the interpolation tables). On an axis-parallel cell with constant coefficients
+// everything that couples a cell to itself acts along one tensor line at a time, so per
+// axis d it is one M x M matrix applied to each line of u~ (Sec. 2.2's tensor structure):
+//   - the stiffness g_d D^T diag(w) D (the metric G is diagonal and constant);
+//   - the cell's own side of its two faces normal to d (Eq. diffreac_weak: the flux,
+//     symmetry and penalty terms with the neighbour's trace set to zero, or the Dirichlet
+//     terms on a boundary face; face weights W_t = w_t1 w_t2 are those of u~'s line);
+//   - on axis 0, the mass term c detJ.
+// These matrices are formed on the host in FP64. What is left per face point is the
+// coupling to the neighbour: its weighted trace (u~ and the reference normal derivative)
+// times two coefficient vectors of length M. Cells exchange traces through shared memory,
+// one axis at a time; neighbours across the brick boundary are turned into traces at the
+// start of the item from their GLL coefficients (face layer of nodes, end row of the GLL
+// derivative along the normal, facet sum factorisation to the face Gauss points with the
+// weights folded in), one brick-boundary face per thread. x and y are staged through
 // shared memory so that the global accesses are coalesced rows of the brick.
+#include <limits.h>
+
 #include <type_traits>
 
 #include "dg_internal.h"
 
 namespace dgc {
 
-// Reference tables and the affine per-point weights, passed by value (constant bank).
+// Tables and per-axis operators, passed by value (constant bank).
 template <int P, typename T>
 struct CTab {
-  T interp[P * P];        // [q][j] GLL basis j at Gauss point q
-  T dcol[P * P];          // [q][r] derivative of Gauss-Lagrange basis r at Gauss point q
-  T e0[P], e1[P], d0[P], d1[P];  // Gauss-Lagrange basis and derivative at xi = 0, 1
-  T gd0[P], gd1[P];       // GLL basis derivative at xi = 0, 1
-  T mw[P * P * P];        // c detJ w_q0 w_q1 w_q2
-  T gw[3][P * P * P];     // G_dd w_q0 w_q1 w_q2 (G diagonal on axis-parallel cells)
-  T hbw[3][P * P];        // half the normal-derivative weight of an axis-d face point
-  T pw[3][P * P];         // penalty weight of an axis-d face point
+  T iw[P * P];             // [q][j] w_q * (GLL basis j at Gauss point q): interpolation to u~
+  T it[P * P];             // [q][j] GLL basis j at Gauss point q: transposed interpolation
+  T gd0[P], gd1[P];        // GLL basis derivative at xi = 0, 1
+  T te[4][P];              // e0 / w, d0 / w, e1 / w, d1 / w: weighted traces from u~
+  T K[3][P * P];           // [d][q][r] line operator of axis d (interior faces on both sides)
+  T corr[3][2][P * P];     // [d][side] correction of a cell on the domain boundary
+  T na[3][2][P], nbv[3][2][P];  // neighbour coupling: R[r] += na[r] u~n + nbv[r] dn~n
 };
 
 // Index of the value at position r along axis D of the line (t1, t2) of a cell's
@@ -41,6 +50,33 @@ __device__ __forceinline__ constexpr int lidx(int r, int t1, int t2) {
   return D == 0 ? r + M * (t1 + M * t2) : (D == 1 ? t1 + M * (r + M * t2) : t1 + M * (t2 + M * r));
 }
 
+// Vector access to shared memory: four values (16-byte aligned) and pairs (8-byte
+// aligned for float, 16-byte for double).
+__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double *p, double a, double b, double c, double d) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void store2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void store2(double *p, double a, double b) {
+  *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void load2(const float *p, float &a, float &b) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load2(const double *p, double &a, double &b) {
+  const double2 v = *reinterpret_cast<const double2 *>(p);
+  a = v.x;
+  b = v.y;
+}
+
+// Trace buffer of one axis: [cell][face point][u0, g0, u1, g1] (value and reference normal
+// derivative on the lower and upper face), NT = 4 M^2 words per cell; halo traces of the
+// brick-boundary neighbours: [axis][side][plane][face point][u, g].
 template <int P>
 struct CLayout {
   static constexpr int P3 = P * P * P, M2 = P * P;
@@ -58,11 +94,66 @@ inline size_t cellwise_words(int bx, int by, int bz) {
   return 2 * LY::buf * nb + (size_t)LY::NT * (by * bz + bx * bz + bx * by);
 }
 
-// Trace of a neighbour cell's face normal to axis D from its GLL coefficients `src`:
-// SIDE 1 is the neighbour's lower face (xi_D = 0), SIDE 0 its upper face. Values go to
-// dst[pt * nd], normal derivatives to dst[(M2 + pt) * nd].
+// Host construction of CTab from the reference tables (FP64) and the affine constants.
+template <int P, typename T>
+CTab<P, T> make_tab(const ScalarArgs<T> &a, const HostTables &ht) {
+  constexpr int M = P;
+  CTab<P, T> tb;
+  const double *w = ht.gauss_w;
+  for (int q = 0; q < M; ++q)
+    for (int j = 0; j < P; ++j) {
+      tb.iw[q * P + j] = (T)(w[q] * ht.interp[q * P + j]);
+      tb.it[q * P + j] = (T)ht.interp[q * P + j];
+    }
+  for (int j = 0; j < P; ++j) { tb.gd0[j] = (T)ht.gd0[j]; tb.gd1[j] = (T)ht.gd1[j]; }
+  const double *ev[2] = {ht.e0, ht.e1}, *dv[2] = {ht.d0, ht.d1};
+  for (int r = 0; r < M; ++r) {
+    tb.te[0][r] = (T)(ht.e0[r] / w[r]); tb.te[1][r] = (T)(ht.d0[r] / w[r]);
+    tb.te[2][r] = (T)(ht.e1[r] / w[r]); tb.te[3][r] = (T)(ht.d1[r] / w[r]);
+  }
+  const double sc = (double)a.sc, ss = (double)a.ss;
+  for (int d = 0; d < 3; ++d) {
+    const double g = (double)a.vol_g[d], hb = 0.5 * (double)a.face_b[d], pw = (double)a.face_pw[d];
+    double K[M][M], F[2][2][M][M];  // F[side][0: interior, 1: Dirichlet][row r][col k]
+    for (int q = 0; q < M; ++q)
+      for (int r = 0; r < M; ++r) {
+        double s = 0.0;
+        for (int p = 0; p < M; ++p) s += ht.dcol[p * M + q] * w[p] * ht.dcol[p * M + r];
+        K[q][r] = g * s / w[r];
+      }
+    if (d == 0)
+      for (int q = 0; q < M; ++q) K[q][q] += (double)a.vol_m;
+    for (int s = 0; s < 2; ++s) {
+      const double sg = s ? 1.0 : -1.0;
+      for (int r = 0; r < M; ++r)
+        for (int k = 0; k < M; ++k) {
+          const double et = ev[s][k] / w[k], dt = dv[s][k] / w[k];
+          // own side of an interior face: neighbour trace zero in the jump and average
+          F[s][0][r][k] = ev[s][r] * (sg * sc * hb * dt + pw * et) + dv[s][r] * sg * ss * hb * et;
+          // Dirichlet face: jump = average = trace, outward normal, no factor 1/2
+          F[s][1][r][k] = ev[s][r] * (2.0 * sg * sc * hb * dt + pw * et) + dv[s][r] * 2.0 * sg * ss * hb * et;
+        }
+      for (int r = 0; r < M; ++r) {
+        tb.na[d][s][r] = (T)(-pw * ev[s][r] - sg * ss * hb * dv[s][r]);
+        tb.nbv[d][s][r] = (T)(sg * sc * hb * ev[s][r]);
+      }
+    }
+    const bool dir[2] = {((a.dmask >> (2 * d)) & 1u) != 0, ((a.dmask >> (2 * d + 1)) & 1u) != 0};
+    for (int r = 0; r < M; ++r)
+      for (int k = 0; k < M; ++k) {
+        tb.K[d][r * M + k] = (T)(K[r][k] + F[0][0][r][k] + F[1][0][r][k]);
+        for (int s = 0; s < 2; ++s)
+          tb.corr[d][s][r * M + k] = (T)((dir[s] ? F[s][1][r][k] : 0.0) - F[s][0][r][k]);
+      }
+  }
+  return tb;
+}
+
+// Weighted trace of a neighbour cell's face normal to axis D from its GLL coefficients
+// `src`: SIDE 1 is the neighbour's lower face (xi_D = 0), SIDE 0 its upper face. The pair
+// (W_t u, W_t du/dxi_D) of face point pt goes to dst[2 pt], dst[2 pt + 1].
 template <int P, typename T, int D, int SIDE>
-__device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab<P, T> &tb, T *dst, int nd) {
+__device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab<P, T> &tb, T *dst) {
   constexpr int M = P, P2 = P * P, M2 = M * M;
   constexpr int stn = D == 0 ? 1 : (D == 1 ? P : P2);
   constexpr int st1 = D == 0 ? P : 1;
@@ -86,11 +177,11 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
   for (int n2 = 0; n2 < P; ++n2)
 #pragma unroll
     for (int q1 = 0; q1 < M; ++q1) {
-      T a = tb.interp[q1 * P] * v[P * n2], b = tb.interp[q1 * P] * dv[P * n2];
+      T a = tb.iw[q1 * P] * v[P * n2], b = tb.iw[q1 * P] * dv[P * n2];
 #pragma unroll
       for (int n1 = 1; n1 < P; ++n1) {
-        a = fma(tb.interp[q1 * P + n1], v[n1 + P * n2], a);
-        b = fma(tb.interp[q1 * P + n1], dv[n1 + P * n2], b);
+        a = fma(tb.iw[q1 * P + n1], v[n1 + P * n2], a);
+        b = fma(tb.iw[q1 * P + n1], dv[n1 + P * n2], b);
       }
       tv[q1 + M * n2] = a;
       tdv[q1 + M * n2] = b;
@@ -99,34 +190,44 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
   for (int q2 = 0; q2 < M; ++q2)
 #pragma unroll
     for (int q1 = 0; q1 < M; ++q1) {
-      T a = tb.interp[q2 * P] * tv[q1], b = tb.interp[q2 * P] * tdv[q1];
+      T a = tb.iw[q2 * P] * tv[q1], b = tb.iw[q2 * P] * tdv[q1];
 #pragma unroll
       for (int n2 = 1; n2 < P; ++n2) {
-        a = fma(tb.interp[q2 * P + n2], tv[q1 + M * n2], a);
-        b = fma(tb.interp[q2 * P + n2], tdv[q1 + M * n2], b);
+        a = fma(tb.iw[q2 * P + n2], tv[q1 + M * n2], a);
+        b = fma(tb.iw[q2 * P + n2], tdv[q1 + M * n2], b);
       }
-      dst[(q1 + M * q2) * nd] = a;
-      dst[(M2 + q1 + M * q2) * nd] = b;
+      store2(dst + 2 * (q1 + M * q2), a, b);
     }
 }
 
 // The brick is 8 x 4 x BZ cells (a warp spans 8 x 4 cells); its shape is a template
 // parameter so that every shared-memory slot is an immediate offset from one address.
-// Resident blocks the compiler must allow for (measured at 128^3 x 16 right-hand sides):
-// FP32 Q1 and FP32 Q2 with bricks of 256 cells are held to 128 registers (16 warps per SM;
-// Q1 needs no more, Q2 spills a little and is still fastest), Q2 with bricks of 128 cells to
-// 168 (12 warps); the others take what they need.
+// Resident blocks the compiler must allow for: FP32 with bricks of 256 cells, 2 (128
+// registers, 16 warps per SM); with 128 cells, 3; the others take what they need.
 template <int P, typename T, int BZ>
 constexpr int cellwise_min_blocks() {
   if (sizeof(T) == 4 && P == 2) return 512 / (32 * BZ);
-  if (sizeof(T) == 4 && P == 3) return BZ == 8 ? 2 : (BZ == 4 ? 3 : 1);  // 128 / 168 / any registers
+  if (sizeof(T) == 4 && P == 3) return BZ == 8 ? 2 : (BZ == 4 ? 3 : 1);
   return 1;
 }
 
+// L2 prefetch of the bytes [p, p + n) that lie inside [lo, hi), rounded inwards to the
+// 16-byte granularity of the bulk prefetch (one instruction, no registers held).
+__device__ __forceinline__ void prefetch_l2(const void *lo, const void *hi, const void *p, size_t n) {
+  uintptr_t a = (uintptr_t)p, e = a + n;
+  const uintptr_t l = ((uintptr_t)lo + 15) & ~(uintptr_t)15, h = (uintptr_t)hi & ~(uintptr_t)15;
+  a &= ~(uintptr_t)15;
+  e = (e + 15) & ~(uintptr_t)15;
+  if (a < l) a = l;
+  if (e > h) e = h;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
 template <int P, typename T, int BZ>
-__global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x,
-                                                  T *__restrict__ y, int64_t sdof, int nbx, int nby, int64_t nbricks,
-                                                  int64_t nitems) {
+__global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
+    k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x, T *__restrict__ y, int64_t sdof,
+               int nbx, int nby, int nbricks, int nitems, int nrhs) {
   constexpr int M = P, P2 = P * P, P3 = P2 * P, M2 = M * M, M3 = M2 * M;
   using LY = CLayout<P>;
   constexpr int sX = LY::sX;
@@ -143,22 +244,63 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
   const int warp = tid >> 5, lane = tid & 31;
   constexpr int nwarps = nb >> 5;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const T sc = a.sc, ss = a.ss;
-  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int rhs = (int)(item / nbricks);
-    const int64_t bi = item - (int64_t)rhs * nbricks;
-    const int ibx = (int)(bi % nbx);
-    const int64_t bq = bi / nbx;
-    const int iby = (int)(bq % nby), ibz = (int)(bq / nby);
-    const int ox = ibx * bx, oy = iby * by, oz = ibz * bz;
+  const T *const xend = x + nrhs * sdof;
+  // item -> (right-hand side, brick origin)
+  auto decode = [&](int it, int &r, int &ox, int &oy, int &oz) {
+    r = it / nbricks;
+    const int bi = it - r * nbricks;
+    const int bq = bi / nbx;
+    const int ibz = bq / nby;
+    ox = (bi - bq * nbx) * bx;
+    oy = (bq - ibz * nby) * by;
+    oz = ibz * bz;
+  };
+  // The next item's x rows and the neighbour cells it evaluates brick-boundary traces from
+  // go to L2 one item ahead, so that its staging and halo loads hit L2 instead of DRAM:
+  // by*bz rows, 2*bz rows across y, 2*by rows across z, 2*by*bz single cells across x,
+  // one bulk prefetch each, spread over the even lanes of every warp.
+  auto prefetch_item = [&](int r, int px, int py, int pz) {
+    const T *xb = x + r * sdof;
+    const int qx = min(bx, nx - px);
+    constexpr int nranges = by * bz + 2 * bz + 2 * by + 2 * by * bz;
+    if (tid & 1) return;
+    for (int t0 = tid >> 1; t0 < nranges; t0 += nb / 2) {
+      int t = t0, cy, cz, cx = px, ncx = qx;
+      if (t < by * bz) {
+        cy = py + t % by; cz = pz + t / by;
+      } else if ((t -= by * bz) < 2 * bz) {
+        cz = pz + t % bz; cy = t < bz ? py - 1 : py + by;
+      } else if ((t -= 2 * bz) < 2 * by) {
+        cy = py + t % by; cz = t < by ? pz - 1 : pz + bz;
+      } else {
+        t -= 2 * by;
+        const int pl = t % (by * bz);
+        cy = py + pl % by; cz = pz + pl / by; cx = t < by * bz ? px - 1 : px + bx; ncx = 1;
+      }
+      if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
+      prefetch_l2(x, xend, xb + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3, (size_t)ncx * P3 * sizeof(T));
+    }
+  };
+  // each item is decoded once: the next item's indices, computed for its prefetch, are
+  // carried into the next iteration
+  int rhs = 0, ox = 0, oy = 0, oz = 0;
+  if (blockIdx.x < (unsigned)nitems) decode(blockIdx.x, rhs, ox, oy, oz);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    int nr = 0, nox = 0, noy = 0, noz = 0;
+    const bool more = item + (int)gridDim.x < nitems;
+    if (more) {
+      decode(item + gridDim.x, nr, nox, noy, noz);
+      prefetch_item(nr, nox, noy, noz);
+    }
     const int nax = min(bx, nx - ox), nay = min(by, ny - oy), naz = min(bz, nz - oz);
     const T *xr = x + rhs * sdof;
     T *yr = y + rhs * sdof;
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     const bool act = lx < nax && ly < nay && lz < naz;
-    // stage x: each warp copies whole rows of the brick (coalesced)
-    for (int row = warp; row < by * bz; row += nwarps) {
-      const int ry = row % by, rz = row / by;
+    // stage x: warp w copies the by rows of its own cells (z layer w of the brick), coalesced
+    static_assert(nwarps == bz, "one z layer of the brick per warp");
+    for (int ry = 0; ry < by; ++ry) {
+      const int rz = warp, row = ry + by * rz;
       if (ry >= nay || rz >= naz) continue;
       const T *src = xr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
       T *dst = xs + row * bx * sX;
@@ -176,7 +318,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
         dst[cl * sX + (j - cl * P3)] = __ldg(src + j);
       }
     }
-    // traces of the neighbours across the brick boundary, one face per thread
+    // weighted traces of the neighbours across the brick boundary, one face per thread
     const int nh = 2 * (n0 + n1 + n2);
     for (int h = tid; h < nh; h += nb) {
       int d = 0, rem = h;
@@ -205,17 +347,17 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
       }
       if (!ok) continue;
       const T *src = xr + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3;
-      T *dst = hl + hoff(d) + side * 2 * M2 * nd + p;
+      T *dst = hl + hoff(d) + (side * nd + p) * 2 * M2;
       if (d == 0) {
-        if (side) halo_trace<P, T, 0, 1>(src, tb, dst, nd); else halo_trace<P, T, 0, 0>(src, tb, dst, nd);
+        if (side) halo_trace<P, T, 0, 1>(src, tb, dst); else halo_trace<P, T, 0, 0>(src, tb, dst);
       } else if (d == 1) {
-        if (side) halo_trace<P, T, 1, 1>(src, tb, dst, nd); else halo_trace<P, T, 1, 0>(src, tb, dst, nd);
+        if (side) halo_trace<P, T, 1, 1>(src, tb, dst); else halo_trace<P, T, 1, 0>(src, tb, dst);
       } else {
-        if (side) halo_trace<P, T, 2, 1>(src, tb, dst, nd); else halo_trace<P, T, 2, 0>(src, tb, dst, nd);
+        if (side) halo_trace<P, T, 2, 1>(src, tb, dst); else halo_trace<P, T, 2, 0>(src, tb, dst);
       }
     }
     __syncthreads();
-    // own cell: Gauss-point values u and the mass term of the residual R
+    // own cell: weighted Gauss-point values u~ (interpolation tables carry the weights)
     T u[M3], R[M3];
     if (act) {
       T xl[P3];
@@ -226,9 +368,9 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
       for (int jj = 0; jj < P2; ++jj)
 #pragma unroll
         for (int q = 0; q < M; ++q) {
-          T s = tb.interp[q * P] * xl[jj * P];
+          T s = tb.iw[q * P] * xl[jj * P];
 #pragma unroll
-          for (int j = 1; j < P; ++j) s = fma(tb.interp[q * P + j], xl[jj * P + j], s);
+          for (int j = 1; j < P; ++j) s = fma(tb.iw[q * P + j], xl[jj * P + j], s);
           t1[jj * M + q] = s;
         }
       T t2[P * M2];  // [j2][q1][q0]
@@ -238,26 +380,32 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
         for (int q1 = 0; q1 < M; ++q1)
 #pragma unroll
           for (int q0 = 0; q0 < M; ++q0) {
-            T s = tb.interp[q1 * P] * t1[(j2 * P) * M + q0];
+            T s = tb.iw[q1 * P] * t1[(j2 * P) * M + q0];
 #pragma unroll
-            for (int j = 1; j < P; ++j) s = fma(tb.interp[q1 * P + j], t1[(j2 * P + j) * M + q0], s);
+            for (int j = 1; j < P; ++j) s = fma(tb.iw[q1 * P + j], t1[(j2 * P + j) * M + q0], s);
             t2[(j2 * M + q1) * M + q0] = s;
           }
 #pragma unroll
       for (int q2 = 0; q2 < M; ++q2)
 #pragma unroll
         for (int qq = 0; qq < M2; ++qq) {
-          T s = tb.interp[q2 * P] * t2[qq];
+          T s = tb.iw[q2 * P] * t2[qq];
 #pragma unroll
-          for (int j = 1; j < P; ++j) s = fma(tb.interp[q2 * P + j], t2[j * M2 + qq], s);
+          for (int j = 1; j < P; ++j) s = fma(tb.iw[q2 * P + j], t2[j * M2 + qq], s);
           u[q2 * M2 + qq] = s;
         }
-#pragma unroll
-      for (int q = 0; q < M3; ++q) R[q] = tb.mw[q] * u[q];
     }
-    // per axis: volume contraction, own traces, then the face terms of the two faces
+    // Per axis: publish the weighted traces of the two faces normal to the axis, apply the
+    // axis's line operator (stiffness, own face sides, on axis 0 the mass), correct the own
+    // side of a domain-boundary face, then after the exchange add the neighbours' coupling.
     auto axis = [&](auto Dc, T *trb) {
       constexpr int D = decltype(Dc)::value;
+      constexpr int bd = D == 0 ? bx : (D == 1 ? by : bz);
+      constexpr int nd = D == 0 ? n0 : (D == 1 ? n1 : n2);
+      constexpr int nstep = D == 0 ? 1 : (D == 1 ? bx : bx * by);
+      const int gc = D == 0 ? gx : (D == 1 ? gy : gz);
+      const int nlim = D == 0 ? nx : (D == 1 ? ny : nz);
+      const int lc = D == 0 ? lx : (D == 1 ? ly : lz);
       if (act) {
 #pragma unroll
         for (int t2 = 0; t2 < M; ++t2)
@@ -267,104 +415,76 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
             T v[M];
 #pragma unroll
             for (int r = 0; r < M; ++r) v[r] = u[lidx<M, D>(r, t1, t2)];
-            T f[M];
+            T tr[4];
 #pragma unroll
-            for (int q = 0; q < M; ++q) {
-              T s = tb.dcol[q * M] * v[0];
+            for (int k = 0; k < 4; ++k) {
+              T s = tb.te[k][0] * v[0];
 #pragma unroll
-              for (int r = 1; r < M; ++r) s = fma(tb.dcol[q * M + r], v[r], s);
-              f[q] = tb.gw[D][lidx<M, D>(q, t1, t2)] * s;
+              for (int r = 1; r < M; ++r) s = fma(tb.te[k][r], v[r], s);
+              tr[k] = s;
             }
+            store4(trb + tid * LY::NT + 4 * pt, tr[0], tr[1], tr[2], tr[3]);
 #pragma unroll
             for (int q = 0; q < M; ++q) {
-              T s = R[lidx<M, D>(q, t1, t2)];
+              T s = D == 0 ? tb.K[D][q * M] * v[0] : fma(tb.K[D][q * M], v[0], R[lidx<M, D>(q, t1, t2)]);
 #pragma unroll
-              for (int r = 0; r < M; ++r) s = fma(tb.dcol[r * M + q], f[r], s);
+              for (int r = 1; r < M; ++r) s = fma(tb.K[D][q * M + r], v[r], s);
               R[lidx<M, D>(q, t1, t2)] = s;
             }
-            T u0 = tb.e0[0] * v[0], g0 = tb.d0[0] * v[0], u1 = tb.e1[0] * v[0], g1 = tb.d1[0] * v[0];
-#pragma unroll
-            for (int r = 1; r < M; ++r) {
-              u0 = fma(tb.e0[r], v[r], u0); g0 = fma(tb.d0[r], v[r], g0);
-              u1 = fma(tb.e1[r], v[r], u1); g1 = fma(tb.d1[r], v[r], g1);
-            }
-            trb[(0 * M2 + pt) * nb + tid] = u0;
-            trb[(1 * M2 + pt) * nb + tid] = g0;
-            trb[(2 * M2 + pt) * nb + tid] = u1;
-            trb[(3 * M2 + pt) * nb + tid] = g1;
           }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (s ? gc + 1 >= nlim : gc == 0) {
+#pragma unroll
+            for (int t2 = 0; t2 < M; ++t2)
+#pragma unroll
+              for (int t1 = 0; t1 < M; ++t1)
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                  T acc = R[lidx<M, D>(q, t1, t2)];
+#pragma unroll
+                  for (int r = 0; r < M; ++r) acc = fma(tb.corr[D][s][q * M + r], u[lidx<M, D>(r, t1, t2)], acc);
+                  R[lidx<M, D>(q, t1, t2)] = acc;
+                }
+          }
+        }
         // A face on the brick boundary is read by no cell of the brick, so its slots take
         // the neighbour's trace from the halo instead: every neighbour trace is then at a
         // fixed offset from one address per side.
-        const int lc = D == 0 ? lx : (D == 1 ? ly : lz);
-        constexpr int bd = D == 0 ? bx : (D == 1 ? by : bz);
-        constexpr int nd = D == 0 ? n0 : (D == 1 ? n1 : n2);
         const int p = D == 0 ? ly + by * lz : (D == 1 ? lx + bx * lz : lx + bx * ly);
-        if (lc == 0) {
-          const T *h = hl + hoff(D) + p;
 #pragma unroll
-          for (int i = 0; i < 2 * M2; ++i) trb[i * nb + tid] = h[i * nd];
-        }
-        if (lc == bd - 1) {
-          const T *h = hl + hoff(D) + 2 * M2 * nd + p;
+        for (int side = 0; side < 2; ++side) {
+          if (side ? lc == bd - 1 : lc == 0) {
+            const T *h = hl + hoff(D) + (side * nd + p) * 2 * M2;
 #pragma unroll
-          for (int i = 0; i < 2 * M2; ++i) trb[(2 * M2 + i) * nb + tid] = h[i * nd];
+            for (int pt = 0; pt < M2; ++pt) {
+              T hu, hg;
+              load2(h + 2 * pt, hu, hg);
+              store2(trb + tid * LY::NT + 4 * pt + 2 * side, hu, hg);
+            }
+          }
         }
       }
       __syncthreads();
       if (act) {
-        const int gc = D == 0 ? gx : (D == 1 ? gy : gz);
-        const int nlim = D == 0 ? nx : (D == 1 ? ny : nz);
-        const int lc = D == 0 ? lx : (D == 1 ? ly : lz);
-        constexpr int bd = D == 0 ? bx : (D == 1 ? by : bz);
-        constexpr int nstep = D == 0 ? 1 : (D == 1 ? bx : bx * by);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const bool bnd = s ? gc + 1 >= nlim : gc == 0;
-          const bool dir = ((a.dmask >> (2 * D + s)) & 1u) != 0;
-          // neighbour trace: values at nsrc[pt * nb], derivatives at nsrc[(M2 + pt) * nb]
+          if (s ? gc + 1 >= nlim : gc == 0) continue;  // domain boundary: no neighbour
           const bool inb = s ? lc + 1 < bd : lc > 0;
-          const T *nsrc = trb + tid +
-                          (s ? (inb ? nstep : 2 * M2 * nb) : (inb ? 2 * M2 * nb - nstep : 0));
+          // neighbour trace pair of face point pt at nsrc[4 pt]: the neighbour's lower (s = 1) or
+          // upper (s = 0) face, or this cell's outward slots holding the halo trace
+          const T *nsrc = trb + (inb ? (s ? tid + nstep : tid - nstep) : tid) * LY::NT + (s == inb ? 0 : 2);
 #pragma unroll
           for (int t2 = 0; t2 < M; ++t2)
 #pragma unroll
             for (int t1 = 0; t1 < M; ++t1) {
               const int pt = t1 + M * t2;
-              // this cell's own trace, recomputed from its Gauss-point values (cheaper than
-              // keeping it live in registers across the barrier)
-              T uo, dno;
-              {
-                T v0 = u[lidx<M, D>(0, t1, t2)];
-                uo = (s ? tb.e1[0] : tb.e0[0]) * v0;
-                dno = (s ? tb.d1[0] : tb.d0[0]) * v0;
+              T un, dn;
+              load2(nsrc + 4 * pt, un, dn);
 #pragma unroll
-                for (int r = 1; r < M; ++r) {
-                  const T vr = u[lidx<M, D>(r, t1, t2)];
-                  uo = fma(s ? tb.e1[r] : tb.e0[r], vr, uo);
-                  dno = fma(s ? tb.d1[r] : tb.d0[r], vr, dno);
-                }
-              }
-              const T hb = tb.hbw[D][pt], pwv = tb.pw[D][pt];
-              T Rv, Rn;
-              if (bnd) {
-                const T b = s ? hb + hb : -(hb + hb);
-                Rv = dir ? fma(sc, b * dno, pwv * uo) : T(0);
-                Rn = dir ? ss * uo * b : T(0);
-              } else {
-                const T un = nsrc[pt * nb], dnn = nsrc[(M2 + pt) * nb];
-                const T J = s ? uo - un : un - uo;
-                const T v = fma(sc, hb * (dno + dnn), pwv * J);
-                Rv = s ? v : -v;
-                Rn = ss * hb * J;
-              }
-#pragma unroll
-              for (int r = 0; r < M; ++r) {
-                T acc = R[lidx<M, D>(r, t1, t2)];
-                acc = fma(s ? tb.e1[r] : tb.e0[r], Rv, acc);
-                acc = fma(s ? tb.d1[r] : tb.d0[r], Rn, acc);
-                R[lidx<M, D>(r, t1, t2)] = acc;
-              }
+              for (int r = 0; r < M; ++r)
+                R[lidx<M, D>(r, t1, t2)] =
+                    fma(tb.na[D][s][r], un, fma(tb.nbv[D][s][r], dn, R[lidx<M, D>(r, t1, t2)]));
             }
         }
       }
@@ -382,9 +502,9 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
       for (int j = 0; j < P; ++j)
 #pragma unroll
         for (int qq = 0; qq < M2; ++qq) {
-          T s = tb.interp[j] * R[qq];
+          T s = tb.it[j] * R[qq];
 #pragma unroll
-          for (int q = 1; q < M; ++q) s = fma(tb.interp[q * P + j], R[q * M2 + qq], s);
+          for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j], R[q * M2 + qq], s);
           t2[j * M2 + qq] = s;
         }
       T t1[P2 * M];  // [j2][j1][q0]
@@ -394,24 +514,26 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
         for (int j1 = 0; j1 < P; ++j1)
 #pragma unroll
           for (int q0 = 0; q0 < M; ++q0) {
-            T s = tb.interp[j1] * t2[(j2 * M) * M + q0];
+            T s = tb.it[j1] * t2[(j2 * M) * M + q0];
 #pragma unroll
-            for (int q = 1; q < M; ++q) s = fma(tb.interp[q * P + j1], t2[(j2 * M + q) * M + q0], s);
+            for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j1], t2[(j2 * M + q) * M + q0], s);
             t1[(j2 * P + j1) * M + q0] = s;
           }
 #pragma unroll
       for (int jj = 0; jj < P2; ++jj)
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          T s = tb.interp[j] * t1[jj * M];
+          T s = tb.it[j] * t1[jj * M];
 #pragma unroll
-          for (int q = 1; q < M; ++q) s = fma(tb.interp[q * P + j], t1[jj * M + q], s);
+          for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j], t1[jj * M + q], s);
           xs[tid * sX + jj * P + j] = s;
         }
     }
-    __syncthreads();
-    for (int row = warp; row < by * bz; row += nwarps) {
-      const int ry = row % by, rz = row / by;
+    // each warp stores the rows it staged itself: a warp barrier suffices, and the next
+    // item's staging by the same warp reuses the same rows
+    __syncwarp();
+    for (int ry = 0; ry < by; ++ry) {
+      const int rz = warp, row = ry + by * rz;
       if (ry >= nay || rz >= naz) continue;
       T *dst = yr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
       const T *src = xs + row * bx * sX;
@@ -428,34 +550,22 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>()) k_ce
         dst[j] = src[cl * sX + (j - cl * P3)];
       }
     }
-    __syncthreads();
+    // no block barrier here: the next item's first shared-memory writes are this warp's own
+    // staging rows and the halo region, whose last readers all passed the axis-2 barrier
+    if (more) {
+      rhs = nr;
+      ox = nox;
+      oy = noy;
+      oz = noz;
+    }
   }
 }
 
 template <int P, typename T, int BZ>
 cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof,
                 cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
-  constexpr int M = P, M2 = M * M, M3 = M2 * M;
   constexpr int bx = 8, by = 4, bz = BZ, nb = bx * by * bz;
-  CTab<P, T> tb;
-  for (int i = 0; i < P * P; ++i) { tb.interp[i] = (T)ht.interp[i]; tb.dcol[i] = (T)ht.dcol[i]; }
-  for (int i = 0; i < P; ++i) {
-    tb.e0[i] = (T)ht.e0[i]; tb.e1[i] = (T)ht.e1[i]; tb.d0[i] = (T)ht.d0[i]; tb.d1[i] = (T)ht.d1[i];
-    tb.gd0[i] = (T)ht.gd0[i]; tb.gd1[i] = (T)ht.gd1[i];
-  }
-  const double *w = ht.gauss_w;
-  for (int q = 0; q < M3; ++q) {
-    const double W = w[q % M] * w[(q / M) % M] * w[q / M2];
-    tb.mw[q] = (T)((double)a.vol_m * W);
-    for (int d = 0; d < 3; ++d) tb.gw[d][q] = (T)((double)a.vol_g[d] * W);
-  }
-  for (int pt = 0; pt < M2; ++pt) {
-    const double W = w[pt % M] * w[pt / M];
-    for (int d = 0; d < 3; ++d) {
-      tb.hbw[d][pt] = (T)(0.5 * W * (double)a.face_b[d]);
-      tb.pw[d][pt] = (T)(W * (double)a.face_pw[d]);
-    }
-  }
+  const CTab<P, T> tb = make_tab<P, T>(a, ht);
   const size_t sm = cellwise_words<P>(bx, by, bz) * sizeof(T);
   auto k = k_cellwise<P, T, BZ>;
   cudaError_t e;
@@ -465,9 +575,10 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nb, sm)) != cudaSuccess) return e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int nbx = (a.nx + bx - 1) / bx, nby = (a.ny + by - 1) / by, nbz = (a.nz + bz - 1) / bz;
-  const int64_t nbricks = (int64_t)nbx * nby * nbz;
+  const int64_t nbx = (a.nx + bx - 1) / bx, nby = (a.ny + by - 1) / by, nbz = (a.nz + bz - 1) / bz;
+  const int64_t nbricks = nbx * nby * nbz;
   const int64_t nitems = (int64_t)nrhs * nbricks;
+  if (nitems > INT_MAX) return cudaErrorInvalidValue;  // work items are decoded in 32 bits
   int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
   if (grid > nitems) grid = nitems;
   if (grid_out) *grid_out = (int)grid;
@@ -479,7 +590,7 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
     return cudaSuccess;
   }
   if (ev) cudaEventRecord(ev[0], s);
-  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, nbx, nby, nbricks, nitems);
+  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, (int)nbx, (int)nby, (int)nbricks, (int)nitems, nrhs);
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);

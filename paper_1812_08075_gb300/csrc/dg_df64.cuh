@@ -133,3 +133,34 @@ __device__ __forceinline__ df64 io_in<df64>(double v) {
 template <typename T>
 __device__ __forceinline__ io_t<T> io_out(T v) { return v; }
 __device__ __forceinline__ double io_out(df64 v) { return (double)v.hi + (double)v.lo; }
+
+// Accumulator of a dot product at FP64-class accuracy. For FP32 values it runs on the FP32
+// pipes: each product a b enters as its rounded value p = fl(a b), added to the high sum
+// by TwoSum, and as its exact rounding error fma(a, b, -p), added with the TwoSum error to
+// an FP32 low sum; value() = hi + lo in FP64 (about 44 significant bits after thousands of
+// terms, against 24 for an FP32 sum). For FP64 values it is one FP64 FMA per product.
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s = fma((double)a, (double)b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const df64 t = df_two_sum(hi, p);
+    hi = t.hi;
+    lo = __fadd_rn(lo, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ void add4(float4 a, float4 b) {
+    add(a.x, b.x);
+    add(a.y, b.y);
+    add(a.z, b.z);
+    add(a.w, b.w);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};

@@ -169,8 +169,10 @@ cudaError_t launch_block_jacobi_fused(const dg_operator *op, const double *tab, 
                                       const int *active, int nrhs, double *prz, double *prr, int stride, int *blocks,
                                       cudaStream_t s);
 
-// Anisotropic degrees on affine cells (dg_aniso.cu): per-direction tables (host buffer of
-// aniso_tab_bytes<T>() bytes; returns the trace words per cell) and the three-kernel apply.
+// Anisotropic degrees and quadrature (dg_aniso.cu): per-direction tables (host buffer of
+// aniso_tab_bytes<T>() bytes; returns the trace words per cell) and the three-kernel apply
+// with run-time extents; geo = GEO_AFFINE or GEO_RECOMPUTE (trilinear geometry from the
+// vertices at every point); nq = m0 m1 m2 Gauss points per cell, npts = p0 p1 p2 DOFs.
 template <typename T>
 size_t aniso_tab_bytes();
 template <typename T>
@@ -178,9 +180,9 @@ int aniso_tables(const HostTables ht[3], void *host_tab, int *trace_size);
 template <typename T>
 cudaError_t launch_aniso_apply(const ScalarArgs<T> &a, const void *dtab, int npts, int trace_size, const T *x, T *y,
                                T *rvol, T *traces, T *fres, int nrhs, int64_t sdof, int64_t srv, int64_t str,
-                               int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev);
-void aniso_work_model(const int kax[3], int64_t ncell, int64_t nface, int64_t nbface, double flops[3],
-                      double bytes[3], int es);
+                               int cpb, int fpb, cudaStream_t s, const cudaEvent_t *ev, int geo, bool kappa, int nq);
+void aniso_work_model(const int kax[3], const int max[3], int geo, bool kappa, int64_t ncell, int64_t nface,
+                      int64_t nbface, double flops[3], double bytes[3], int es);
 
 // Stokes block operator (dg_stokes.cu), affine meshes: vector [u: ncell x 3 x P^3 | p: ncell x (P-1)^3];
 // scratch rvol [ncell][4][M^3], traces and fres [ncell][42][M^2] per right-hand side.
@@ -268,6 +270,8 @@ struct dg_operator {
   // points per cell and trace words per cell; the isotropic fields describe k_max
   int aniso = 0;
   int kax[3] = {0, 0, 0};
+  int max_q[3] = {0, 0, 0};  // Gauss points per direction
+  int an_nq = 0;             // m0 m1 m2
   void *d_antab = nullptr;
   int an_npts = 0, an_ts = 0;
   void *d_bjinv = nullptr;     // their inverse eigenvalue sums on the device, operator precision

@@ -19,6 +19,7 @@
 
 #include <vector>
 
+#include "dg_df64.cuh"
 #include "dg_internal.h"
 
 namespace {
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(128) k_block_jacobi_cell(const BJTab<P, T> tb,
   const int64_t nchunks = (ncell + NB - 1) / NB;
   const T a = MODE == BJ_APPLY ? T(0) : (T)fu.alpha[rhs];
   const bool act = MODE == BJ_DIRECTION ? fu.active[rhs] != 0 : true;
-  double dot = 0.0, dot2 = 0.0;
+  DotAcc<T> acc_rz, acc_rr;  // r.z and r.r at FP64-class accuracy (double-float for FP32)
   const bool work = MODE == BJ_APPLY || a != T(0);
   for (int64_t ch = blockIdx.x; work && ch < nchunks; ch += gridDim.x) {
     const int64_t c0 = ch * NB;
@@ -322,16 +323,13 @@ __global__ void __launch_bounds__(128) k_block_jacobi_cell(const BJTab<P, T> tb,
         bj_sweep_pos<P, T, 2, false>(tb, pz, v, u);
         bj_sweep_pos<P, T, 1, false>(tb, py, u, v);
         bj_sweep_pos<P, T, 0, false>(tb, px, v, u);
-        T g = T(0), h = T(0);  // r.z and r.r of the cell (FP32 groups for FP32 vectors), then FP64
 #pragma unroll
         for (int i = 0; i < P3; ++i) {
           const T ri = st[tid * sX + i];
-          g = fma(ri, u[i], g);
-          if constexpr (MODE == BJ_UPDATE) h = fma(ri, ri, h);
+          acc_rz.add(ri, u[i]);
+          if constexpr (MODE == BJ_UPDATE) acc_rr.add(ri, ri);
           if constexpr (MODE != BJ_UPDATE) st[tid * sX + i] = u[i];
         }
-        dot += (double)g;
-        dot2 += (double)h;
       }
       __syncthreads();
     }
@@ -363,6 +361,7 @@ __global__ void __launch_bounds__(128) k_block_jacobi_cell(const BJTab<P, T> tb,
     }
   }
   if (MODE != BJ_DIRECTION && partial) {
+    double dot = acc_rz.value(), dot2 = acc_rr.value();
     __shared__ double part[2][NB / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

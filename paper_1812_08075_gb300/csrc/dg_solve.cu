@@ -15,6 +15,7 @@
 
 #include <algorithm>
 
+#include "dg_df64.cuh"
 #include "dg_internal.h"
 
 namespace {
@@ -95,13 +96,10 @@ __global__ void k_reduce(const double *__restrict__ partial, double *out, int nb
 
 // Vector kernels come in two forms. The scalar form (any T) accumulates every product
 // in FP64. The float4 form (V4, FP32 vectors whose length is a multiple of 4 and whose
-// buffers are 16-byte aligned) moves four elements per access and sums the four products
-// of a group in FP32 before adding the group to the FP64 accumulator: one FP64 add per
-// four elements instead of two conversions and an FP64 FMA per element, at a rounding
-// error of a few FP32 ulps per group, far below the FP32 vectors' own.
-__device__ __forceinline__ float dot4(float4 a, float4 b) {
-  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
-}
+// buffers are 16-byte aligned) moves four elements per access and accumulates the
+// products in double-float on the FP32 pipes (DotAcc<float>: each product's rounding error
+// kept exactly, FP64-class accuracy), since one FP64 operation per element would bound
+// these kernels by the FP64 pipe of this part instead of by memory.
 __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {  // a x + y
   return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
@@ -130,7 +128,9 @@ __global__ void k_dot(const T *__restrict__ u, const T *__restrict__ v, double *
   double s = 0.0;
   if constexpr (V4) {
     const float4 *U = (const float4 *)(u + off), *V = (const float4 *)(v + off);
-    for (int64_t i = i0; i < n / 4; i += st) s += (double)dot4(U[i], V[i]);
+    DotAcc<float> acc;
+    for (int64_t i = i0; i < n / 4; i += st) acc.add4(U[i], V[i]);
+    s = acc.value();
   } else {
     for (int64_t i = i0; i < n; i += st) s = fma((double)u[off + i], (double)v[off + i], s);
   }
@@ -147,13 +147,16 @@ __global__ void k_init_dir(const T *__restrict__ r, T *__restrict__ p, const T *
   if constexpr (V4) {
     const float4 *R = (const float4 *)(r + off), *D = (const float4 *)dinv;
     float4 *Pv = (float4 *)(p + off);
+    DotAcc<float> as, at;
     for (int64_t i = i0; i < n / 4; i += st) {
       const float4 v = R[i];
       const float4 z = dinv ? mul4(D[i], v) : v;
       Pv[i] = z;
-      s += (double)dot4(v, z);
-      t += (double)dot4(v, v);
+      as.add4(v, z);
+      at.add4(v, v);
     }
+    s = as.value();
+    t = at.value();
   } else {
     for (int64_t i = i0; i < n; i += st) {
       const T v = r[off + i];
@@ -231,17 +234,20 @@ __global__ void k_update(T *__restrict__ x, T *__restrict__ r, const T *__restri
       const float a = (float)ad;
       float4 *X = (float4 *)(x + off), *R = (float4 *)(r + off);
       const float4 *Pv = (const float4 *)(p + off), *A = (const float4 *)(Ap + off), *D = (const float4 *)dinv;
+      DotAcc<float> as, at;
       for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 4; i += (int64_t)gridDim.x * blockDim.x) {
         X[i] = axpy4(a, Pv[i], X[i]);
         const float4 v = axpy4(-a, A[i], R[i]);
         R[i] = v;
         if (dinv) {
-          s += (double)dot4(v, mul4(D[i], v));
-          t += (double)dot4(v, v);
+          as.add4(v, mul4(D[i], v));
+          at.add4(v, v);
         } else {
-          s += (double)dot4(v, v);
+          as.add4(v, v);
         }
       }
+      s = as.value();
+      t = at.value();
     }
     block_partial2(s, dinv ? t : s, prz, prr);
     return;

@@ -34,6 +34,7 @@ EXPORTED = [
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
     "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
     "dg_operator_create_aniso", "dg_mixed_cg_solve", "dg_measure_fma_peak",
+    "dg_measure_mma_peak",
 ]
 
 
@@ -108,8 +109,9 @@ def lib():
         L.dg_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.dg_operator_diagonal.argtypes = [vp, vp, vp]
         L.dg_operator_block_jacobi.argtypes = [vp, vp, vp, i32, vp]
-        L.dg_operator_create_aniso.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dg_penalty),
-                                               ctypes.POINTER(dg_coefficients), ctypes.POINTER(ctypes.c_void_p)]
+        L.dg_operator_create_aniso.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(dg_penalty), ctypes.POINTER(dg_coefficients),
+                                               ctypes.POINTER(ctypes.c_void_p)]
         L.dg_apply_semilinear.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp, vp]
         L.dg_operator_predict.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_time.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
@@ -123,6 +125,7 @@ def lib():
         L.dg_apply_affine_static.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              i32, vp, vp, vp]
         L.dg_measure_fma_peak.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.dg_measure_mma_peak.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
         for name in EXPORTED:
             if name not in ("dg_status_string",):
@@ -165,10 +168,11 @@ def dg_operator_create(mesh: int, degree: int, quad_points_1d: int, penalty: dg_
     return h.value
 
 
-def dg_operator_create_aniso(mesh: int, degrees, penalty: dg_penalty, coef: dg_coefficients) -> int:
+def dg_operator_create_aniso(mesh: int, degrees, penalty: dg_penalty, coef: dg_coefficients, quad=None) -> int:
     h = ctypes.c_void_p()
     ks = (ctypes.c_int32 * 3)(*degrees)
-    _check(lib().dg_operator_create_aniso(mesh, ks, ctypes.byref(penalty), ctypes.byref(coef), ctypes.byref(h)),
+    qs = None if quad is None else (ctypes.c_int32 * 3)(*quad)
+    _check(lib().dg_operator_create_aniso(mesh, ks, qs, ctypes.byref(penalty), ctypes.byref(coef), ctypes.byref(h)),
            "dg_operator_create_aniso")
     return h.value
 
@@ -309,6 +313,13 @@ def dg_measure_fma_peak(precision: int, stream: Optional[int] = None) -> float:
     return t.value
 
 
+def dg_measure_mma_peak(kind: int, stream: Optional[int] = None) -> float:
+    """Measured tensor-core throughput (TFLOP/s): kind 0 FP64 DMMA m8n8k4, 1 TF32 m16n8k8."""
+    t = ctypes.c_double()
+    _check(lib().dg_measure_mma_peak(kind, stream, ctypes.byref(t)), "dg_measure_mma_peak")
+    return t.value
+
+
 def dg_reference_tables(degree: int, m: int = 0):
     m = m or degree + 1
     out = {k: np.zeros(n) for k, n in (("gauss_nodes", m), ("gauss_weights", m), ("gll_nodes", degree + 1),
@@ -366,8 +377,9 @@ class Operator:
     def __init__(self, mesh: Mesh, degree: int, *, quad_points: int = 0, c: float = 1.0, mu: float = 1.0,
                  theta: float = -1.0, penalty_mode: int = DG_PEN_CONFIG, penalty_alpha: float = 2.0,
                  dirichlet_mask: int = 0b111111, precision: int = DG_FP64, max_rhs: int = 1,
-                 problem: int = DG_SCALAR, geometry: int = DG_GEOM_AUTO, degrees=None):
-        """degrees=(k_0, k_1, k_2): anisotropic degrees (dg_operator_create_aniso; degree unused)."""
+                 problem: int = DG_SCALAR, geometry: int = DG_GEOM_AUTO, degrees=None, quad=None):
+        """degrees=(k_0, k_1, k_2): anisotropic degrees, quad=(m_0, m_1, m_2) their Gauss points
+        (dg_operator_create_aniso; degree and quad_points unused)."""
         import torch
         self.mesh = mesh
         self.degree = degree
@@ -377,7 +389,7 @@ class Operator:
         pen = dg_penalty(penalty_mode, 0, penalty_alpha)
         co = dg_coefficients(problem, precision, dirichlet_mask, max_rhs, geometry, 0, c, mu, theta)
         if degrees is not None:
-            self.handle = dg_operator_create_aniso(mesh.handle, degrees, pen, co)
+            self.handle = dg_operator_create_aniso(mesh.handle, degrees, pen, co, quad)
         else:
             self.handle = dg_operator_create(mesh.handle, degree, quad_points, pen, co)
         self.ndofs = dg_operator_ndofs(self.handle)

@@ -66,6 +66,17 @@ def lognormal_kappa(ncell: int, m: int, seed: int = 2, sigma: float = 0.5):
     return k[:nv].copy(), k[nv:].copy()
 
 
+def lognormal_kappa_aniso(ncell: int, quad, seed: int = 2, sigma: float = 0.5):
+    """lognormal_kappa for per-direction point counts quad = (m0, m1, m2): kappa_vol
+    [ncell * m0 m1 m2] and kappa_face [ncell * 2 (m1 m2 + m0 m2 + m0 m1)] (six faces, each
+    with the points of its two tangential directions), one draw, volume values first."""
+    m0, m1, m2 = quad
+    nv = ncell * m0 * m1 * m2
+    nf = ncell * 2 * (m1 * m2 + m0 * m2 + m0 * m1)
+    k = np.exp(np.random.default_rng(seed).normal(0.0, sigma, size=nv + nf))
+    return k[:nv].copy(), k[nv:].copy()
+
+
 def sin_product_source(nx: int, ny: int, nz: int, nodes) -> np.ndarray:
     """The smooth source f = sin(pi x) sin(pi y) sin(pi z) of the mixed-precision solve,
     evaluated at the volume points of the uniform unit-cube lattice: cell c's point q is

@@ -561,6 +561,81 @@ def test_anisotropic_with_equal_degrees_is_the_isotropic_operator_on_a_perturbed
     assert np.abs(iso - ani).max() == 0.0
 
 
+@pytest.mark.parametrize("n,degrees,quad,theta,mask", [
+    ((2, 3, 2), (1, 3, 2), (3, 4, 3), -1.0, 0b111111),
+    ((3, 2, 2), (2, 2, 2), (4, 3, 5), 1.0, 0b100101),
+    ((2, 2, 2), (3, 1, 2), (4, 4, 6), 0.0, 0b011011),
+])
+def test_anisotropic_quadrature_affine_matches_kronecker(n, degrees, quad, theta, mask):
+    # m_a Gauss points per direction, chosen apart from k_a + 1 (Sec. 2.1's tensor-product
+    # rule; Sec. 4 raises m on purpose): every integrand of an affine cell is a polynomial
+    # that m_a >= k_a + 1 points integrate exactly, so the operator must still equal the
+    # exactly integrated Kronecker construction
+    orc = oracle.Problem(*n, max(degrees), theta=theta, dirichlet_mask=mask, degrees=degrees, quad=quad)
+    A = orc.assemble().toarray()
+    K = kr.scalar_matrix(*n, max(degrees), theta=theta, mask=mask, degrees=degrees).toarray()
+    assert np.abs(A - K).max() <= 1e-12 * np.abs(K).max()
+
+
+def _aniso_kappa_linear(n, quad):
+    """kappa = 1 + x + 2y + 3z at the volume and face Gauss points of the affine lattice,
+    in the per-direction layouts (points from numpy's Gauss-Legendre rule)."""
+    nx, ny, nz = n
+    s = [(np.polynomial.legendre.leggauss(m)[0] + 1) / 2 for m in quad]
+    kv, kf = [], []
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                c0 = np.array([cx / nx, cy / ny, cz / nz])
+                h = np.array([1 / nx, 1 / ny, 1 / nz])
+                for q2 in range(quad[2]):
+                    for q1 in range(quad[1]):
+                        for q0 in range(quad[0]):
+                            x = c0 + h * np.array([s[0][q0], s[1][q1], s[2][q2]])
+                            kv.append(1 + x[0] + 2 * x[1] + 3 * x[2])
+                for lf in range(6):
+                    a, side = lf // 2, lf % 2
+                    t1, t2 = (1, 2) if a == 0 else ((0, 2) if a == 1 else (0, 1))
+                    for qt in range(quad[t2]):
+                        for qs in range(quad[t1]):
+                            xi = np.zeros(3)
+                            xi[a], xi[t1], xi[t2] = side, s[t1][qs], s[t2][qt]
+                            x = c0 + h * xi
+                            kf.append(1 + x[0] + 2 * x[1] + 3 * x[2])
+    return np.array(kv), np.array(kf)
+
+
+def test_anisotropic_quadrature_with_linear_kappa_is_independent_of_the_rule():
+    # with kappa linear in x, every integrand of an affine cell is still a polynomial of
+    # degree <= 2 m_a - 1 per direction, so two rules with m_a >= k_a + 1 give the same
+    # operator; kappa values sit in the per-direction layouts, so a mis-indexed point or
+    # face would change the result
+    n, degrees = (2, 3, 2), (2, 1, 3)
+    x = wl.uniform_vector(np.prod(n) * np.prod([d + 1 for d in degrees]), 3)
+    ys = []
+    for quad in ((3, 2, 4), (4, 4, 5), (5, 3, 6)):
+        kv, kf = _aniso_kappa_linear(n, quad)
+        orc = oracle.Problem(*n, 3, degrees=degrees, quad=quad, kappa_vol=kv, kappa_face=kf, theta=1.0)
+        ys.append(orc.apply(x))
+    for y in ys[1:]:
+        assert np.abs(y - ys[0]).max() <= 1e-12 * np.abs(ys[0]).max()
+    # and kappa really enters: a constant kappa = 1 gives a different operator
+    plain = oracle.Problem(*n, 3, degrees=degrees, quad=(3, 2, 4), theta=1.0).apply(x)
+    assert np.abs(plain - ys[0]).max() > 1e-3 * np.abs(ys[0]).max()
+
+
+def test_anisotropic_quadrature_penalty_closed_form_on_a_perturbed_mesh():
+    # u = 1: interior jumps and gradients vanish, so 1^T A 1 = c |Omega| + sum over Dirichlet
+    # boundary faces of gamma_F |F|, gamma_a = alpha k_a (k_a + 1) n_a with k_a the degree
+    # along the normal; exact for any m_a >= 2 because detJ has degree <= 2 per direction and
+    # the boundary faces stay planar
+    n, degrees, quad = (3, 2, 3), (1, 3, 2), (2, 5, 3)
+    orc = oracle.Problem(*n, 3, degrees=degrees, quad=quad, vertices=wl.perturbed_vertices(*n, seed=1), c=1.5)
+    one = np.ones(orc.ndofs())
+    want = 1.5 + sum(2 * 2.0 * degrees[a] * (degrees[a] + 1) * n[a] for a in range(3))
+    assert abs(one @ orc.apply(one) - want) <= 1e-11 * want
+
+
 def test_stokes_transpose_equals_assembled_transpose():
     # theta = +1 makes the viscous block non-symmetric; the pressure coupling [[., B^T], [B, 0]]
     # is its own transpose, so A^T swaps the viscous face coefficients only

@@ -68,7 +68,7 @@ def _case(n, k, c, theta, alpha, mask, seed, stream=None, oracle_cells=None):
     else:
         cells = wl.sample_cells(orc.ncell, oracle_cells, seed=seed + 100)
         got = yy.reshape(-1, p3)[cells].ravel()
-        err_oracle = _relerr(got, orc.apply_cells(xh, cells))
+        err_oracle = _relerr(got, orc.apply_cells(xh, cells).ravel())
     return err_apply, err_oracle
 
 
