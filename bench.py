@@ -434,10 +434,20 @@ def next_rows_apply(n_cells=64, k=3):
     aff32 = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32)
     w32, y32 = w.float(), torch.empty_like(w.float())
     ms_bj32 = event_ms(lambda: aff32.block_jacobi(w32, y32))
+    # anisotropic degrees and quadrature on the trilinear mesh (geometry recomputed)
+    aniso = {}
+    for prec, tag in ((dg.DG_FP64, "fp64"), (dg.DG_FP32, "fp32")):
+        an = dg.Operator(op.mesh, 0, degrees=(1, 3, 2), quad=(3, 4, 3), precision=prec)
+        xa = torch.from_numpy(wl.uniform_vector(an.ndofs, 7)).to("cuda", an.dtype)
+        ya = torch.empty_like(xa)
+        ms_a = event_ms(lambda: an.apply(xa, ya))
+        aniso[tag] = {"ms": ms_a, "dof_s": an.ndofs / (ms_a * 1e-3)}
+        del an, xa, ya
     return {"workload": f"{n_cells}^3 trilinear cells (block Jacobi: affine), Q{k}, FP64 unless stated",
             "ndofs": op.ndofs, "forward_apply_ms": ms_fwd, "rhs_ms": ms_rhs,
             "semilinear_residual_ms": ms_res, "semilinear_jacobian_ms": ms_jac,
             "block_jacobi_fp64_ms": ms_bj, "block_jacobi_fp32_ms": ms_bj32,
+            "aniso_k132_m343_trilinear": aniso,
             "note": "semilinear and rhs recompute the geometry in the kernels; the forward apply reads stored geometry"}
 
 
@@ -455,10 +465,15 @@ def solve_entry(n, k, nrhs, rtol, inner_rtol=1e-3, delta=0.1, fp64_max_iters=200
     op32 = dg.Operator(mesh, k, precision=dg.DG_FP32, max_rhs=nrhs)
     b = config4_rhs(op64, n, k, nrhs)
     stream = torch.cuda.current_stream().cuda_stream
+    # both operators take the variant and blocking the framework's tuner measures fastest
+    # for nrhs right-hand sides, so the all-FP64 CG runs on its best apply too
+    tune64, tune32 = op64.autotune(nrhs), op32.autotune(nrhs)
     out = {"workload": f"scalar SIPG, {n}^3 affine cells, Q{k}, {nrhs} right-hand sides (Gauss-projected "
                        f"sin-product load vector + U[-1,1] noise), x0 = 0",
            "ndofs": op64.ndofs, "nrhs": nrhs, "rtol": rtol,
-           "fp32_operator": None, "mixed_preconditioner": PRECOND_NAMES[precond]}
+           "fp64_operator": {"variant": VARIANT_NAMES[op64.stats().variant], "apply_ms": tune64["ms_best"]},
+           "fp32_operator": {"variant": VARIANT_NAMES[op32.stats().variant], "apply_ms": tune32["ms_best"]},
+           "mixed_preconditioner": PRECOND_NAMES[precond]}
     # set up the preconditioners and the FP32 operator's variant before timing
     for op, pcs, bb in ((op64, fp64_preconds, b), (op32, (precond,), b.float())):
         for pc in pcs:
@@ -467,7 +482,6 @@ def solve_entry(n, k, nrhs, rtol, inner_rtol=1e-3, delta=0.1, fp64_max_iters=200
                 dg.dg_cg_solve(op.handle, bb.data_ptr(), xz.data_ptr(), nrhs, dg.dg_cg_options(1e-1, 50, 50, 0, pc),
                                stream)
                 del xz
-    out["fp32_operator"] = VARIANT_NAMES[op32.stats().variant]
 
     def relres(x):
         r = b - op64.apply(x)
@@ -622,7 +636,9 @@ def run_ours(args, rank, world, dist):
                 ms_k, kt_k, _ = time_applies(o, xx, yy, 10, 3, None, profile=True)
                 st_k = o.stats()
                 ent = {"dof_s": o.ndofs / (ms_k * 1e-3), "ms": ms_k, "kernel_ms": kt_k,
-                       "blocking": [st_k.variant, st_k.cells_per_block, st_k.faces_per_block]}
+                       "blocking": [st_k.variant, st_k.cells_per_block, st_k.faces_per_block],
+                       "geometry": "recomputed in the kernels" if st_k.geometry == dg.DG_GEOM_RECOMPUTE
+                       else "stored per point"}
                 ent.update(roofline_entry(sum(st_k.flops), 2 * es * o.ndofs + vert_bytes, ms_k, pk,
                                           prec == dg.DG_FP32, impl_bytes=sum(st_k.bytes)))
                 if prec == dg.DG_FP32:  # error of the FP32 result against the FP64 apply of the same x

@@ -71,8 +71,8 @@ typedef struct {
  *                  the Dirichlet face terms; other boundary faces carry none.
  *   max_rhs        1..16, the largest nrhs any apply on this operator will use.
  *   geometry       DG_GEOM_AUTO / STORED (per-quadrature-point geometry precomputed once)
- *                  / RECOMPUTE (from vertex coordinates inside the kernels); ignored on
- *                  affine meshes.
+ *                  / RECOMPUTE (from vertex coordinates inside the kernels; scalar problem
+ *                  with k+1 points, FP64 or FP32); ignored on affine meshes.
  *   c              reaction coefficient (scalar), mu viscosity (Stokes),
  *   theta          -1 symmetric (SIPG, the paper's choice), 0 incomplete, +1 non-symmetric. */
 typedef struct {

@@ -262,7 +262,7 @@ static dg_status create_impl(const dg_mesh *mesh, int degree, int quad_points_1d
   if (co->dirichlet_mask < 0 || co->dirichlet_mask > 63) return fail(DG_ERR_INVALID_ARG);
   if (co->geometry < DG_GEOM_AUTO || co->geometry > DG_GEOM_RECOMPUTE) return fail(DG_ERR_INVALID_ARG);
   if (co->geometry == DG_GEOM_RECOMPUTE && !mesh->affine && !any_recompute &&
-      (co->precision != DG_FP64 || co->problem != DG_SCALAR || m != degree + 1))
+      (co->problem != DG_SCALAR || m != degree + 1))
     return fail(DG_ERR_UNSUPPORTED);
 
   dg_operator *o = new (std::nothrow) dg_operator;
@@ -567,10 +567,16 @@ static dg_status apply_impl(const dg_operator *op_c, const void *x, void *y, int
       return DG_OK;
     }
     for (int r = 0; r < nrhs; ++r) {
-      e = launch_scalar_adjoint<double>(op->p, GEO_RECOMPUTE, kap, scalar_args<double>(op, transpose), op->theta,
-                                (const double *)x + r * sdof, nullptr, (double *)y + r * sdof, nullptr, nullptr,
-                                (double *)op->d_rvol, (double *)op->d_tr, nullptr, (double *)op->d_fres, op->cpb,
-                                op->fpb, s, r == 0 ? ev : nullptr);
+      if (op->precision == DG_FP32)
+        e = launch_scalar_adjoint<float>(op->p, GEO_RECOMPUTE, kap, scalar_args<float>(op, transpose), op->theta,
+                                         (const float *)x + r * sdof, nullptr, (float *)y + r * sdof, nullptr,
+                                         nullptr, (float *)op->d_rvol, (float *)op->d_tr, nullptr,
+                                         (float *)op->d_fres, op->cpb, op->fpb, s, r == 0 ? ev : nullptr);
+      else
+        e = launch_scalar_adjoint<double>(op->p, GEO_RECOMPUTE, kap, scalar_args<double>(op, transpose), op->theta,
+                                          (const double *)x + r * sdof, nullptr, (double *)y + r * sdof, nullptr,
+                                          nullptr, (double *)op->d_rvol, (double *)op->d_tr, nullptr,
+                                          (double *)op->d_fres, op->cpb, op->fpb, s, r == 0 ? ev : nullptr);
       if (e != cudaSuccess) return fail(DG_ERR_CUDA);
     }
     return DG_OK;
@@ -987,7 +993,7 @@ dg_status dg_operator_autotune(dg_operator *op, int nrhs, void *stream, dg_tune_
     }
     if (st != DG_OK) break;
     int bgeo = op->geo;
-    if (op->geo == GEO_STORED && op->precision == DG_FP64 && op->problem == DG_SCALAR && op->m == op->p && !df) {
+    if (op->geo == GEO_STORED && op->problem == DG_SCALAR && op->m == op->p && !df) {
       op->geo = GEO_RECOMPUTE;  // stored vs recomputed per-point geometry
       op->cpb = bc;
       op->fpb = bf;

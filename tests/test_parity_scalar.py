@@ -95,6 +95,32 @@ def test_fp32_against_fp64_oracle(k, geom):
     assert err <= TOL32
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("kappa", [False, True])
+def test_fp32_recomputed_geometry(k, kappa):
+    """FP32 on a trilinear mesh with the geometry recomputed in the kernels (nothing
+    stored): forward apply and transposed apply against the FP64 oracle."""
+    n = (4, 3, 5)
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k, precision=dg.DG_FP32, geometry=dg.DG_GEOM_RECOMPUTE, max_rhs=2,
+                     theta=1.0)
+    assert op.stats().geometry == dg.DG_GEOM_RECOMPUTE
+    orc = oracle.Problem(*n, k, vertices=verts, theta=1.0)
+    if kappa:
+        kv, kf = wl.lognormal_kappa(op.mesh.ncell, k + 1, seed=2)
+        orc.kappa_vol, orc.kappa_face = kv, kf
+        op.set_kappa(torch.from_numpy(kv).float().cuda(), torch.from_numpy(kf).float().cuda())
+    xs = np.stack([wl.uniform_vector(op.ndofs, 20 + r) for r in range(2)])
+    xd = torch.from_numpy(xs).float().cuda()
+    y = op.apply(xd).double().cpu().numpy()
+    yt = torch.empty_like(xd)
+    dg.dg_apply_adjoint(op.handle, xd.data_ptr(), None, yt.data_ptr(), None, None, None, nrhs=2)
+    yt = yt.double().cpu().numpy()
+    for r in range(2):
+        assert relerr(y[r], orc.apply(xs[r])) <= TOL32
+        assert relerr(yt[r], orc.apply(xs[r], transpose=True)) <= TOL32
+
+
 @pytest.mark.parametrize("case", ["fp64_q3_2rhs", "fp64_4cells", "fp64_kappa_3rhs", "fp32_three_kernel",
                                   "df64_q3", "fp32_fused_unpipelined"])
 def test_apply_host_matches_device(case):
@@ -161,6 +187,26 @@ def test_config2_full_size_sampled(k):
     ref = orc.apply_cells(x, cells, nthreads=0)
     err = float(np.abs(y[cells] - ref).max() / np.abs(ref).max())
     assert err <= TOL64, err
+
+
+def test_config2_q3_tuned_as_benchmarked_sampled():
+    """The operator exactly as the benchmark times it: 64^3 trilinear Q3, FP64, blocking
+    chosen by dg_operator_autotune, and then the same operator in double-float with its
+    own tuned blocking; sampled cells against the oracle."""
+    n, k = (64, 64, 64), 3
+    verts = wl.perturbed_vertices(*n, seed=1)
+    op = dg.Operator(dg.Mesh(*n, verts), k)
+    op.autotune(1)
+    x = wl.uniform_vector(op.ndofs, 0)
+    xd = torch.from_numpy(x).cuda()
+    cells = wl.sample_cells(op.mesh.ncell, 96, seed=31)
+    ref = oracle.Problem(*n, k, vertices=verts).apply_cells(x, cells, nthreads=0)
+    y = op.apply(xd).cpu().numpy().reshape(op.mesh.ncell, -1)
+    assert float(np.abs(y[cells] - ref).max() / np.abs(ref).max()) <= TOL64
+    op.set_variant(dg.DG_VARIANT_DF64)
+    op.autotune(1)
+    y = op.apply(xd).cpu().numpy().reshape(op.mesh.ncell, -1)
+    assert float(np.abs(y[cells] - ref).max() / np.abs(ref).max()) <= TOL64
 
 
 # ---------------------------------------------------------------- fused persistent variant
