@@ -211,19 +211,6 @@ constexpr int cellwise_min_blocks() {
   return 1;
 }
 
-// L2 prefetch of the bytes [p, p + n) that lie inside [lo, hi), rounded inwards to the
-// 16-byte granularity of the bulk prefetch (one instruction, no registers held).
-__device__ __forceinline__ void prefetch_l2(const void *lo, const void *hi, const void *p, size_t n) {
-  uintptr_t a = (uintptr_t)p, e = a + n;
-  const uintptr_t l = ((uintptr_t)lo + 15) & ~(uintptr_t)15, h = (uintptr_t)hi & ~(uintptr_t)15;
-  a &= ~(uintptr_t)15;
-  e = (e + 15) & ~(uintptr_t)15;
-  if (a < l) a = l;
-  if (e > h) e = h;
-  if (e > a)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
-}
-
 template <int P, typename T, int BZ>
 __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x, T *__restrict__ y, int64_t sdof,
@@ -278,7 +265,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
         cy = py + pl % by; cz = pz + pl / by; cx = t < by * bz ? px - 1 : px + bx; ncx = 1;
       }
       if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
-      prefetch_l2(x, xend, xb + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3, (size_t)ncx * P3 * sizeof(T));
+      dg_prefetch_l2(x, xend, xb + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3, (size_t)ncx * P3 * sizeof(T));
     }
   };
   // each item is decoded once: the next item's indices, computed for its prefetch, are

@@ -18,6 +18,22 @@ struct df64 {
   __host__ __device__ df64(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
 };
 
+#ifdef __CUDACC__
+// L2 prefetch of the bytes [p, p + n) that lie inside [lo, hi), rounded inwards to the
+// 16-byte granularity of the bulk prefetch (one instruction, no registers held). Kernels
+// use it for the inputs of the block that will run one wave after them.
+__device__ __forceinline__ void dg_prefetch_l2(const void *lo, const void *hi, const void *p, size_t n) {
+  uintptr_t a = (uintptr_t)p, e = a + n;
+  const uintptr_t l = ((uintptr_t)lo + 15) & ~(uintptr_t)15, h = (uintptr_t)hi & ~(uintptr_t)15;
+  a &= ~(uintptr_t)15;
+  e = (e + 15) & ~(uintptr_t)15;
+  if (a < l) a = l;
+  if (e > h) e = h;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+#endif
+
 // Element type of the input and output vectors of kernels computing in T.
 template <typename T>
 struct IOType { using type = T; };

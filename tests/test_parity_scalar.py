@@ -389,5 +389,6 @@ def test_recomputed_geometry_forward(k):
     y = op.apply(torch.from_numpy(xs).cuda()).cpu().numpy()
     for r in range(2):
         assert relerr(y[r], orc.apply(xs[r])) <= TOL64
-    with pytest.raises(dg.DGError):
-        dg.Operator(dg.Mesh(*n, verts), k, precision=dg.DG_FP32, geometry=dg.DG_GEOM_RECOMPUTE)
+    with pytest.raises(dg.DGError) as e:  # over-integration needs stored geometry
+        dg.Operator(dg.Mesh(*n, verts), k, quad_points=k + 2, geometry=dg.DG_GEOM_RECOMPUTE)
+    assert e.value.status == dg.DG_ERR_UNSUPPORTED
