@@ -444,7 +444,8 @@ dg_status dg_measure_fma_peak(int precision, void *stream, double *tflops);
 /* Measured tensor-core throughput for measurement harnesses, with the same protocol as
  * dg_measure_fma_peak: kind 0 = FP64 mma.sync m8n8k4 (DMMA), kind 1 = TF32 mma.sync
  * m16n8k8 with FP32 accumulation; every warp keeps four independent accumulations in
- * flight. *tflops in TFLOP/s (one multiply-add = 2 flops). These decide whether the
+ * flight. kind 2 = DMMA and DFMA chains issued together by every warp (their combined
+ * rate, which shows whether the two share one pipe). *tflops in TFLOP/s (one multiply-add = 2 flops). These decide whether the
  * batched 1D contractions of the sum factorisation (Sec. 2.2) could gain from the tensor
  * cores of this part. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_measure_mma_peak(int kind, void *stream, double *tflops);

@@ -85,13 +85,14 @@ struct CLayout {
   static constexpr int buf = NT > sX ? NT : sX;
 };
 
-// Shared memory words: two trace buffers (the second one doubles as x/y staging) and the
-// brick-boundary traces of the three axes.
+// Shared memory words: the x / y staging rows, one trace buffer (the z exchange; x and y
+// neighbours are lanes of the same warp and exchange by shuffles) and the brick-boundary
+// traces of the three axes.
 template <int P>
 inline size_t cellwise_words(int bx, int by, int bz) {
   using LY = CLayout<P>;
   const size_t nb = (size_t)bx * by * bz;
-  return 2 * LY::buf * nb + (size_t)LY::NT * (by * bz + bx * bz + bx * by);
+  return (size_t)(LY::sX + LY::NT) * nb + (size_t)LY::NT * (by * bz + bx * bz + bx * by);
 }
 
 // Host construction of CTab from the reference tables (FP64) and the affine constants.
@@ -221,10 +222,9 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
   constexpr int bx = 8, by = 4, bz = BZ, nb = bx * by * bz;
   constexpr int n0 = by * bz, n1 = bx * bz, n2 = bx * by;  // brick-boundary planes per axis
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *buf0 = reinterpret_cast<T *>(smem_raw);
-  T *buf1 = buf0 + LY::buf * nb;
-  T *xs = buf1;                 // x / y staging: [cell of the brick][sX]
-  T *hl = buf1 + LY::buf * nb;  // [axis][side][qty][pt][plane]
+  T *trz = reinterpret_cast<T *>(smem_raw);  // z traces: [cell][pt][u0, g0, u1, g1]
+  T *xs = trz + LY::NT * nb;                   // x / y staging: [cell of the brick][sX]
+  T *hl = xs + LY::sX * nb;                    // halo traces: [axis][side][plane][pt][u, g]
   auto hoff = [](int d) { return d == 0 ? 0 : (d == 1 ? LY::NT * n0 : LY::NT * (n0 + n1)); };
   const int tid = threadIdx.x;
   const int lx = tid % bx, ly = (tid / bx) % by, lz = tid / (bx * by);
@@ -346,6 +346,8 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     __syncthreads();
     // own cell: weighted Gauss-point values u~ (interpolation tables carry the weights)
     T u[M3], R[M3];
+#pragma unroll
+    for (int q = 0; q < M3; ++q) u[q] = T(0);  // lanes outside the mesh take part in the shuffles
     if (act) {
       T xl[P3];
 #pragma unroll
@@ -382,17 +384,79 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
           u[q2 * M2 + qq] = s;
         }
     }
-    // Per axis: publish the weighted traces of the two faces normal to the axis, apply the
-    // axis's line operator (stiffness, own face sides, on axis 0 the mass), correct the own
-    // side of a domain-boundary face, then after the exchange add the neighbours' coupling.
-    auto axis = [&](auto Dc, T *trb) {
+    // x and y axes: a warp spans 8 x 4 cells of one z layer, so the x and y neighbours are
+    // lanes +-1 and +-8. Per tensor line: the four weighted traces, the neighbours' pairs by
+    // shuffles (the halo trace at the brick boundary), the axis's line operator (stiffness,
+    // own face sides, on axis 0 the mass) and the neighbour coupling; all lanes take part.
+    auto axis_xy = [&](auto Dc) {
       constexpr int D = decltype(Dc)::value;
-      constexpr int bd = D == 0 ? bx : (D == 1 ? by : bz);
-      constexpr int nd = D == 0 ? n0 : (D == 1 ? n1 : n2);
-      constexpr int nstep = D == 0 ? 1 : (D == 1 ? bx : bx * by);
-      const int gc = D == 0 ? gx : (D == 1 ? gy : gz);
-      const int nlim = D == 0 ? nx : (D == 1 ? ny : nz);
-      const int lc = D == 0 ? lx : (D == 1 ? ly : lz);
+      constexpr unsigned full = 0xffffffffu;
+      constexpr int dl = D == 0 ? 1 : bx;
+      constexpr int bd = D == 0 ? bx : by;
+      constexpr int nd = D == 0 ? n0 : n1;
+      const int gc = D == 0 ? gx : gy;
+      const int nlim = D == 0 ? nx : ny;
+      const int lc = D == 0 ? lx : ly;
+      const int p = D == 0 ? ly + by * lz : lx + bx * lz;
+      const bool lo_bnd = gc == 0, hi_bnd = gc + 1 >= nlim;
+      const T *hlo = hl + hoff(D) + p * 2 * M2, *hhi = hl + hoff(D) + (nd + p) * 2 * M2;
+#pragma unroll
+      for (int t2 = 0; t2 < M; ++t2)
+#pragma unroll
+        for (int t1 = 0; t1 < M; ++t1) {
+          const int pt = t1 + M * t2;
+          T v[M];
+#pragma unroll
+          for (int r = 0; r < M; ++r) v[r] = u[lidx<M, D>(r, t1, t2)];
+          T tr[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            T s = tb.te[k][0] * v[0];
+#pragma unroll
+            for (int r = 1; r < M; ++r) s = fma(tb.te[k][r], v[r], s);
+            tr[k] = s;
+          }
+          // upper neighbour's lower-face pair, lower neighbour's upper-face pair
+          T hu = __shfl_down_sync(full, tr[0], dl), hg = __shfl_down_sync(full, tr[1], dl);
+          T lu = __shfl_up_sync(full, tr[2], dl), lg = __shfl_up_sync(full, tr[3], dl);
+          if (lc == bd - 1) load2(hhi + 2 * pt, hu, hg);
+          if (lc == 0) load2(hlo + 2 * pt, lu, lg);
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            T s = D == 0 ? tb.K[D][q * M] * v[0] : fma(tb.K[D][q * M], v[0], R[lidx<M, D>(q, t1, t2)]);
+#pragma unroll
+            for (int r = 1; r < M; ++r) s = fma(tb.K[D][q * M + r], v[r], s);
+            if (!hi_bnd) s = fma(tb.na[D][1][q], hu, fma(tb.nbv[D][1][q], hg, s));
+            if (!lo_bnd) s = fma(tb.na[D][0][q], lu, fma(tb.nbv[D][0][q], lg, s));
+            R[lidx<M, D>(q, t1, t2)] = s;
+          }
+        }
+      // own side of a domain-boundary face
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (s ? hi_bnd : lo_bnd) {
+#pragma unroll
+          for (int t2 = 0; t2 < M; ++t2)
+#pragma unroll
+            for (int t1 = 0; t1 < M; ++t1)
+#pragma unroll
+              for (int q = 0; q < M; ++q) {
+                T acc = R[lidx<M, D>(q, t1, t2)];
+#pragma unroll
+                for (int r = 0; r < M; ++r) acc = fma(tb.corr[D][s][q * M + r], u[lidx<M, D>(r, t1, t2)], acc);
+                R[lidx<M, D>(q, t1, t2)] = acc;
+              }
+        }
+      }
+    };
+    // z axis: neighbours in the warps of the adjacent z layers, exchanged through shared
+    // memory: publish the weighted traces, line operator and boundary correction, barrier,
+    // then the neighbours' coupling. A face on the brick boundary is read by no cell of the
+    // brick, so its slots take the neighbour's trace from the halo instead.
+    auto axis_z = [&]() {
+      constexpr int D = 2;
+      constexpr int bd = bz, nd = n2, nstep = bx * by;
+      const int gc = gz, nlim = nz, lc = lz;
       if (act) {
 #pragma unroll
         for (int t2 = 0; t2 < M; ++t2)
@@ -410,10 +474,10 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
               for (int r = 1; r < M; ++r) s = fma(tb.te[k][r], v[r], s);
               tr[k] = s;
             }
-            store4(trb + tid * LY::NT + 4 * pt, tr[0], tr[1], tr[2], tr[3]);
+            store4(trz + tid * LY::NT + 4 * pt, tr[0], tr[1], tr[2], tr[3]);
 #pragma unroll
             for (int q = 0; q < M; ++q) {
-              T s = D == 0 ? tb.K[D][q * M] * v[0] : fma(tb.K[D][q * M], v[0], R[lidx<M, D>(q, t1, t2)]);
+              T s = fma(tb.K[D][q * M], v[0], R[lidx<M, D>(q, t1, t2)]);
 #pragma unroll
               for (int r = 1; r < M; ++r) s = fma(tb.K[D][q * M + r], v[r], s);
               R[lidx<M, D>(q, t1, t2)] = s;
@@ -435,10 +499,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
                 }
           }
         }
-        // A face on the brick boundary is read by no cell of the brick, so its slots take
-        // the neighbour's trace from the halo instead: every neighbour trace is then at a
-        // fixed offset from one address per side.
-        const int p = D == 0 ? ly + by * lz : (D == 1 ? lx + bx * lz : lx + bx * ly);
+        const int p = lx + bx * ly;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
           if (side ? lc == bd - 1 : lc == 0) {
@@ -447,7 +508,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
             for (int pt = 0; pt < M2; ++pt) {
               T hu, hg;
               load2(h + 2 * pt, hu, hg);
-              store2(trb + tid * LY::NT + 4 * pt + 2 * side, hu, hg);
+              store2(trz + tid * LY::NT + 4 * pt + 2 * side, hu, hg);
             }
           }
         }
@@ -460,7 +521,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
           const bool inb = s ? lc + 1 < bd : lc > 0;
           // neighbour trace pair of face point pt at nsrc[4 pt]: the neighbour's lower (s = 1) or
           // upper (s = 0) face, or this cell's outward slots holding the halo trace
-          const T *nsrc = trb + (inb ? (s ? tid + nstep : tid - nstep) : tid) * LY::NT + (s == inb ? 0 : 2);
+          const T *nsrc = trz + (inb ? (s ? tid + nstep : tid - nstep) : tid) * LY::NT + (s == inb ? 0 : 2);
 #pragma unroll
           for (int t2 = 0; t2 < M; ++t2)
 #pragma unroll
@@ -476,13 +537,11 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
         }
       }
     };
-    // x staging (buf1) was read above; axis 1 reuses buf1, axis 2 reuses buf0 (whose
-    // axis-0 readers all passed the axis-1 barrier)
-    axis(std::integral_constant<int, 0>{}, buf0);
-    axis(std::integral_constant<int, 1>{}, buf1);
-    axis(std::integral_constant<int, 2>{}, buf0);
-    // transposed interpolation to the GLL coefficients, staged for a coalesced store
-    // (buf1's last readers, the axis-1 face terms, all passed the axis-2 barrier)
+    axis_xy(std::integral_constant<int, 0>{});
+    axis_xy(std::integral_constant<int, 1>{});
+    axis_z();
+    // transposed interpolation to the GLL coefficients, staged in this warp's own rows of xs
+    // for a coalesced store
     if (act) {
       T t2[P * M2];  // [j2][q1][q0]
 #pragma unroll

@@ -105,6 +105,33 @@ __global__ void __launch_bounds__(256) k_mma_probe_tf32(float *out, int iters) {
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Mixed probe: per iteration each warp issues four DMMA (2048 flops) and every thread
+// eight DFMA chains (8 x 2 x 32 = 512 flops per warp). Whether the two share one pipe
+// shows in the total rate: near the DFMA-only rate if they do, above it if not.
+__global__ void __launch_bounds__(256) k_mma_probe_mixed(double *out, int iters) {
+  double a = 1e-3 * (threadIdx.x + 1), b = 0.999;
+  double c[4][2], f[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { c[i][0] = 1e-3 * i; c[i][1] = 2e-3 * i; }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) f[i] = 1e-3 * (threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                   : "+d"(c[i][0]), "+d"(c[i][1])
+                   : "d"(a), "d"(b));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] = fma(f[i], b, 1e-3);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s += c[i][0] + c[i][1];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += f[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <typename T, typename K>
 cudaError_t probe_mma(K kern, double flops_per_warp_iter, cudaStream_t s, double *tflops) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -142,9 +169,14 @@ cudaError_t probe_mma(K kern, double flops_per_warp_iter, cudaStream_t s, double
 }  // namespace
 
 extern "C" dg_status dg_measure_mma_peak(int kind, void *stream, double *tflops) {
-  if (!tflops || (kind != 0 && kind != 1)) return dg_record_error(DG_ERR_INVALID_ARG);
-  const cudaError_t e = kind == 0 ? probe_mma<double>(k_mma_probe_f64, 4 * 512.0, (cudaStream_t)stream, tflops)
-                                  : probe_mma<float>(k_mma_probe_tf32, 4 * 2048.0, (cudaStream_t)stream, tflops);
+  if (!tflops || kind < 0 || kind > 2) return dg_record_error(DG_ERR_INVALID_ARG);
+  cudaError_t e;
+  if (kind == 0)
+    e = probe_mma<double>(k_mma_probe_f64, 4 * 512.0, (cudaStream_t)stream, tflops);
+  else if (kind == 1)
+    e = probe_mma<float>(k_mma_probe_tf32, 4 * 2048.0, (cudaStream_t)stream, tflops);
+  else
+    e = probe_mma<double>(k_mma_probe_mixed, 4 * 512.0 + 8 * 2 * 32.0, (cudaStream_t)stream, tflops);
   if (e == cudaErrorMemoryAllocation) return dg_record_error(DG_ERR_OOM);
   return e == cudaSuccess ? DG_OK : dg_record_error(DG_ERR_CUDA);
 }

@@ -314,7 +314,8 @@ def dg_measure_fma_peak(precision: int, stream: Optional[int] = None) -> float:
 
 
 def dg_measure_mma_peak(kind: int, stream: Optional[int] = None) -> float:
-    """Measured tensor-core throughput (TFLOP/s): kind 0 FP64 DMMA m8n8k4, 1 TF32 m16n8k8."""
+    """Measured tensor-core throughput (TFLOP/s): kind 0 FP64 DMMA m8n8k4, 1 TF32 m16n8k8,
+    2 DMMA and DFMA issued together."""
     t = ctypes.c_double()
     _check(lib().dg_measure_mma_peak(kind, stream, ctypes.byref(t)), "dg_measure_mma_peak")
     return t.value
