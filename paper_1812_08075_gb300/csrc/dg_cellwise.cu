@@ -153,12 +153,15 @@ CTab<P, T> make_tab(const ScalarArgs<T> &a, const HostTables &ht) {
 // Weighted trace of a neighbour cell's face normal to axis D from its GLL coefficients
 // `src`: SIDE 1 is the neighbour's lower face (xi_D = 0), SIDE 0 its upper face. The pair
 // (W_t u, W_t du/dxi_D) of face point pt goes to dst[2 pt], dst[2 pt + 1].
-template <int P, typename T, int D, int SIDE>
-__device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab<P, T> &tb, T *dst) {
+// One code path for every axis and side (strides and side at run time, a single call
+// site): six specialisations made the kernel's code outgrow the instruction cache.
+template <int P, typename T>
+__device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab<P, T> &tb, T *dst, int stn, int st1,
+                                            int st2, int side) {
   constexpr int M = P, P2 = P * P, M2 = M * M;
-  constexpr int stn = D == 0 ? 1 : (D == 1 ? P : P2);
-  constexpr int st1 = D == 0 ? P : 1;
-  constexpr int st2 = D == 2 ? P : P2;
+  T gd[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) gd[j] = side ? tb.gd0[j] : tb.gd1[j];
   T v[P2], dv[P2];
 #pragma unroll
   for (int n2 = 0; n2 < P; ++n2)
@@ -167,10 +170,10 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
       T line[P];
 #pragma unroll
       for (int j = 0; j < P; ++j) line[j] = __ldg(src + n1 * st1 + n2 * st2 + j * stn);
-      v[n1 + P * n2] = SIDE ? line[0] : line[P - 1];
-      T s = (SIDE ? tb.gd0[0] : tb.gd1[0]) * line[0];
+      v[n1 + P * n2] = side ? line[0] : line[P - 1];
+      T s = gd[0] * line[0];
 #pragma unroll
-      for (int j = 1; j < P; ++j) s = fma(SIDE ? tb.gd0[j] : tb.gd1[j], line[j], s);
+      for (int j = 1; j < P; ++j) s = fma(gd[j], line[j], s);
       dv[n1 + P * n2] = s;
     }
   T tv[M * P], tdv[M * P];  // after the sweep along t1: [n2][q1]
@@ -335,13 +338,12 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
       if (!ok) continue;
       const T *src = xr + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3;
       T *dst = hl + hoff(d) + (side * nd + p) * 2 * M2;
-      if (d == 0) {
-        if (side) halo_trace<P, T, 0, 1>(src, tb, dst); else halo_trace<P, T, 0, 0>(src, tb, dst);
-      } else if (d == 1) {
-        if (side) halo_trace<P, T, 1, 1>(src, tb, dst); else halo_trace<P, T, 1, 0>(src, tb, dst);
-      } else {
-        if (side) halo_trace<P, T, 2, 1>(src, tb, dst); else halo_trace<P, T, 2, 0>(src, tb, dst);
-      }
+      // strides of the normal direction and of the two tangential directions in the
+      // neighbour's GLL coefficients (j0 + p (j1 + p j2))
+      const int stn = d == 0 ? 1 : (d == 1 ? P : P2);
+      const int st1 = d == 0 ? P : 1;
+      const int st2 = d == 2 ? P : P2;
+      halo_trace<P, T>(src, tb, dst, stn, st1, st2, side);
     }
     __syncthreads();
     // own cell: weighted Gauss-point values u~ (interpolation tables carry the weights)
