@@ -450,6 +450,14 @@ dg_status dg_measure_fma_peak(int precision, void *stream, double *tflops);
  * cores of this part. Errors: DG_ERR_INVALID_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_measure_mma_peak(int kind, void *stream, double *tflops);
 
+/* Device-side faults recorded by kernels on the current device since the last clear
+ * (bit mask in *faults, 0 if none): bit 0 = a wait of the persistent cellwise kernel for
+ * its bulk copies into shared memory (x rows and brick-boundary neighbours, FP32 k = 2)
+ * gave up after about one second; that launch stopped early and its output is invalid.
+ * Synchronises with the device (it reads device memory). clear != 0 resets the mask.
+ * Errors: DG_ERR_INVALID_ARG (faults NULL), DG_ERR_CUDA. */
+dg_status dg_device_faults(int clear, unsigned *faults);
+
 /* Reference-element tables the CUDA path uses (host, double), for inspection:
  * gauss_nodes/weights [m] on [0,1], gll_nodes [k+1], interp [m][k+1] (GLL Lagrange
  * basis at Gauss points), dcol [m][m] (derivative of the Gauss-point Lagrange basis at

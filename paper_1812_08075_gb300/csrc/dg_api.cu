@@ -1119,7 +1119,12 @@ dg_status predict_t(const dg_operator *op, int nrhs, const Candidate &c, double 
                                q);
     nk = 3;
   }
-  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  if (e != cudaSuccess) {
+    // a configuration that cannot launch (its shared-memory or occupancy query failed):
+    // clear the runtime's last-error state, which the next launch would otherwise report
+    cudaGetLastError();
+    return fail(DG_ERR_CUDA);
+  }
   double t = 0.0;
   for (int k = 0; k < nk; ++k) t += kernel_cost_ms(flops[k] * nrhs, bytes[k] * nrhs, q[k], es == 8, op->p);
   *ms = t;

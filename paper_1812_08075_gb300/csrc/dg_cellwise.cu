@@ -31,6 +31,57 @@
 
 namespace dgc {
 
+// Set by a cellwise launch whose wait for its bulk copies gave up (bit 0); read and cleared
+// by dg_device_faults.
+__device__ unsigned g_cellwise_fault = 0;
+
+// Bulk copies global -> shared completed on an mbarrier (Blackwell TMA engine, untiled form)
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 16-byte aligned source and destination, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Generic-proxy accesses of this thread ordered before later async-proxy (bulk copy) ones
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Wait for the phase of the given parity, at most about one second (clock cycles); false
+// when it gave up (the fault word is then set and the caller carries on).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000LL) {
+      atomicOr(&g_cellwise_fault, 1u);
+      return false;
+    }
+  }
+}
+
 // Tables and per-axis operators, passed by value (constant bank).
 template <int P, typename T>
 struct CTab {
@@ -85,14 +136,31 @@ struct CLayout {
   static constexpr int buf = NT > sX ? NT : sX;
 };
 
+// FP32 with x rows staged as laid out in memory (k = 2) copies each item's x rows and the
+// GLL coefficients of its brick-boundary neighbours into shared memory with bulk copies
+// (cp.async.bulk, completed on mbarriers) one item ahead. Neighbour staging: the 2 bz rows
+// across y and the 2 by rows across z (bx cells each, as in memory) and the 2 by bz single
+// cells across x, each in a slot holding the 16-byte-aligned span around the cell. The slot
+// stride (36 words, 4 mod 32) keeps the lanes reading consecutive slots on 8 banks.
+template <int P, typename T>
+__host__ __device__ constexpr bool cellwise_stage() {
+  return sizeof(T) == 4 && (P * P * P) % 2 == 1;
+}
+constexpr int kHaloSlot = 36;
+template <int P>
+inline constexpr size_t halo_stage_words(int bx, int by, int bz) {
+  return (size_t)(2 * bz + 2 * by) * bx * P * P * P + (size_t)2 * by * bz * kHaloSlot;
+}
+
 // Shared memory words: the x / y staging rows, one trace buffer (the z exchange; x and y
 // neighbours are lanes of the same warp and exchange by shuffles) and the brick-boundary
 // traces of the three axes.
 template <int P>
-inline size_t cellwise_words(int bx, int by, int bz) {
+inline size_t cellwise_words(int bx, int by, int bz, bool stage) {
   using LY = CLayout<P>;
   const size_t nb = (size_t)bx * by * bz;
-  return (size_t)(LY::sX + LY::NT) * nb + (size_t)LY::NT * (by * bz + bx * bz + bx * by);
+  return (size_t)(LY::sX + LY::NT) * nb + (size_t)LY::NT * (by * bz + bx * bz + bx * by) +
+         (stage ? halo_stage_words<P>(bx, by, bz) : 0);
 }
 
 // Host construction of CTab from the reference tables (FP64) and the affine constants.
@@ -155,7 +223,7 @@ CTab<P, T> make_tab(const ScalarArgs<T> &a, const HostTables &ht) {
 // (W_t u, W_t du/dxi_D) of face point pt goes to dst[2 pt], dst[2 pt + 1].
 // One code path for every axis and side (strides and side at run time, a single call
 // site): six specialisations made the kernel's code outgrow the instruction cache.
-template <int P, typename T>
+template <int P, typename T, bool SHARED>
 __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab<P, T> &tb, T *dst, int stn, int st1,
                                             int st2, int side) {
   constexpr int M = P, P2 = P * P, M2 = M * M;
@@ -169,7 +237,7 @@ __device__ __forceinline__ void halo_trace(const T *__restrict__ src, const CTab
     for (int n1 = 0; n1 < P; ++n1) {
       T line[P];
 #pragma unroll
-      for (int j = 0; j < P; ++j) line[j] = __ldg(src + n1 * st1 + n2 * st2 + j * stn);
+      for (int j = 0; j < P; ++j) line[j] = SHARED ? src[n1 * st1 + n2 * st2 + j * stn] : __ldg(src + n1 * st1 + n2 * st2 + j * stn);
       v[n1 + P * n2] = side ? line[0] : line[P - 1];
       T s = gd[0] * line[0];
 #pragma unroll
@@ -218,7 +286,7 @@ constexpr int cellwise_min_blocks() {
 template <int P, typename T, int BZ>
 __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x, T *__restrict__ y, int64_t sdof,
-               int nbx, int nby, int nbricks, int nitems, int nrhs) {
+               int nbx, int nby, int nbricks, int nitems, int nrhs, int bulk_ok) {
   constexpr int M = P, P2 = P * P, P3 = P2 * P, M2 = M * M, M3 = M2 * M;
   using LY = CLayout<P>;
   constexpr int sX = LY::sX;
@@ -228,6 +296,13 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
   T *trz = reinterpret_cast<T *>(smem_raw);  // z traces: [cell][pt][u0, g0, u1, g1]
   T *xs = trz + LY::NT * nb;                   // x / y staging: [cell of the brick][sX]
   T *hl = xs + LY::sX * nb;                    // halo traces: [axis][side][plane][pt][u, g]
+  constexpr bool STAGE = cellwise_stage<P, T>();
+  T *const hsy = hl + LY::NT * (n0 + n1 + n2);  // neighbour rows across y: [side][z][bx cells]
+  T *const hsz = hsy + 2 * bz * bx * P3;        // neighbour rows across z: [side][y][bx cells]
+  T *const hsx = hsz + 2 * by * bx * P3;        // neighbour cells across x: [side][y + by z][slot]
+  // mbar[w]: x rows of warp w; mbar[nwarps]: the neighbours (one arrival per thread)
+  __shared__ __align__(8) unsigned long long mbar[(32 * BZ) / 32 + 1];
+  __shared__ unsigned blk_fault;  // a wait of this block gave up (read by all after a barrier)
   auto hoff = [](int d) { return d == 0 ? 0 : (d == 1 ? LY::NT * n0 : LY::NT * (n0 + n1)); };
   const int tid = threadIdx.x;
   const int lx = tid % bx, ly = (tid / bx) % by, lz = tid / (bx * by);
@@ -248,11 +323,12 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
   // The next item's x rows and the neighbour cells it evaluates brick-boundary traces from
   // go to L2 one item ahead, so that its staging and halo loads hit L2 instead of DRAM:
   // by*bz rows, 2*bz rows across y, 2*by rows across z, 2*by*bz single cells across x,
-  // one bulk prefetch each, spread over the even lanes of every warp.
-  auto prefetch_item = [&](int r, int px, int py, int pz) {
+  // one bulk prefetch each, spread over the even lanes of every warp. With bulk staging of
+  // the next item only its rows are prefetched (its neighbours are copied one item ahead).
+  auto prefetch_item = [&](int r, int px, int py, int pz, bool rows_only) {
     const T *xb = x + r * sdof;
     const int qx = min(bx, nx - px);
-    constexpr int nranges = by * bz + 2 * bz + 2 * by + 2 * by * bz;
+    const int nranges = rows_only ? by * bz : by * bz + 2 * bz + 2 * by + 2 * by * bz;
     if (tid & 1) return;
     for (int t0 = tid >> 1; t0 < nranges; t0 += nb / 2) {
       int t = t0, cy, cz, cx = px, ncx = qx;
@@ -271,41 +347,133 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
       dg_prefetch_l2(x, xend, xb + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3, (size_t)ncx * P3 * sizeof(T));
     }
   };
-  // each item is decoded once: the next item's indices, computed for its prefetch, are
-  // carried into the next iteration
+  // Bulk staging applies to a whole brick inside the mesh (its rows and neighbour cells
+  // then start on 16-byte boundaries: bulk_ok says x, the right-hand-side stride and nx
+  // allow it).
+  auto full_brick = [&](int px, int py, int pz) {
+    return STAGE && bulk_ok && px + bx <= nx && py + by <= ny && pz + bz <= nz;
+  };
+  // words from the 16-byte boundary below cell c's first coefficient to it
+  auto cell_off = [](int64_t c) { return (int)((c * P3) & 3); };
+  // neighbours of brick (px, py, pz): copy unit tid (rows across y, rows across z, cells
+  // across x); every thread arrives once on mbar[nwarps], announcing its copy's bytes
+  auto issue_halo = [&](int r, int px, int py, int pz) {
+    const T *xb = x + r * sdof;
+    constexpr unsigned rb = bx * P3 * sizeof(T);
+    unsigned bytes = 0;
+    const T *src = x;
+    T *dst = hsy;
+    int t = tid;
+    if (t < 2 * bz) {
+      const int side = t / bz, cz = pz + t - side * bz, cy = side ? py + by : py - 1;
+      if (side ? cy < ny : cy >= 0) {
+        src = xb + (px + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3;
+        dst = hsy + t * bx * P3;
+        bytes = rb;
+      }
+    } else if ((t -= 2 * bz) < 2 * by) {
+      const int side = t / by, cy = py + t - side * by, cz = side ? pz + bz : pz - 1;
+      if (side ? cz < nz : cz >= 0) {
+        src = xb + (px + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3;
+        dst = hsz + t * bx * P3;
+        bytes = rb;
+      }
+    } else if ((t -= 2 * by) < 2 * n0) {
+      const int side = t / n0, pl = t - side * n0, cx = side ? px + bx : px - 1;
+      if (side ? cx < nx : cx >= 0) {
+        const int64_t c = cx + (int64_t)nx * (py + pl % by + (int64_t)ny * (pz + pl / by));
+        const int o = cell_off(c);
+        src = xb + c * P3 - o;
+        dst = hsx + t * kHaloSlot;
+        bytes = (unsigned)(((o + P3 + 3) & ~3) * sizeof(T));
+      }
+    }
+    if (bytes) {
+      mbar_arrive_expect(&mbar[nwarps], bytes);
+      bulk_g2s(dst, src, bytes, &mbar[nwarps]);
+    } else {
+      mbar_arrive(&mbar[nwarps]);
+    }
+  };
+  // x rows of this warp's z layer of brick (px, py, pz), issued by lane 0
+  auto issue_rows = [&](int r, int px, int py, int pz) {
+    const T *xb = x + r * sdof;
+    constexpr unsigned rb = bx * P3 * sizeof(T);
+    mbar_arrive_expect(&mbar[warp], by * rb);
+    for (int ry = 0; ry < by; ++ry)
+      bulk_g2s(xs + (ry + by * warp) * bx * sX, xb + (px + (int64_t)nx * (py + ry + (int64_t)ny * (pz + warp))) * P3,
+               rb, &mbar[warp]);
+  };
+  // the same neighbour layout filled by plain loads (cells across x at offset 0), for an
+  // item that is not bulk-staged
+  auto fill_halo = [&](const T *xb, int px, int py, int pz) {
+    constexpr int wy = 2 * bz * bx * P3, wz = 2 * by * bx * P3, wx = 2 * n0 * P3;
+    for (int j = tid; j < wy + wz + wx; j += nb) {
+      int t = j;
+      int cx, cy, cz, e;
+      T *dst;
+      if (t < wy) {
+        const int row = t / (bx * P3), side = row / bz;
+        e = t - row * bx * P3;
+        cx = px + e / P3; e -= (e / P3) * P3;
+        cz = pz + row - side * bz; cy = side ? py + by : py - 1;
+        dst = hsy + t;
+      } else if ((t -= wy) < wz) {
+        const int row = t / (bx * P3), side = row / by;
+        e = t - row * bx * P3;
+        cx = px + e / P3; e -= (e / P3) * P3;
+        cy = py + row - side * by; cz = side ? pz + bz : pz - 1;
+        dst = hsz + t;
+      } else {
+        t -= wz;
+        const int slot = t / P3, side = slot / n0, pl = slot - side * n0;
+        e = t - slot * P3;
+        cy = py + pl % by; cz = pz + pl / by; cx = side ? px + bx : px - 1;
+        dst = hsx + slot * kHaloSlot + e;
+      }
+      if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
+      *dst = __ldg(xb + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3 + e);
+    }
+  };
   int rhs = 0, ox = 0, oy = 0, oz = 0;
   if (blockIdx.x < (unsigned)nitems) decode(blockIdx.x, rhs, ox, oy, oz);
+  bool cur_bulk = false;  // this item's rows and neighbours are bulk copies in flight
+  unsigned ph = 0;        // parity of the mbarrier phase the bulk items wait for
+  if constexpr (STAGE) {
+    if (tid == 0) {
+      for (int w = 0; w <= nwarps; ++w) mbar_init(&mbar[w], w < nwarps ? 1u : (unsigned)nb);
+      blk_fault = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (blockIdx.x < (unsigned)nitems && full_brick(ox, oy, oz)) {
+      cur_bulk = true;
+      issue_halo(rhs, ox, oy, oz);
+      if (lane == 0) issue_rows(rhs, ox, oy, oz);
+    }
+  }
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     int nr = 0, nox = 0, noy = 0, noz = 0;
     const bool more = item + (int)gridDim.x < nitems;
+    bool nxt_bulk = false;
     if (more) {
       decode(item + gridDim.x, nr, nox, noy, noz);
-      prefetch_item(nr, nox, noy, noz);
+      nxt_bulk = full_brick(nox, noy, noz);
+      prefetch_item(nr, nox, noy, noz, nxt_bulk);
     }
     const int nax = min(bx, nx - ox), nay = min(by, ny - oy), naz = min(bz, nz - oz);
     const T *xr = x + rhs * sdof;
     T *yr = y + rhs * sdof;
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     const bool act = lx < nax && ly < nay && lz < naz;
-    // stage x: warp w copies the by rows of its own cells (z layer w of the brick), coalesced
     static_assert(nwarps == bz, "one z layer of the brick per warp");
-    for (int ry = 0; ry < by; ++ry) {
-      const int rz = warp, row = ry + by * rz;
-      if (ry >= nay || rz >= naz) continue;
-      const T *src = xr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
-      T *dst = xs + row * bx * sX;
-      if constexpr (sX == P3 && sizeof(T) == 4) {
-        if ((nax * P3) % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-          // the staged row is laid out as in memory: copy it as 16-byte vectors
-          const float4 *s4 = reinterpret_cast<const float4 *>(src);
-          float4 *d4 = reinterpret_cast<float4 *>(dst);
-          for (int j = lane; j < nax * P3 / 4; j += 32) d4[j] = __ldg(s4 + j);
-          continue;
-        }
-      }
-      for (int j = lane; j < nax * P3; j += 32) {
-        const int cl = j / P3;
-        dst[cl * sX + (j - cl * P3)] = __ldg(src + j);
+    bool waited = true;  // false when a bulk-copy wait gave up
+    if constexpr (STAGE) {
+      if (cur_bulk) {
+        waited = mbar_wait(&mbar[nwarps], ph);
+      } else {
+        fill_halo(xr, ox, oy, oz);
+        __syncthreads();
       }
     }
     // weighted traces of the neighbours across the brick boundary, one face per thread
@@ -321,31 +489,66 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
       const int side = rem >= nd ? 1 : 0;
       const int p = rem - side * nd;
       int cx, cy, cz;  // neighbour cell
+      int sp;          // its row (across y or z) or slot (across x) in the neighbour staging
       bool ok;
       if (d == 0) {
         const int py = p % by, pz = p / by;
         cy = oy + py; cz = oz + pz; cx = side ? ox + bx : ox - 1;
         ok = py < nay && pz < naz && (side ? ox + bx < nx : ox > 0);
+        sp = side * n0 + p;
       } else if (d == 1) {
         const int px = p % bx, pz = p / bx;
         cx = ox + px; cz = oz + pz; cy = side ? oy + by : oy - 1;
         ok = px < nax && pz < naz && (side ? oy + by < ny : oy > 0);
+        sp = side * bz + pz;
       } else {
         const int px = p % bx, py = p / bx;
         cx = ox + px; cy = oy + py; cz = side ? oz + bz : oz - 1;
         ok = px < nax && py < nay && (side ? oz + bz < nz : oz > 0);
+        sp = side * by + py;
       }
       if (!ok) continue;
-      const T *src = xr + (cx + (int64_t)nx * (cy + (int64_t)ny * cz)) * P3;
+      const int64_t c = cx + (int64_t)nx * (cy + (int64_t)ny * cz);
+      const T *src;
+      if constexpr (STAGE)
+        src = d == 0 ? hsx + sp * kHaloSlot + (cur_bulk ? cell_off(c) : 0)
+                     : (d == 1 ? hsy : hsz) + sp * bx * P3 + (cx - ox) * P3;
+      else
+        src = xr + c * P3;
       T *dst = hl + hoff(d) + (side * nd + p) * 2 * M2;
       // strides of the normal direction and of the two tangential directions in the
       // neighbour's GLL coefficients (j0 + p (j1 + p j2))
       const int stn = d == 0 ? 1 : (d == 1 ? P : P2);
       const int st1 = d == 0 ? P : 1;
       const int st2 = d == 2 ? P : P2;
-      halo_trace<P, T>(src, tb, dst, stn, st1, st2, side);
+      halo_trace<P, T, STAGE>(src, tb, dst, stn, st1, st2, side);
     }
-    __syncthreads();
+    // x: warp w's rows are those of its own cells (z layer w of the brick): bulk-copied,
+    // or loaded here coalesced
+    if (STAGE && cur_bulk) {
+      waited &= mbar_wait(&mbar[warp], ph);
+    } else {
+      for (int ry = 0; ry < by; ++ry) {
+        const int rz = warp, row = ry + by * rz;
+        if (ry >= nay || rz >= naz) continue;
+        const T *src = xr + (ox + (int64_t)nx * (oy + ry + (int64_t)ny * (oz + rz))) * P3;
+        T *dst = xs + row * bx * sX;
+        if constexpr (sX == P3 && sizeof(T) == 4) {
+          if ((nax * P3) % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            // the staged row is laid out as in memory: copy it as 16-byte vectors
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+            for (int j = lane; j < nax * P3 / 4; j += 32) d4[j] = __ldg(s4 + j);
+            continue;
+          }
+        }
+        for (int j = lane; j < nax * P3; j += 32) {
+          const int cl = j / P3;
+          dst[cl * sX + (j - cl * P3)] = __ldg(src + j);
+        }
+      }
+      __syncwarp();
+    }
     // own cell: weighted Gauss-point values u~ (interpolation tables carry the weights)
     T u[M3], R[M3];
 #pragma unroll
@@ -385,6 +588,24 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
           for (int j = 1; j < P; ++j) s = fma(tb.iw[q2 * P + j], t2[j * M2 + qq], s);
           u[q2 * M2 + qq] = s;
         }
+    }
+    if constexpr (STAGE) {
+      // the neighbour staging was read through the generic proxy: order that before the
+      // next item's bulk copies into it, which are issued after this barrier
+      fence_proxy_async();
+      if (!waited) blk_fault = 1u;
+      __syncthreads();
+      if (blk_fault) {
+        // a bulk copy did not complete within the time limit (the fault word records it):
+        // wait once more, bounded, for the copies in flight, then leave
+        mbar_wait(&mbar[nwarps], ph);
+        mbar_wait(&mbar[warp], ph);
+        return;
+      }
+      if (cur_bulk) ph ^= 1u;
+      if (nxt_bulk) issue_halo(nr, nox, noy, noz);
+    } else {
+      __syncthreads();
     }
     // x and y axes: a warp spans 8 x 4 cells of one z layer, so the x and y neighbours are
     // lanes +-1 and +-8. Per tensor line: the four weighted traces, the neighbours' pairs by
@@ -598,14 +819,25 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
         dst[j] = src[cl * sX + (j - cl * P3)];
       }
     }
-    // no block barrier here: the next item's first shared-memory writes are this warp's own
-    // staging rows and the halo region, whose last readers all passed the axis-2 barrier
+    // this warp's rows of the next item as a bulk copy, once the warp's reads of them are
+    // ordered before the copy's writes
+    if constexpr (STAGE) {
+      if (nxt_bulk) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) issue_rows(nr, nox, noy, noz);
+      }
+    }
     if (more) {
       rhs = nr;
       ox = nox;
       oy = noy;
       oz = noz;
+      cur_bulk = nxt_bulk;
     }
+    // no block barrier here: the next item's first shared-memory writes are this warp's own
+    // staging rows, the halo traces, whose last readers all passed the axis-2 barrier, and
+    // the neighbour staging, whose last readers passed the first barrier
   }
 }
 
@@ -614,7 +846,7 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
                 cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
   constexpr int bx = 8, by = 4, bz = BZ, nb = bx * by * bz;
   const CTab<P, T> tb = make_tab<P, T>(a, ht);
-  const size_t sm = cellwise_words<P>(bx, by, bz) * sizeof(T);
+  const size_t sm = cellwise_words<P>(bx, by, bz, cellwise_stage<P, T>()) * sizeof(T);
   auto k = k_cellwise<P, T, BZ>;
   cudaError_t e;
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
@@ -638,7 +870,10 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
     return cudaSuccess;
   }
   if (ev) cudaEventRecord(ev[0], s);
-  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, (int)nbx, (int)nby, (int)nbricks, (int)nitems, nrhs);
+  // bulk staging needs every brick row and neighbour span on a 16-byte boundary
+  const int bulk_ok = cellwise_stage<P, T>() && (reinterpret_cast<uintptr_t>(x) & 15) == 0 && sdof % 4 == 0 &&
+                      a.nx % 4 == 0;
+  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, (int)nbx, (int)nby, (int)nbricks, (int)nitems, nrhs, bulk_ok);
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
@@ -656,8 +891,8 @@ size_t cellwise_smem_bytes(int p, int cells, int es) {
   const int bz = cellwise_bz(cells);
   if (!bz) return 0;
   switch (p) {
-    case 2: return dgc::cellwise_words<2>(8, 4, bz) * es;
-    case 3: return dgc::cellwise_words<3>(8, 4, bz) * es;
+    case 2: return dgc::cellwise_words<2>(8, 4, bz, false) * es;
+    case 3: return dgc::cellwise_words<3>(8, 4, bz, es == 4) * es;
     default: return 0;
   }
 }
@@ -692,3 +927,16 @@ template cudaError_t launch_cellwise_apply<float>(int, const ScalarArgs<float> &
 template cudaError_t launch_cellwise_apply<double>(int, const ScalarArgs<double> &, const HostTables &,
                                                    const double *, double *, int, int64_t, int, cudaStream_t,
                                                    const cudaEvent_t *, int *, LaunchInfo *);
+
+extern "C" dg_status dg_device_faults(int clear, unsigned *faults) {
+  if (!faults) return dg_record_error(DG_ERR_INVALID_ARG);
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, dgc::g_cellwise_fault, sizeof v) != cudaSuccess) return dg_record_error(DG_ERR_CUDA);
+  if (clear && v) {
+    const unsigned zero = 0;
+    if (cudaMemcpyToSymbol(dgc::g_cellwise_fault, &zero, sizeof zero) != cudaSuccess)
+      return dg_record_error(DG_ERR_CUDA);
+  }
+  *faults = v;
+  return DG_OK;
+}

@@ -32,6 +32,17 @@ __device__ __forceinline__ void dg_prefetch_l2(const void *lo, const void *hi, c
   if (e > a)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
 }
+
+// Asynchronous copy of one 4-, 8- or 16-byte element global -> shared (cp.async): the
+// thread issues it without waiting, and dg_cp_async_wait_all() waits for all of its own.
+template <typename T>
+__device__ __forceinline__ void dg_cp_async(T *dst, const T *src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void dg_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 #endif
 
 // Element type of the input and output vectors of kernels computing in T.

@@ -19,6 +19,8 @@
 //   k_back  - adds the six face residuals to R_vol along the normal direction and applies
 //             the transposed interpolation (A^(i),T, Algorithm 1 Part 3) to produce y.
 #pragma once
+#include <type_traits>
+
 #include "dg_df64.cuh"
 #include "dg_internal.h"
 
@@ -233,10 +235,18 @@ __device__ __forceinline__ FaceId decode_face(const ScalarArgs<T> &a, int64_t f)
   return r;
 }
 
+// The FP32 and double-float face kernels on curved faces copy their faces' traces and
+// stored geometry into shared memory with asynchronous copies (all of a thread's loads in
+// flight at once); the FP64 kernel, bound by its FP64 arithmetic, loads them directly.
+template <typename T>
+__host__ __device__ constexpr bool face_async_stage() {
+  return !std::is_same<T, double>::value;
+}
+
 template <int M, typename T>
 __host__ __device__ constexpr size_t face_smem_bytes(int fpb, int geo) {
   return align16<T>(sizeof(SmemTables<1, M, T>)) + align16<T>(fpb * sizeof(FaceId)) +
-         (geo == GEO_AFFINE ? 0 : size_t(9) * fpb * M * M * sizeof(T));
+         (geo == GEO_AFFINE ? 0 : size_t(face_async_stage<T>() ? 16 : 9) * fpb * M * M * sizeof(T));
 }
 
 // trace / face-residual addressing: [cell][lf][qty][M^2]
@@ -311,21 +321,30 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
     return;
   }
   // curved faces (stored geometry): stage traces, pointwise terms, tangential back-projection
+  constexpr bool ASYNC = face_async_stage<T>();
   T *sU = SM;                   // [face][4][M2]: u-, dn-, u+, dn+
   T *sR = SM + 4 * fpb * M2;    // [face][5][M2]: Rv, Rt1-, Rt2-, Rt1+, Rt2+
+  T *sG = SM + 9 * fpb * M2;    // [face][7][M2]: the faces' stored geometry (ASYNC)
   for (int i = tid; i < nf * 4 * M2; i += nt) {
     const int lfc = i / (4 * M2), r = i - lfc * (4 * M2);
     const int slot = r / M2, qf = r - slot * M2;
     const FaceId &F = sF[lfc];
     const int ax = F.axis;
-    T v = T(0);
+    const T *src = nullptr;
     if (slot < 2) {
-      if (F.cm >= 0) v = traces[tr_idx<M>(F.cm, 2 * ax + 1, slot, qf)];
-      else v = traces[tr_idx<M>(F.cp, 2 * ax, slot, qf)];  // boundary face at the lower end
+      if (F.cm >= 0) src = traces + tr_idx<M>(F.cm, 2 * ax + 1, slot, qf);
+      else src = traces + tr_idx<M>(F.cp, 2 * ax, slot, qf);  // boundary face at the lower end
     } else if (F.cm >= 0 && F.cp >= 0) {
-      v = traces[tr_idx<M>(F.cp, 2 * ax, slot - 2, qf)];
+      src = traces + tr_idx<M>(F.cp, 2 * ax, slot - 2, qf);
     }
-    sU[i] = v;
+    if (ASYNC && src) dg_cp_async(sU + i, src);
+    else sU[i] = src ? *src : T(0);
+  }
+  if constexpr (ASYNC) {
+    // the block's faces are consecutive: their geometry is one contiguous range
+    const T *g0 = a.gface + f0 * (7 * M2);
+    for (int i = tid; i < nf * 7 * M2; i += nt) dg_cp_async(sG + i, g0 + i);
+    dg_cp_async_wait_all();
   }
   __syncthreads();
   for (int i = tid; i < nf * M2; i += nt) {
@@ -334,7 +353,7 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
     const FaceId &F = sF[lfc];
     const int ax = F.axis, t1 = F.t1, t2 = F.t2;
     const int qs = qf % M, qt = qf / M;
-    const T *gf = a.gface + f * (7 * M2) + qf;
+    const T *gf = ASYNC ? sG + lfc * (7 * M2) + qf : a.gface + f * (7 * M2) + qf;
     const T *u0 = sU + lfc * 4 * M2;
     T *R = sR + lfc * 5 * M2;
     // tangential reference derivatives of side "-" (slot 0) or the single boundary side

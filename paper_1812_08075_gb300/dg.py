@@ -34,7 +34,7 @@ EXPORTED = [
     "dg_operator_autotune", "dg_rhs", "dg_operator_diagonal", "dg_operator_block_jacobi",
     "dg_operator_predict", "dg_operator_time", "dg_operator_autotune_prior", "dg_apply_semilinear",
     "dg_operator_create_aniso", "dg_mixed_cg_solve", "dg_measure_fma_peak",
-    "dg_measure_mma_peak",
+    "dg_measure_mma_peak", "dg_device_faults",
 ]
 
 
@@ -126,6 +126,7 @@ def lib():
                                              i32, vp, vp, vp]
         L.dg_measure_fma_peak.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.dg_measure_mma_peak.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.dg_device_faults.argtypes = [i32, ctypes.POINTER(ctypes.c_uint)]
         L.dg_operator_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double * 3), ctypes.POINTER(i64)]
         for name in EXPORTED:
             if name not in ("dg_status_string",):
@@ -319,6 +320,14 @@ def dg_measure_mma_peak(kind: int, stream: Optional[int] = None) -> float:
     t = ctypes.c_double()
     _check(lib().dg_measure_mma_peak(kind, stream, ctypes.byref(t)), "dg_measure_mma_peak")
     return t.value
+
+
+def dg_device_faults(clear: bool = True) -> int:
+    """Bit mask of device-side faults recorded since the last clear (0 if none): bit 0, a
+    cellwise kernel's wait for its bulk copies gave up."""
+    v = ctypes.c_uint()
+    _check(lib().dg_device_faults(int(clear), ctypes.byref(v)), "dg_device_faults")
+    return v.value
 
 
 def dg_reference_tables(degree: int, m: int = 0):

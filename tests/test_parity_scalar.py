@@ -306,6 +306,17 @@ def test_cellwise_fp32_bricks_and_rhs(brick):
     assert run_cellwise((21, 7, 17), 2, dg.DG_FP32, nrhs=3, brick=brick, theta=1.0, mask=0b011110) <= TOL32
 
 
+@pytest.mark.parametrize("n,brick,nrhs", [((16, 8, 16), 256, 2), ((20, 9, 17), 256, 3), ((24, 13, 10), 128, 2),
+                                          ((12, 6, 5), 64, 2), ((8, 4, 8), 256, 1), ((36, 18, 34), 256, 4)])
+def test_cellwise_fp32_bulk_staged(n, brick, nrhs):
+    # nx a multiple of 4: whole bricks take their x rows and brick-boundary neighbours into
+    # shared memory by bulk copies one item ahead, ragged bricks by loads. In the largest
+    # case (500 items, more than one wave of blocks) blocks run several items, mixing both.
+    assert dg.dg_device_faults(clear=True) == 0
+    assert run_cellwise(n, 2, dg.DG_FP32, nrhs=nrhs, brick=brick) <= TOL32
+    assert dg.dg_device_faults() == 0
+
+
 def test_config4_fp64_full_size_sampled():
     # the FP64 operator of config 4 (128^3 affine cells, Q2): residuals of the refinement
     # and the all-FP64 CG; 16 right-hand sides through the tuned three-kernel apply
