@@ -22,7 +22,9 @@
 // start of the item from their GLL coefficients (face layer of nodes, end row of the GLL
 // derivative along the normal, facet sum factorisation to the face Gauss points with the
 // weights folded in), one brick-boundary face per thread. x and y are staged through
-// shared memory so that the global accesses are coalesced rows of the brick.
+// shared memory so that the global accesses are coalesced rows of the brick. In FP32 the
+// sweeps along y and z and four of the six interpolation sweeps run two tensor lines at a
+// time on the packed FP32 FMA (f32x2), with the same operations per line as the scalar code.
 #include <limits.h>
 
 #include <type_traits>
@@ -99,6 +101,45 @@ struct CTab {
 template <int M, int D>
 __device__ __forceinline__ constexpr int lidx(int r, int t1, int t2) {
   return D == 0 ? r + M * (t1 + M * t2) : (D == 1 ? t1 + M * (r + M * t2) : t1 + M * (t2 + M * r));
+}
+
+// Packed FP32 (f32x2: one instruction does the FMA of two lanes) on pairs of tensor lines
+// that share every coefficient. Each lane does the same operations in the same order as the
+// scalar code, so results are unchanged.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float c) { return make_float2(c, c); }
+
+// One sum-factorisation sweep over NO outputs, contracting NJ inputs:
+// out[o os + b] = sum_j c[o co + j cj] in[j is + b], for b over NR rows of M unit-stride
+// values. With PK, pairs of neighbouring values in a row (lines sharing the coefficients)
+// go through packed FMAs.
+template <int NO, int NJ, int NR, int M, bool PK, typename T>
+__device__ __forceinline__ void sweep(T *out, const int os, const T *in, const int is, const T *c, const int co,
+                                      const int cj) {
+#pragma unroll
+  for (int o = 0; o < NO; ++o)
+#pragma unroll
+    for (int row = 0; row < NR; ++row) {
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        const int b = row * M + q;
+        if constexpr (PK) {
+          if (q & 1) continue;  // the second value of a pair
+          if (q + 1 < M) {
+            float2 s = __fmul2_rn(bc(c[o * co]), pk(in[b], in[b + 1]));
+#pragma unroll
+            for (int j = 1; j < NJ; ++j) s = __ffma2_rn(bc(c[o * co + j * cj]), pk(in[j * is + b], in[j * is + b + 1]), s);
+            out[o * os + b] = s.x;
+            out[o * os + b + 1] = s.y;
+            continue;
+          }
+        }
+        T s = c[o * co] * in[b];
+#pragma unroll
+        for (int j = 1; j < NJ; ++j) s = fma(c[o * co + j * cj], in[j * is + b], s);
+        out[o * os + b] = s;
+      }
+    }
 }
 
 // Vector access to shared memory: four values (16-byte aligned) and pairs (8-byte
@@ -297,6 +338,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
   T *xs = trz + LY::NT * nb;                   // x / y staging: [cell of the brick][sX]
   T *hl = xs + LY::sX * nb;                    // halo traces: [axis][side][plane][pt][u, g]
   constexpr bool STAGE = cellwise_stage<P, T>();
+  constexpr bool PK = std::is_same<T, float>::value;  // packed FP32 FMAs on pairs of lines
   T *const hsy = hl + LY::NT * (n0 + n1 + n2);  // neighbour rows across y: [side][z][bx cells]
   T *const hsz = hsy + 2 * bz * bx * P3;        // neighbour rows across z: [side][y][bx cells]
   T *const hsx = hsz + 2 * by * bx * P3;        // neighbour cells across x: [side][y + by z][slot]
@@ -570,24 +612,8 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
       T t2[P * M2];  // [j2][q1][q0]
 #pragma unroll
       for (int j2 = 0; j2 < P; ++j2)
-#pragma unroll
-        for (int q1 = 0; q1 < M; ++q1)
-#pragma unroll
-          for (int q0 = 0; q0 < M; ++q0) {
-            T s = tb.iw[q1 * P] * t1[(j2 * P) * M + q0];
-#pragma unroll
-            for (int j = 1; j < P; ++j) s = fma(tb.iw[q1 * P + j], t1[(j2 * P + j) * M + q0], s);
-            t2[(j2 * M + q1) * M + q0] = s;
-          }
-#pragma unroll
-      for (int q2 = 0; q2 < M; ++q2)
-#pragma unroll
-        for (int qq = 0; qq < M2; ++qq) {
-          T s = tb.iw[q2 * P] * t2[qq];
-#pragma unroll
-          for (int j = 1; j < P; ++j) s = fma(tb.iw[q2 * P + j], t2[j * M2 + qq], s);
-          u[q2 * M2 + qq] = s;
-        }
+        sweep<M, P, 1, M, PK>(t2 + j2 * M2, M, t1 + j2 * P * M, M, tb.iw, P, 1);
+      sweep<M, P, M, M, PK>(u, M2, t2, M2, tb.iw, P, 1);
     }
     if constexpr (STAGE) {
       // the neighbour staging was read through the generic proxy: order that before the
@@ -628,6 +654,48 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
 #pragma unroll
         for (int t1 = 0; t1 < M; ++t1) {
           const int pt = t1 + M * t2;
+          if constexpr (PK && D == 1) {
+            // lines (t1, t2) and (t1 + 1, t2), neighbours in x, as one packed pair
+            if (t1 & 1) continue;
+            if (t1 + 1 < M) {
+              float2 v2[M];
+#pragma unroll
+              for (int r = 0; r < M; ++r) v2[r] = pk(u[lidx<M, D>(r, t1, t2)], u[lidx<M, D>(r, t1 + 1, t2)]);
+              float2 tr2[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                float2 s = __fmul2_rn(bc(tb.te[k][0]), v2[0]);
+#pragma unroll
+                for (int r = 1; r < M; ++r) s = __ffma2_rn(bc(tb.te[k][r]), v2[r], s);
+                tr2[k] = s;
+              }
+              T huA = __shfl_down_sync(full, tr2[0].x, dl), huB = __shfl_down_sync(full, tr2[0].y, dl);
+              T hgA = __shfl_down_sync(full, tr2[1].x, dl), hgB = __shfl_down_sync(full, tr2[1].y, dl);
+              T luA = __shfl_up_sync(full, tr2[2].x, dl), luB = __shfl_up_sync(full, tr2[2].y, dl);
+              T lgA = __shfl_up_sync(full, tr2[3].x, dl), lgB = __shfl_up_sync(full, tr2[3].y, dl);
+              if (lc == bd - 1) {
+                load2(hhi + 2 * pt, huA, hgA);
+                load2(hhi + 2 * (pt + 1), huB, hgB);
+              }
+              if (lc == 0) {
+                load2(hlo + 2 * pt, luA, lgA);
+                load2(hlo + 2 * (pt + 1), luB, lgB);
+              }
+              const float2 hu = pk(huA, huB), hg = pk(hgA, hgB), lu = pk(luA, luB), lg = pk(lgA, lgB);
+#pragma unroll
+              for (int q = 0; q < M; ++q) {
+                float2 s = __ffma2_rn(bc(tb.K[D][q * M]), v2[0],
+                                      pk(R[lidx<M, D>(q, t1, t2)], R[lidx<M, D>(q, t1 + 1, t2)]));
+#pragma unroll
+                for (int r = 1; r < M; ++r) s = __ffma2_rn(bc(tb.K[D][q * M + r]), v2[r], s);
+                if (!hi_bnd) s = __ffma2_rn(bc(tb.na[D][1][q]), hu, __ffma2_rn(bc(tb.nbv[D][1][q]), hg, s));
+                if (!lo_bnd) s = __ffma2_rn(bc(tb.na[D][0][q]), lu, __ffma2_rn(bc(tb.nbv[D][0][q]), lg, s));
+                R[lidx<M, D>(q, t1, t2)] = s.x;
+                R[lidx<M, D>(q, t1 + 1, t2)] = s.y;
+              }
+              continue;
+            }
+          }
           T v[M];
 #pragma unroll
           for (int r = 0; r < M; ++r) v[r] = u[lidx<M, D>(r, t1, t2)];
@@ -686,6 +754,35 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
 #pragma unroll
           for (int t1 = 0; t1 < M; ++t1) {
             const int pt = t1 + M * t2;
+            if constexpr (PK) {
+              // lines (t1, t2) and (t1 + 1, t2), neighbours in x, as one packed pair
+              if (t1 & 1) continue;
+              if (t1 + 1 < M) {
+                float2 v2[M];
+#pragma unroll
+                for (int r = 0; r < M; ++r) v2[r] = pk(u[lidx<M, D>(r, t1, t2)], u[lidx<M, D>(r, t1 + 1, t2)]);
+                float2 tr2[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  float2 s = __fmul2_rn(bc(tb.te[k][0]), v2[0]);
+#pragma unroll
+                  for (int r = 1; r < M; ++r) s = __ffma2_rn(bc(tb.te[k][r]), v2[r], s);
+                  tr2[k] = s;
+                }
+                store4(trz + tid * LY::NT + 4 * pt, tr2[0].x, tr2[1].x, tr2[2].x, tr2[3].x);
+                store4(trz + tid * LY::NT + 4 * (pt + 1), tr2[0].y, tr2[1].y, tr2[2].y, tr2[3].y);
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                  float2 s = __ffma2_rn(bc(tb.K[D][q * M]), v2[0],
+                                        pk(R[lidx<M, D>(q, t1, t2)], R[lidx<M, D>(q, t1 + 1, t2)]));
+#pragma unroll
+                  for (int r = 1; r < M; ++r) s = __ffma2_rn(bc(tb.K[D][q * M + r]), v2[r], s);
+                  R[lidx<M, D>(q, t1, t2)] = s.x;
+                  R[lidx<M, D>(q, t1 + 1, t2)] = s.y;
+                }
+                continue;
+              }
+            }
             T v[M];
 #pragma unroll
             for (int r = 0; r < M; ++r) v[r] = u[lidx<M, D>(r, t1, t2)];
@@ -750,6 +847,24 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
 #pragma unroll
             for (int t1 = 0; t1 < M; ++t1) {
               const int pt = t1 + M * t2;
+              if constexpr (PK) {
+                if (t1 & 1) continue;
+                if (t1 + 1 < M) {
+                  T unA, dnA, unB, dnB;
+                  load2(nsrc + 4 * pt, unA, dnA);
+                  load2(nsrc + 4 * (pt + 1), unB, dnB);
+                  const float2 un2 = pk(unA, unB), dn2 = pk(dnA, dnB);
+#pragma unroll
+                  for (int r = 0; r < M; ++r) {
+                    const float2 a2 = __ffma2_rn(bc(tb.na[D][s][r]), un2,
+                                                 __ffma2_rn(bc(tb.nbv[D][s][r]), dn2,
+                                                            pk(R[lidx<M, D>(r, t1, t2)], R[lidx<M, D>(r, t1 + 1, t2)])));
+                    R[lidx<M, D>(r, t1, t2)] = a2.x;
+                    R[lidx<M, D>(r, t1 + 1, t2)] = a2.y;
+                  }
+                  continue;
+                }
+              }
               T un, dn;
               load2(nsrc + 4 * pt, un, dn);
 #pragma unroll
@@ -767,27 +882,11 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     // for a coalesced store
     if (act) {
       T t2[P * M2];  // [j2][q1][q0]
-#pragma unroll
-      for (int j = 0; j < P; ++j)
-#pragma unroll
-        for (int qq = 0; qq < M2; ++qq) {
-          T s = tb.it[j] * R[qq];
-#pragma unroll
-          for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j], R[q * M2 + qq], s);
-          t2[j * M2 + qq] = s;
-        }
+      sweep<P, M, M, M, PK>(t2, M2, R, M2, tb.it, 1, P);
       T t1[P2 * M];  // [j2][j1][q0]
 #pragma unroll
       for (int j2 = 0; j2 < P; ++j2)
-#pragma unroll
-        for (int j1 = 0; j1 < P; ++j1)
-#pragma unroll
-          for (int q0 = 0; q0 < M; ++q0) {
-            T s = tb.it[j1] * t2[(j2 * M) * M + q0];
-#pragma unroll
-            for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j1], t2[(j2 * M + q) * M + q0], s);
-            t1[(j2 * P + j1) * M + q0] = s;
-          }
+        sweep<P, M, 1, M, PK>(t1 + j2 * P * M, M, t2 + j2 * M2, M, tb.it, 1, P);
 #pragma unroll
       for (int jj = 0; jj < P2; ++jj)
 #pragma unroll
