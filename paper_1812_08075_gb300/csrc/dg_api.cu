@@ -625,6 +625,20 @@ extern "C" {
 
 }  // extern "C"
 
+dg_status dg_apply_dot_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s,
+                                double *dot_partial, int dot_stride, int *nblocks) {
+  if (!op || op->precision != DG_FP32 || op->variant != DG_VARIANT_CELLWISE || !cellwise_ok(op) || op->aniso ||
+      op->problem != DG_SCALAR || !dot_partial || !nblocks)
+    return DG_ERR_UNSUPPORTED;
+  dg_operator *o = const_cast<dg_operator *>(op);
+  const cudaError_t e = launch_cellwise_apply<float>(op->p, scalar_args<float>(op, false), op->ht, (const float *)x,
+                                                     (float *)y, nrhs, op->ndofs, op->brick, s, nullptr,
+                                                     &o->fused_grid, nullptr, dot_partial, dot_stride);
+  if (e != cudaSuccess) return fail(DG_ERR_CUDA);
+  *nblocks = op->fused_grid;
+  return DG_OK;
+}
+
 dg_status dg_apply_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose) {
   return apply_impl(op, x, y, nrhs, s, transpose);
 }

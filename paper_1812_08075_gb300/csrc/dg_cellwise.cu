@@ -142,6 +142,27 @@ __device__ __forceinline__ void sweep(T *out, const int os, const T *in, const i
     }
 }
 
+// Two running sums of FP32 products in double-float (lanes x and y): each product's
+// rounding error is kept exactly (FMA), and the high parts add by TwoSum (Knuth), as in the
+// solver's dot products.
+struct DotPair {
+  float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+  static __device__ __forceinline__ float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float2 p = __fmul2_rn(a, b);
+    const float2 e = __ffma2_rn(a, b, neg(p));  // a b - p exactly
+    // TwoSum(hi, p): sm + t = hi + p exactly
+    const float2 sm = __fadd2_rn(hi, p);
+    const float2 bb = __fadd2_rn(sm, neg(hi));
+    const float2 t = __fadd2_rn(__fadd2_rn(hi, neg(__fadd2_rn(sm, neg(bb)))), __fadd2_rn(p, neg(bb)));
+    hi = sm;
+    lo = __fadd2_rn(lo, __fadd2_rn(t, e));
+  }
+  __device__ __forceinline__ double value() const {
+    return ((double)hi.x + (double)lo.x) + ((double)hi.y + (double)lo.y);
+  }
+};
+
 // Vector access to shared memory: four values (16-byte aligned) and pairs (8-byte
 // aligned for float, 16-byte for double).
 __device__ __forceinline__ void store4(float *p, float a, float b, float c, float d) {
@@ -324,10 +345,13 @@ constexpr int cellwise_min_blocks() {
   return 1;
 }
 
-template <int P, typename T, int BZ>
+// DOT (FP32): also the per-block partial sums of x . y per right-hand side, written to
+// dotp[rhs * dot_stride + block] (every right-hand side, 0 where the block had no item).
+template <int P, typename T, int BZ, bool DOT>
 __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     k_cellwise(const ScalarArgs<T> a, const CTab<P, T> tb, const T *__restrict__ x, T *__restrict__ y, int64_t sdof,
-               int nbx, int nby, int nbricks, int nitems, int nrhs, int bulk_ok) {
+               int nbx, int nby, int nbricks, int nitems, int nrhs, int bulk_ok, double *__restrict__ dotp,
+               int dot_stride) {
   constexpr int M = P, P2 = P * P, P3 = P2 * P, M2 = M * M, M3 = M2 * M;
   using LY = CLayout<P>;
   constexpr int sX = LY::sX;
@@ -345,10 +369,17 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
   // mbar[w]: x rows of warp w; mbar[nwarps]: the neighbours (one arrival per thread)
   __shared__ __align__(8) unsigned long long mbar[(32 * BZ) / 32 + 1];
   __shared__ unsigned blk_fault;  // a wait of this block gave up (read by all after a barrier)
+  // DOT: x . y of the block's cells per warp and right-hand side (written by the warp's lane 0)
+  __shared__ double dacc[DOT ? (32 * BZ) / 32 * 16 : 1];
+  static_assert(!DOT || std::is_same<T, float>::value, "the fused dot is an FP32 form");
   auto hoff = [](int d) { return d == 0 ? 0 : (d == 1 ? LY::NT * n0 : LY::NT * (n0 + n1)); };
   const int tid = threadIdx.x;
   const int lx = tid % bx, ly = (tid / bx) % by, lz = tid / (bx * by);
   const int warp = tid >> 5, lane = tid & 31;
+  if constexpr (DOT) {
+    if (lane == 0)
+      for (int r = 0; r < 16; ++r) dacc[warp * 16 + r] = 0.0;
+  }
   constexpr int nwarps = nb >> 5;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const T *const xend = x + nrhs * sdof;
@@ -878,6 +909,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     axis_xy(std::integral_constant<int, 0>{});
     axis_xy(std::integral_constant<int, 1>{});
     axis_z();
+    double cell_dot = 0.0;  // DOT: x . y of this thread's cell
     // transposed interpolation to the GLL coefficients, staged in this warp's own rows of xs
     // for a coalesced store
     if (act) {
@@ -887,6 +919,7 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
 #pragma unroll
       for (int j2 = 0; j2 < P; ++j2)
         sweep<P, M, 1, M, PK>(t1 + j2 * P * M, M, t2 + j2 * M2, M, tb.it, 1, P);
+      T yv[P3];
 #pragma unroll
       for (int jj = 0; jj < P2; ++jj)
 #pragma unroll
@@ -894,8 +927,25 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
           T s = tb.it[j] * t1[jj * M];
 #pragma unroll
           for (int q = 1; q < M; ++q) s = fma(tb.it[q * P + j], t1[jj * M + q], s);
-          xs[tid * sX + jj * P + j] = s;
+          yv[jj * P + j] = s;
         }
+      if constexpr (DOT) {
+        // this cell's x . y, x still in the staging slots that y is about to take
+        DotPair dp;
+#pragma unroll
+        for (int i = 0; i + 1 < P3; i += 2)
+          dp.add(pk(xs[tid * sX + i], xs[tid * sX + i + 1]), pk(yv[i], yv[i + 1]));
+        if constexpr (P3 & 1) dp.add(pk(xs[tid * sX + P3 - 1], 0.f), pk(yv[P3 - 1], 0.f));
+        cell_dot = dp.value();
+      }
+#pragma unroll
+      for (int i = 0; i < P3; ++i) xs[tid * sX + i] = yv[i];
+    }
+    if constexpr (DOT) {
+      // the warp's sum of its cells' x . y, added to its slot of this item's right-hand side
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cell_dot += __shfl_down_sync(0xffffffffu, cell_dot, o);
+      if (lane == 0) dacc[warp * 16 + rhs] += cell_dot;
     }
     // each warp stores the rows it staged itself: a warp barrier suffices, and the next
     // item's staging by the same warp reuses the same rows
@@ -938,15 +988,24 @@ __global__ void __launch_bounds__(32 * BZ, cellwise_min_blocks<P, T, BZ>())
     // staging rows, the halo traces, whose last readers all passed the axis-2 barrier, and
     // the neighbour staging, whose last readers passed the first barrier
   }
+  if constexpr (DOT) {
+    // the block's partial sums, over its warps in a fixed order
+    __syncthreads();
+    for (int r = tid; r < nrhs; r += nb) {
+      double v = 0.0;
+      for (int w = 0; w < nwarps; ++w) v += dacc[w * 16 + r];
+      dotp[(int64_t)r * dot_stride + blockIdx.x] = v;
+    }
+  }
 }
 
-template <int P, typename T, int BZ>
-cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof,
-                cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
+template <int P, typename T, int BZ, bool DOT>
+cudaError_t run_k(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof,
+                  cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q, double *dotp, int dot_stride) {
   constexpr int bx = 8, by = 4, bz = BZ, nb = bx * by * bz;
   const CTab<P, T> tb = make_tab<P, T>(a, ht);
   const size_t sm = cellwise_words<P>(bx, by, bz, cellwise_stage<P, T>()) * sizeof(T);
-  auto k = k_cellwise<P, T, BZ>;
+  auto k = k_cellwise<P, T, BZ, DOT>;
   cudaError_t e;
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
     return e;
@@ -960,6 +1019,7 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
   if (nitems > INT_MAX) return cudaErrorInvalidValue;  // work items are decoded in 32 bits
   int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
   if (grid > nitems) grid = nitems;
+  if (DOT && grid > dot_stride) return cudaErrorInvalidValue;  // one partial per block and rhs
   if (grid_out) *grid_out = (int)grid;
   if (q) {
     q->blocks = grid;
@@ -972,13 +1032,25 @@ cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, 
   // bulk staging needs every brick row and neighbour span on a 16-byte boundary
   const int bulk_ok = cellwise_stage<P, T>() && (reinterpret_cast<uintptr_t>(x) & 15) == 0 && sdof % 4 == 0 &&
                       a.nx % 4 == 0;
-  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, (int)nbx, (int)nby, (int)nbricks, (int)nitems, nrhs, bulk_ok);
+  k<<<(unsigned)grid, nb, sm, s>>>(a, tb, x, y, sdof, (int)nbx, (int)nby, (int)nbricks, (int)nitems, nrhs, bulk_ok,
+                                   dotp, dot_stride);
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
     cudaEventRecord(ev[3], s);
   }
   return cudaGetLastError();
+}
+
+template <int P, typename T, int BZ>
+cudaError_t run(const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs, int64_t sdof,
+                cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q, double *dotp, int dot_stride) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (dotp) return run_k<P, T, BZ, true>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
+  } else {
+    if (dotp) return cudaErrorInvalidValue;  // the fused dot is an FP32 form
+  }
+  return run_k<P, T, BZ, false>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, nullptr, 0);
 }
 
 }  // namespace dgc
@@ -998,11 +1070,12 @@ size_t cellwise_smem_bytes(int p, int cells, int es) {
 
 template <int P, typename T>
 static cudaError_t run_bz(int bz, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
-                          int64_t sdof, cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q) {
+                          int64_t sdof, cudaStream_t s, const cudaEvent_t *ev, int *grid_out, LaunchInfo *q,
+                          double *dotp, int dot_stride) {
   switch (bz) {
-    case 2: return dgc::run<P, T, 2>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
-    case 4: return dgc::run<P, T, 4>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
-    case 8: return dgc::run<P, T, 8>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
+    case 2: return dgc::run<P, T, 2>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
+    case 4: return dgc::run<P, T, 4>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
+    case 8: return dgc::run<P, T, 8>(a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1010,22 +1083,22 @@ static cudaError_t run_bz(int bz, const ScalarArgs<T> &a, const HostTables &ht, 
 template <typename T>
 cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
                                   int64_t sdof, int cells, cudaStream_t s, const cudaEvent_t *ev, int *grid_out,
-                                  LaunchInfo *q) {
+                                  LaunchInfo *q, double *dotp, int dot_stride) {
   if (ht.m != p || ht.p != p) return cudaErrorInvalidValue;
   const int bz = cellwise_bz(cells);
   switch (p) {
-    case 2: return run_bz<2, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
-    case 3: return run_bz<3, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q);
+    case 2: return run_bz<2, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
+    case 3: return run_bz<3, T>(bz, a, ht, x, y, nrhs, sdof, s, ev, grid_out, q, dotp, dot_stride);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_cellwise_apply<float>(int, const ScalarArgs<float> &, const HostTables &, const float *,
                                                   float *, int, int64_t, int, cudaStream_t, const cudaEvent_t *, int *,
-                                                  LaunchInfo *);
+                                                  LaunchInfo *, double *, int);
 template cudaError_t launch_cellwise_apply<double>(int, const ScalarArgs<double> &, const HostTables &,
                                                    const double *, double *, int, int64_t, int, cudaStream_t,
-                                                   const cudaEvent_t *, int *, LaunchInfo *);
+                                                   const cudaEvent_t *, int *, LaunchInfo *, double *, int);
 
 extern "C" dg_status dg_device_faults(int clear, unsigned *faults) {
   if (!faults) return dg_record_error(DG_ERR_INVALID_ARG);

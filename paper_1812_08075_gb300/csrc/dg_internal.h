@@ -165,11 +165,14 @@ cudaError_t launch_fused_apply(int p, const ScalarArgs<T> &a, const HostTables &
                                LaunchInfo *query = nullptr);
 
 // One-thread-per-cell persistent apply for affine meshes, degree k <= 2 (dg_cellwise.cu):
-// bricks of 8 x 4 x (cells / 32) cells per block, cells = 64, 128 or 256.
+// bricks of 8 x 4 x (cells / 32) cells per block, cells = 64, 128 or 256. dotp (FP32
+// only): also the per-block partial sums of x . y per right-hand side, written to
+// dotp[rhs * dot_stride + block] for block < *grid_out (dot_stride >= the grid).
 template <typename T>
 cudaError_t launch_cellwise_apply(int p, const ScalarArgs<T> &a, const HostTables &ht, const T *x, T *y, int nrhs,
                                   int64_t stride_dofs, int cells, cudaStream_t s, const cudaEvent_t *ev,
-                                  int *grid_out, LaunchInfo *query = nullptr);
+                                  int *grid_out, LaunchInfo *query = nullptr, double *dotp = nullptr,
+                                  int dot_stride = 0);
 size_t cellwise_smem_bytes(int p, int cells, int es);  // 0 if (p, cells) is not supported
 
 // out[i] = in[i] as double-float (dg_scalar_df64.cu)
@@ -315,4 +318,10 @@ int dg_device_sms();
 // Shared by the API and the solver (dg_api.cu).
 dg_status dg_record_error(dg_status s);
 dg_status dg_apply_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s, bool transpose);
+// y = A x with the per-block partial sums of x . y per right-hand side in
+// dot_partial[rhs * dot_stride + block], block < *nblocks, where the operator's kernel
+// computes them in the same pass (the FP32 cellwise variant). Otherwise launches nothing
+// and returns DG_ERR_UNSUPPORTED without recording an error.
+dg_status dg_apply_dot_internal(const dg_operator *op, const void *x, void *y, int nrhs, cudaStream_t s,
+                                double *dot_partial, int dot_stride, int *nblocks);
 void dg_solver_release(dg_operator *op);

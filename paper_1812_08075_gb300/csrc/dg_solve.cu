@@ -477,10 +477,21 @@ dg_status enqueue_iterations(const dg_operator *op, T *x, T *r, T *p, T *Ap, con
   const dim3 g(grid_vec(V4 ? n / 4 : n, nrhs), nrhs);
   Scalars *S = &W->S;
   for (int it = 0; it < iters; ++it) {
-    dg_status st = dg_apply_internal(op, p, Ap, nrhs, s, false);
-    if (st != DG_OK) return st;
-    k_dot<T, V4><<<g, kThreads, 0, s>>>(p, Ap, W->partial, n);
-    k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
+    // Ap and p . Ap: in one pass where the operator's kernel forms the dot (FP32 cellwise,
+    // two vector passes fewer), else the apply and a dot kernel
+    int nbd = 0;
+    dg_status st = sizeof(T) == 4 ? dg_apply_dot_internal(op, p, Ap, nrhs, s, W->partial, kMaxBlocks, &nbd)
+                                  : DG_ERR_UNSUPPORTED;
+    if (st == DG_OK) {
+      k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, nbd);
+    } else if (st == DG_ERR_UNSUPPORTED) {
+      st = dg_apply_internal(op, p, Ap, nrhs, s, false);
+      if (st != DG_OK) return st;
+      k_dot<T, V4><<<g, kThreads, 0, s>>>(p, Ap, W->partial, n);
+      k_reduce<<<nrhs, kThreads, 0, s>>>(W->partial, S->pAp, g.x);
+    } else {
+      return st;
+    }
     k_alpha<<<1, 32, 0, s>>>(S, nrhs);
     if constexpr (sizeof(T) == 4) {
       if (z && block_jacobi_fusable(op)) {

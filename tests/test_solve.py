@@ -205,3 +205,40 @@ def test_mixed_cg_reliable_updates_argument_errors():
     with pytest.raises(dg.DGError):  # operators swapped
         dg.dg_mixed_cg_solve(op32.handle, op64.handle, b.data_ptr(), x.data_ptr(), 1, 0.1,
                              dg.dg_cg_options(1e-8, 100, 10, 1, 0), None)
+
+
+def test_fp32_cg_step_with_the_dot_formed_in_the_cellwise_apply():
+    # The FP32 cellwise apply forms p . Ap in the same pass as Ap inside CG. One CG step
+    # from x0 = 0 (no preconditioner) gives x1 = alpha b with alpha = (b . b) / (b . A b):
+    # alpha read back from x1 must equal the FP64 value from the FP32 apply's output. The
+    # mesh gives 432 (right-hand side, brick) items for about 300 blocks, so blocks sum
+    # items of several right-hand sides.
+    n, k, nrhs = (48, 24, 24), 2, 4
+    op = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    op.set_variant(dg.DG_VARIANT_CELLWISE, 256)
+    b = torch.from_numpy(rhs(n, k, nrhs)).float().cuda()
+    y = op.apply(b).double()
+    bb = b.double()
+    alpha_ref = (bb * bb).sum(1) / (bb * y).sum(1)
+    x = torch.zeros_like(b)
+    ok, info = dg.dg_cg_solve(op.handle, b.data_ptr(), x.data_ptr(), nrhs, opts(1e-30, max_iters=1, chunk=1, graph=0),
+                              None)
+    assert not ok and all(i["iters"] == 1 for i in info)
+    big = bb.abs() > 0.5 * bb.abs().amax(1, keepdim=True)  # entries where x / b is well conditioned
+    for r in range(nrhs):
+        alpha = (x[r].double()[big[r]] / bb[r][big[r]]).mean()
+        assert abs(float(alpha / alpha_ref[r]) - 1.0) <= 2e-7, (r, float(alpha), float(alpha_ref[r]))
+    # the same solve to 1e-3 (within FP32 CG's reach on this mesh) with the fused variant
+    # (apply and dot in separate passes):
+    # both converge in about the same number of iterations (the two FP32 applies round
+    # differently, so the counts need not be equal)
+    op_f = dg.Operator(dg.Mesh(*n), k, precision=dg.DG_FP32, max_rhs=nrhs)
+    op_f.set_variant(dg.DG_VARIANT_FUSED)
+    its = []
+    for o in (op, op_f):
+        xo = torch.zeros_like(b)
+        ok, info = dg.dg_cg_solve(o.handle, b.data_ptr(), xo.data_ptr(), nrhs, opts(1e-3), None)
+        assert ok, info
+        its.append(max(i["iters"] for i in info))
+    print(f"FP32 CG to 1e-3: cellwise with the fused dot {its[0]} iterations, fused variant {its[1]}")
+    assert abs(its[0] - its[1]) <= 5 + its[1] // 10, its
