@@ -318,17 +318,22 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
     const bool inner = F.cm >= 0 && F.cp >= 0;
     const int side1 = F.cm >= 0 ? 1 : 0;  // xi_a of the first side (T-, or the boundary cell)
     // geometry of both sides: b (reference components) and pw
+    // (arrays below are indexed with compile-time indices only, the run-time axes go
+    // through selects, so that they stay in registers)
     T bm[3] = {T(0), T(0), T(0)}, bp[3] = {T(0), T(0), T(0)}, pw;
     if (GEO == GEO_AFFINE) {
       const T bW = W * a.face_b[ax];
-      bm[ax] = inner ? bW : (side1 ? bW : -bW);
-      bp[ax] = bW;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        bm[k] = k == ax ? (inner ? bW : (side1 ? bW : -bW)) : T(0);
+        bp[k] = k == ax ? bW : T(0);
+      }
       pw = W * a.face_pw[ax];
     } else {
       T xi[3], J[3][3], A[3][3], n[3];
-      xi[t1] = tb.s[qs];
-      xi[t2] = tb.s[qt];
-      xi[ax] = side1 ? T(1) : T(0);
+      const T xin = side1 ? T(1) : T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) xi[k] = k == ax ? xin : (k == t1 ? tb.s[qs] : tb.s[qt]);
       dgg::jacobian_from_coeffs(CF + lfc * 72, xi[0], xi[1], xi[2], J);
       dgg::area_vector(J, ax, inner ? 1 : (side1 ? 1 : -1), n);
       T det = dgg::adjugate(J, A);
@@ -336,30 +341,36 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
       for (int k = 0; k < 3; ++k) bm[k] = W * fma(A[k][0], n[0], fma(A[k][1], n[1], A[k][2] * n[2])) / det;
       pw = io_in<T>(a.gamma_face[f]) * W * sqrt(fma(n[0], n[0], fma(n[1], n[1], n[2] * n[2])));
       if (inner) {
-        xi[ax] = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (k == ax) xi[k] = T(0);
         dgg::jacobian_from_coeffs(CF + lfc * 72 + 36, xi[0], xi[1], xi[2], J);
         det = dgg::adjugate(J, A);
 #pragma unroll
         for (int k = 0; k < 3; ++k) bp[k] = W * fma(A[k][0], n[0], fma(A[k][1], n[1], A[k][2] * n[2])) / det;
       }
     }
+    const T bmn = dg_pick3(bm[0], bm[1], bm[2], ax), bm1 = dg_pick3(bm[0], bm[1], bm[2], t1);
+    const T bm2 = dg_pick3(bm[0], bm[1], bm[2], t2);
+    const T bpn = dg_pick3(bp[0], bp[1], bp[2], ax), bp1 = dg_pick3(bp[0], bp[1], bp[2], t1);
+    const T bp2 = dg_pick3(bp[0], bp[1], bp[2], t2);
     const T *S = SU + lfc * 8 * M2;
-    // b . grad_ref of r and x on each side
-    auto bgrad = [&](const T *u, const T *b) -> T {
-      T g = b[ax] * u[M2 + qf];
+    // b . grad_ref of r and x on each side (b given by its normal and tangential components)
+    auto bgrad = [&](const T *u, const T &bn, const T &b1, const T &b2) -> T {
+      T g = bn * u[M2 + qf];
       if (GEO != GEO_AFFINE) {
         T d1, d2;
         tangential<M, T>(u, tb.dcol, qs, qt, d1, d2);
-        g = fma(b[t1], d1, fma(b[t2], d2, g));
+        g = fma(b1, d1, fma(b2, d2, g));
       }
       return g;
     };
-    const T grm = bgrad(S, bm);
-    const T gxm = DK ? bgrad(S + 4 * M2, bm) : T(0);
+    const T grm = bgrad(S, bmn, bm1, bm2);
+    const T gxm = DK ? bgrad(S + 4 * M2, bmn, bm1, bm2) : T(0);
     T *R = SR + lfc * 5 * M2;
     if (inner) {
-      const T grp = bgrad(S + 2 * M2, bp);
-      const T gxp = DK ? bgrad(S + 6 * M2, bp) : T(0);
+      const T grp = bgrad(S + 2 * M2, bpn, bp1, bp2);
+      const T gxp = DK ? bgrad(S + 6 * M2, bpn, bp1, bp2) : T(0);
       T km = T(1), kp = T(1);
       if (KAPPA) {
         km = io_in<T>(a.kappa_face[(F.cm * 6 + 2 * ax + 1) * M2 + qf]);
@@ -370,17 +381,17 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
       const T Rv = fma(sc, flux, pw * Jr);
       const T sJ = ss * half * Jr;
       const T sm = KAPPA ? sJ * km : sJ, sp = KAPPA ? sJ * kp : sJ;
-      fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = sm * bm[ax];
-      fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = sp * bp[ax];
+      fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = sm * bmn;
+      fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = sp * bpn;
       if (GEO == GEO_AFFINE) {
         fres[tr_idx<M>(F.cm, 2 * ax + 1, 0, qf)] = Rv;
         fres[tr_idx<M>(F.cp, 2 * ax, 0, qf)] = -Rv;
       } else {
         R[qf] = Rv;
-        R[M2 + qf] = sm * bm[t1];
-        R[2 * M2 + qf] = sm * bm[t2];
-        R[3 * M2 + qf] = sp * bp[t1];
-        R[4 * M2 + qf] = sp * bp[t2];
+        R[M2 + qf] = sm * bm1;
+        R[2 * M2 + qf] = sm * bm2;
+        R[3 * M2 + qf] = sp * bp1;
+        R[4 * M2 + qf] = sp * bp2;
       }
       if (DK) {
         const T Jx = S[4 * M2 + qf] - S[6 * M2 + qf];
@@ -396,9 +407,9 @@ __global__ void __launch_bounds__(256) k_face_adj(const ScalarArgs<T> a, const d
         const T u = S[qf];
         Rv = fma(sc * kb, grm, pw * u);
         const T su = ss * kb * u;
-        s1 = su * bm[t1];
-        s2 = su * bm[t2];
-        sn = su * bm[ax];
+        s1 = su * bm1;
+        s2 = su * bm2;
+        sn = su * bmn;
         if (DK) dk = fma(-gxm, u, thetaT * S[4 * M2 + qf] * grm);
       }
       fres[tr_idx<M>(cb, lf, 1, qf)] = sn;

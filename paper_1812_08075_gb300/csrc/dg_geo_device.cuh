@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 
+#include "dg_internal.h"
+
 namespace dgg {
 
 __device__ __forceinline__ void cell_corners(const double *verts, int nx, int ny, int64_t cell, double V[8][3]) {
@@ -60,8 +62,10 @@ __device__ __forceinline__ T adjugate(const T J[3][3], T A[3][3]) {
 template <typename T>
 __device__ __forceinline__ void area_vector(const T J[3][3], int a, int dir, T n[3]) {
   const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-  const T u0 = J[0][t1], u1 = J[1][t1], u2 = J[2][t1];
-  const T v0 = J[0][t2], v1 = J[1][t2], v2 = J[2][t2];
+  const T u0 = dg_pick3(J[0][0], J[0][1], J[0][2], t1), u1 = dg_pick3(J[1][0], J[1][1], J[1][2], t1);
+  const T u2 = dg_pick3(J[2][0], J[2][1], J[2][2], t1);
+  const T v0 = dg_pick3(J[0][0], J[0][1], J[0][2], t2), v1 = dg_pick3(J[1][0], J[1][1], J[1][2], t2);
+  const T v2 = dg_pick3(J[2][0], J[2][1], J[2][2], t2);
   // (a, t1, t2) is an even permutation of (0,1,2) for a = 0, 2 and odd for a = 1; dir = +-1
   const T sg = ((a == 1) != (dir < 0)) ? T(-1) : T(1);
   n[0] = sg * (u1 * v2 - u2 * v1);

@@ -33,6 +33,13 @@ __device__ __forceinline__ void dg_prefetch_l2(const void *lo, const void *hi, c
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
 }
 
+// v_i for a run-time i in {0, 1, 2}, by selects: indexing a local array with a run-time
+// axis instead would place the array in local memory.
+template <typename T>
+__device__ __forceinline__ T dg_pick3(const T &v0, const T &v1, const T &v2, int i) {
+  return i == 0 ? v0 : (i == 1 ? v1 : v2);
+}
+
 // Asynchronous copy of one 4-, 8- or 16-byte element global -> shared (cp.async): the
 // thread issues it without waiting, and dg_cp_async_wait_all() waits for all of its own.
 template <typename T>

@@ -366,9 +366,12 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
       d2.add(tb.dcol[qt * M + r], u0[qs + r * M]);
     }
     const T ds1 = d1.get(), ds2 = d2.get();
-    const T bm[3] = {gf[0], gf[M2], gf[2 * M2]};
+    // the face's geometry vector in the normal and the two tangential directions, picked by
+    // selects (indexing a local array with the run-time axes would put it in local memory)
+    const T g0 = gf[0], g1 = gf[M2], g2 = gf[2 * M2];
+    const T bmn = dg_pick3(g0, g1, g2, ax), bm1 = dg_pick3(g0, g1, g2, t1), bm2 = dg_pick3(g0, g1, g2, t2);
     Acc<T> gacc;
-    gacc.init(bm[t2], ds2); gacc.add(bm[t1], ds1); gacc.add(bm[ax], u0[M2 + qf]);
+    gacc.init(bm2, ds2); gacc.add(bm1, ds1); gacc.add(bmn, u0[M2 + qf]);
     const T gm = gacc.get();
     const T pw = gf[6 * M2];
     if (F.cm >= 0 && F.cp >= 0) {
@@ -382,9 +385,10 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
         e2.add(tb.dcol[qt * M + r], u1[qs + r * M]);
       }
       const T es1 = e1.get(), es2 = e2.get();
-      const T bp[3] = {gf[3 * M2], gf[4 * M2], gf[5 * M2]};
+      const T h0 = gf[3 * M2], h1 = gf[4 * M2], h2 = gf[5 * M2];
+      const T bpn = dg_pick3(h0, h1, h2, ax), bp1 = dg_pick3(h0, h1, h2, t1), bp2 = dg_pick3(h0, h1, h2, t2);
       Acc<T> pacc;
-      pacc.init(bp[t2], es2); pacc.add(bp[t1], es1); pacc.add(bp[ax], u1[M2 + qf]);
+      pacc.init(bp2, es2); pacc.add(bp1, es1); pacc.add(bpn, u1[M2 + qf]);
       const T gp = pacc.get();
       T km = T(1), kp = T(1);
       if (KAPPA) {
@@ -397,12 +401,12 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
       const T sJ = ss * half * J;
       const T sm = KAPPA ? sJ * km : sJ, sp = KAPPA ? sJ * kp : sJ;
       R[qf] = Rv;
-      R[M2 + qf] = sm * bm[t1];
-      R[2 * M2 + qf] = sm * bm[t2];
-      R[3 * M2 + qf] = sp * bp[t1];
-      R[4 * M2 + qf] = sp * bp[t2];
-      fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = sm * bm[ax];
-      fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = sp * bp[ax];
+      R[M2 + qf] = sm * bm1;
+      R[2 * M2 + qf] = sm * bm2;
+      R[3 * M2 + qf] = sp * bp1;
+      R[4 * M2 + qf] = sp * bp2;
+      fres[tr_idx<M>(F.cm, 2 * ax + 1, 1, qf)] = sm * bmn;
+      fres[tr_idx<M>(F.cp, 2 * ax, 1, qf)] = sp * bpn;
     } else {
       const int side = F.cm >= 0 ? 1 : 0;
       const int64_t cb = side ? F.cm : F.cp;
@@ -413,9 +417,9 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
         const T u = u0[qf];
         Rv = fma(sc * kb, gm, pw * u);
         const T su = ss * kb * u;
-        s1 = su * bm[t1];
-        s2 = su * bm[t2];
-        sn = su * bm[ax];
+        s1 = su * bm1;
+        s2 = su * bm2;
+        sn = su * bmn;
       }
       R[qf] = Rv;
       R[M2 + qf] = s1;
