@@ -49,6 +49,11 @@ __device__ __forceinline__ void dg_cp_async(T *dst, const T *src) {
                "n"((int)sizeof(T))
                : "memory");
 }
+// 16 bytes at once (both addresses 16-byte aligned), bypassing L1
+__device__ __forceinline__ void dg_cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
 __device__ __forceinline__ void dg_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 #endif
 

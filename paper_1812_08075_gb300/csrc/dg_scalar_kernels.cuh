@@ -325,26 +325,54 @@ __global__ void __launch_bounds__(256) k_face(const ScalarArgs<T> a, const T *__
   T *sU = SM;                   // [face][4][M2]: u-, dn-, u+, dn+
   T *sR = SM + 4 * fpb * M2;    // [face][5][M2]: Rv, Rt1-, Rt2-, Rt1+, Rt2+
   T *sG = SM + 9 * fpb * M2;    // [face][7][M2]: the faces' stored geometry (ASYNC)
-  for (int i = tid; i < nf * 4 * M2; i += nt) {
-    const int lfc = i / (4 * M2), r = i - lfc * (4 * M2);
-    const int slot = r / M2, qf = r - slot * M2;
-    const FaceId &F = sF[lfc];
-    const int ax = F.axis;
-    const T *src = nullptr;
-    if (slot < 2) {
-      if (F.cm >= 0) src = traces + tr_idx<M>(F.cm, 2 * ax + 1, slot, qf);
-      else src = traces + tr_idx<M>(F.cp, 2 * ax, slot, qf);  // boundary face at the lower end
-    } else if (F.cm >= 0 && F.cp >= 0) {
-      src = traces + tr_idx<M>(F.cp, 2 * ax, slot - 2, qf);
-    }
-    if (ASYNC && src) dg_cp_async(sU + i, src);
-    else sU[i] = src ? *src : T(0);
-  }
   if constexpr (ASYNC) {
+    // a face's trace row (M^2 values) and the block's geometry in 16-byte pieces where their
+    // sizes allow (every start is then 16-byte aligned), else one value at a time
+    constexpr int V = (M2 * sizeof(T)) % 16 == 0 ? int(16 / sizeof(T)) : 1;
+    for (int i = tid; i < nf * 4 * (M2 / V); i += nt) {
+      const int lfc = i / (4 * (M2 / V)), r = i - lfc * (4 * (M2 / V));
+      const int slot = r / (M2 / V), qf = (r - slot * (M2 / V)) * V;
+      const FaceId &F = sF[lfc];
+      const int ax = F.axis;
+      const T *src = nullptr;
+      if (slot < 2) {
+        if (F.cm >= 0) src = traces + tr_idx<M>(F.cm, 2 * ax + 1, slot, qf);
+        else src = traces + tr_idx<M>(F.cp, 2 * ax, slot, qf);  // boundary face at the lower end
+      } else if (F.cm >= 0 && F.cp >= 0) {
+        src = traces + tr_idx<M>(F.cp, 2 * ax, slot - 2, qf);
+      }
+      T *dst = sU + lfc * (4 * M2) + slot * M2 + qf;
+      if constexpr (V > 1) {
+        if (src) dg_cp_async16(dst, src);
+        else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        if (src) dg_cp_async(dst, src);
+        else *dst = T(0);
+      }
+    }
     // the block's faces are consecutive: their geometry is one contiguous range
     const T *g0 = a.gface + f0 * (7 * M2);
-    for (int i = tid; i < nf * 7 * M2; i += nt) dg_cp_async(sG + i, g0 + i);
+    if constexpr (V > 1) {
+      for (int i = tid; i < nf * 7 * (M2 / V); i += nt) dg_cp_async16(sG + i * V, g0 + i * V);
+    } else {
+      for (int i = tid; i < nf * 7 * M2; i += nt) dg_cp_async(sG + i, g0 + i);
+    }
     dg_cp_async_wait_all();
+  } else {
+    for (int i = tid; i < nf * 4 * M2; i += nt) {
+      const int lfc = i / (4 * M2), r = i - lfc * (4 * M2);
+      const int slot = r / M2, qf = r - slot * M2;
+      const FaceId &F = sF[lfc];
+      const int ax = F.axis;
+      T v = T(0);
+      if (slot < 2) {
+        if (F.cm >= 0) v = traces[tr_idx<M>(F.cm, 2 * ax + 1, slot, qf)];
+        else v = traces[tr_idx<M>(F.cp, 2 * ax, slot, qf)];  // boundary face at the lower end
+      } else if (F.cm >= 0 && F.cp >= 0) {
+        v = traces[tr_idx<M>(F.cp, 2 * ax, slot - 2, qf)];
+      }
+      sU[i] = v;
+    }
   }
   __syncthreads();
   for (int i = tid; i < nf * M2; i += nt) {
