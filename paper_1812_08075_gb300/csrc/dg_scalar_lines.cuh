@@ -49,6 +49,19 @@ __device__ __forceinline__ void line_contract(const T (&mat)[NI * NO], const TI 
   }
 }
 
+// n contiguous values of T global -> shared, all of a thread's copies in flight at once
+// (cp.async; 16-byte pieces when both ends and the size allow), then one wait and the
+// block barrier.
+template <typename T>
+__device__ __forceinline__ void stage_async(T *dst, const T *src, int n, int tid, int nt) {
+  constexpr int V = int(16 / sizeof(T));
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && n % V == 0) {
+    for (int i = tid; i < n / V; i += nt) dg_cp_async16(dst + i * V, src + i * V);
+  } else {
+    for (int i = tid; i < n; i += nt) dg_cp_async(dst + i, src + i);
+  }
+}
+
 // base and stride of the line along axis d through the face point qf = s + M t (s, t the
 // other two axes in increasing order), in a [M][M][M] block with axis 0 fastest
 template <int M>
@@ -75,7 +88,12 @@ __global__ void __launch_bounds__(256) k_cell_lines(const ScalarArgs<T> a, const
   const int nc = (int)min((int64_t)cpb, a.ncell - c0);
   {
     const io_t<T> *xb = x + c0 * P3;
-    for (int i = tid; i < nc * P3; i += nt) S0[i] = io_in<T>(xb[i]);
+    if constexpr (std::is_same<io_t<T>, T>::value) {
+      stage_async<T>(S0, xb, nc * P3, tid, nt);
+      dg_cp_async_wait_all();
+    } else {
+      for (int i = tid; i < nc * P3; i += nt) S0[i] = io_in<T>(xb[i]);
+    }
   }
   __syncthreads();
   // interpolation: [c][j2][j1][j0] -> [c][j2][j1][q0] -> [c][j2][q1][q0] -> U [c][q2][q1][q0]
@@ -203,8 +221,9 @@ __global__ void __launch_bounds__(256) k_back_lines(const ScalarArgs<T> a, const
   fres += blockIdx.y * st;
   const int64_t c0 = (int64_t)blockIdx.x * cpb;
   const int nc = (int)min((int64_t)cpb, a.ncell - c0);
-  for (int i = tid; i < nc * M3; i += nt) S0[i] = rvol[c0 * M3 + i];
-  for (int i = tid; i < nc * 12 * M2; i += nt) SF[i] = fres[c0 * 12 * M2 + i];
+  stage_async<T>(S0, rvol + c0 * M3, nc * M3, tid, nt);
+  stage_async<T>(SF, fres + c0 * 12 * M2, nc * 12 * M2, tid, nt);
+  dg_cp_async_wait_all();
   __syncthreads();
   // face residuals lifted along the normal axis of each face pair, one axis at a time
   for (int d = 0; d < 3; ++d) {
