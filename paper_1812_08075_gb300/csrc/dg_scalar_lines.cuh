@@ -49,19 +49,6 @@ __device__ __forceinline__ void line_contract(const T (&mat)[NI * NO], const TI 
   }
 }
 
-// n contiguous values of T global -> shared, all of a thread's copies in flight at once
-// (cp.async; 16-byte pieces when both ends and the size allow), then one wait and the
-// block barrier.
-template <typename T>
-__device__ __forceinline__ void stage_async(T *dst, const T *src, int n, int tid, int nt) {
-  constexpr int V = int(16 / sizeof(T));
-  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && n % V == 0) {
-    for (int i = tid; i < n / V; i += nt) dg_cp_async16(dst + i * V, src + i * V);
-  } else {
-    for (int i = tid; i < n; i += nt) dg_cp_async(dst + i, src + i);
-  }
-}
-
 // base and stride of the line along axis d through the face point qf = s + M t (s, t the
 // other two axes in increasing order), in a [M][M][M] block with axis 0 fastest
 template <int M>
