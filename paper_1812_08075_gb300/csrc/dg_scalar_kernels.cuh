@@ -48,9 +48,9 @@ __device__ __forceinline__ void load_tables(SmemTables<P, M, T> &s, const DevTab
 template <typename T>
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
-// n contiguous values of T global -> shared, all of a thread's copies in flight at once
-// (cp.async; 16-byte pieces when both ends and the size allow), then one wait and the
-// block barrier.
+// Issues the copy of n contiguous values of T global -> shared with all of a thread's
+// copies in flight at once (cp.async; 16-byte pieces when both ends and the size allow).
+// The caller then waits (dg_cp_async_wait_all) and synchronises the block.
 template <typename T>
 __device__ __forceinline__ void stage_async(T *dst, const T *src, int n, int tid, int nt) {
   constexpr int V = int(16 / sizeof(T));
