@@ -32,6 +32,14 @@ LineTab<P, M, T> line_tables(const HostTables &h) {
   return t;
 }
 
+// The loops over the three axes are unrolled (compile-time line strides and bases: less
+// index arithmetic) for FP32 up to M = 4; for double-float and larger M the unrolled code
+// measured slower (instruction cache), so they stay loops.
+template <int M, typename T>
+__host__ __device__ constexpr int axis_unroll() {
+  return (std::is_same<T, float>::value && M <= 4) ? 3 : 1;
+}
+
 // out[o * os] = sum_n mat[o][n] in[n * is] for o < NO (mat row-major NO x NI, or its
 // transpose when TR), one line
 template <int NI, int NO, bool TR, typename T, typename TI, typename TO>
@@ -64,6 +72,7 @@ __global__ void __launch_bounds__(256) k_cell_lines(const ScalarArgs<T> a, const
                                                     T *__restrict__ traces, int cpb, int64_t sx, int64_t sr,
                                                     int64_t st) {
   constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  constexpr int kAxisUnroll = axis_unroll<M, T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S0 = reinterpret_cast<T *>(smem_raw);
   T *S1 = S0 + cpb * M3, *S2 = S1 + cpb * M3, *S3 = S2 + cpb * M3;
@@ -101,8 +110,7 @@ __global__ void __launch_bounds__(256) k_cell_lines(const ScalarArgs<T> a, const
   // reference derivative d/dxi_d at every point of the line, into G_d (S0, S1, S3)
   {
     T *tr = traces + c0 * (12 * M2);
-    for (int l = tid; l < nc * 3 * M2; l += nt) {
-      const int c = l / (3 * M2), r = l - c * (3 * M2), d = r / M2, qf = r - d * M2;
+    auto trace_line = [&](int c, int d, int qf) {
       int base, stride;
       line_of<M>(d, qf, base, stride);
       const T *u = U + c * M3 + base;
@@ -128,6 +136,17 @@ __global__ void __launch_bounds__(256) k_cell_lines(const ScalarArgs<T> a, const
 #pragma unroll
         for (int j = 1; j < M; ++j) acc.add(tb.dcol[q * M + j], v[j]);
         g[q * stride] = acc.get();
+      }
+    };
+    if constexpr (kAxisUnroll == 3) {
+      // one pass per axis, unrolled: each pass's line stride and base are compile-time
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        for (int l = tid; l < nc * M2; l += nt) trace_line(l / M2, d, l % M2);
+    } else {
+      for (int l = tid; l < nc * 3 * M2; l += nt) {
+        const int c = l / (3 * M2), r = l - c * (3 * M2), d = r / M2;
+        trace_line(c, d, r - d * M2);
       }
     }
   }
@@ -168,6 +187,7 @@ __global__ void __launch_bounds__(256) k_cell_lines(const ScalarArgs<T> a, const
   }
   __syncthreads();
   // R += D_d^T f_d, one axis at a time; the last axis writes R_vol
+#pragma unroll kAxisUnroll
   for (int d = 0; d < 3; ++d) {
     const T *F = d == 0 ? S0 : (d == 1 ? S1 : S3);
     for (int l = tid; l < nc * M2; l += nt) {
@@ -199,6 +219,7 @@ __global__ void __launch_bounds__(256) k_back_lines(const ScalarArgs<T> a, const
                                                     io_t<T> *__restrict__ y, int cpb, int64_t sy, int64_t sr,
                                                     int64_t st) {
   constexpr int P3 = P * P * P, M2 = M * M, M3 = M * M * M;
+  constexpr int kAxisUnroll = axis_unroll<M, T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S0 = reinterpret_cast<T *>(smem_raw);
   T *S1 = S0 + cpb * M3, *SF = S1 + cpb * M3;
@@ -213,6 +234,7 @@ __global__ void __launch_bounds__(256) k_back_lines(const ScalarArgs<T> a, const
   dg_cp_async_wait_all();
   __syncthreads();
   // face residuals lifted along the normal axis of each face pair, one axis at a time
+#pragma unroll kAxisUnroll
   for (int d = 0; d < 3; ++d) {
     for (int l = tid; l < nc * M2; l += nt) {
       const int c = l / M2, qf = l - c * M2;
